@@ -1,0 +1,276 @@
+"""Seeded synthetic inputs shared by the CUDA path, its tests, the bench and the oracle.
+
+This module holds only problem set-up: grid descriptions, initial fields, Lagrangian marker
+and probe point sets, and random perturbations.  It contains none of the method's arithmetic
+(no fluxes, reconstructions, delta kernels or time stepping), so that neither side of a parity
+test can lean on the other through it.
+
+Set-ups follow arXiv:1905.00182:
+  * Sec. 3.1 (acoustic pulse scattered by a cylinder): rho = 1, u = 0,
+    p = 1/gamma + eps exp(-ln2 ((x-4)^2 + y^2) / 0.04), eps = 1e-3, cylinder D = 1 at the origin;
+  * Sec. 3.3 (rotating cylinder in a stream): Mach 0.2, Re 150, markers move with Omega x X;
+  * Sec. 3.6 (sphere scattering): rigid sphere of radius 0.5 at the origin; here an initial
+    Gaussian pulse centred at (2, 0, 0) replaces the periodic source.
+The sphere surface uses golden-spiral (Fibonacci) points with equal areas instead of the
+paper's triangulation; circle markers get a seeded phase offset.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+WENO5JS = 0
+TENO5 = 1
+MLP_TENO5 = 2
+
+FP64 = 0
+FP32_PERTURB = 1
+
+BC_ZERO_GRAD = 0
+BC_FREESTREAM = 1
+BC_PERIODIC = 2
+
+
+@dataclasses.dataclass
+class GridSpec:
+    dim: int
+    n: tuple                       # interior cells (nx, ny, nz); nz = 1 in 2D
+    lo: tuple                      # domain box
+    hi: tuple
+    gamma: float = 1.4
+    Re: float = 0.0                # <= 0: inviscid
+    qinf: tuple = (1.0, 0.0, 0.0, 0.0, 0.0)
+    scheme: int = WENO5JS
+    precision: int = FP64
+    bc: tuple = ((0, 0), (0, 0), (0, 0))
+    sponge_cells: int = 0
+    sponge_sigma: float = 0.0
+    alpha_pen: float = 0.0
+    beta_pen: float = 0.0
+    max_markers: int = 0
+
+    @property
+    def nv(self) -> int:
+        return self.dim + 2
+
+    @property
+    def h(self) -> tuple:
+        return tuple((self.hi[a] - self.lo[a]) / self.n[a] for a in range(self.dim))
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.n[: self.dim]))
+
+    def shape(self) -> tuple:
+        """Interior state shape [nv][nz][ny][nx]."""
+        nx, ny, nz = self.n
+        return (self.nv, nz, ny, nx)
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the splitmix64 generator (Steele, Lea & Flood 2014)."""
+    out = np.empty(count, dtype=np.float64)
+    mask = (1 << 64) - 1
+    x = seed & mask
+    for i in range(count):
+        x = (x + 0x9E3779B97F4A7C15) & mask
+        z = x
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z = z ^ (z >> 31)
+        out[i] = (z >> 11) * (1.0 / 9007199254740992.0)
+    return out
+
+
+def freestream(dim: int, gamma: float, rho: float = 1.0, vel=(0.0, 0.0, 0.0), p: Optional[float] = None):
+    """Conservative free-stream vector (padded to 5 entries) from rho, velocity and pressure."""
+    if p is None:
+        p = 1.0 / gamma
+    m = [rho * vel[a] for a in range(dim)]
+    ke = 0.5 * rho * sum(vel[a] ** 2 for a in range(dim))
+    q = [rho] + m + [p / (gamma - 1.0) + ke]
+    return tuple(q + [0.0] * (5 - len(q)))
+
+
+def node_coords(spec: GridSpec):
+    """Cell-centred node coordinates x_i = lo + (i + 1/2) h per active direction."""
+    return [spec.lo[a] + (np.arange(spec.n[a]) + 0.5) * spec.h[a] for a in range(spec.dim)]
+
+
+def mesh(spec: GridSpec):
+    """Coordinate arrays broadcast to the interior [nz][ny][nx] shape."""
+    xs = node_coords(spec)
+    if spec.dim == 2:
+        Y, X = np.meshgrid(xs[1], xs[0], indexing="ij")
+        return X[None], Y[None], None
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    return X, Y, Z
+
+
+def conservative(spec: GridSpec, rho, vel, p) -> np.ndarray:
+    """Pack primitive fields into the conservative state [rho, rho u, ..., E]."""
+    shape = spec.shape()
+    Q = np.empty(shape, dtype=np.float64)
+    Q[0] = rho
+    ke = np.zeros(shape[1:])
+    for a in range(spec.dim):
+        Q[1 + a] = rho * vel[a]
+        ke = ke + 0.5 * rho * vel[a] * vel[a]
+    Q[spec.nv - 1] = p / (spec.gamma - 1.0) + ke
+    return Q
+
+
+def gaussian_pulse_state(spec: GridSpec, center, amp: float = 1e-3, halfwidth: float = 0.2,
+                         rho0: float = 1.0, p0: Optional[float] = None, vel0=(0.0, 0.0, 0.0)):
+    """Initial pressure pulse p = p0 + amp exp(-ln2 |x - c|^2 / halfwidth^2), uniform rho, u."""
+    if p0 is None:
+        p0 = 1.0 / spec.gamma
+    X, Y, Z = mesh(spec)
+    r2 = (X - center[0]) ** 2 + (Y - center[1]) ** 2
+    if spec.dim == 3:
+        r2 = r2 + (Z - center[2]) ** 2
+    p = p0 + amp * np.exp(-math.log(2.0) * r2 / halfwidth ** 2)
+    rho = np.full(p.shape, rho0)
+    vel = [np.full(p.shape, vel0[a]) for a in range(spec.dim)]
+    return conservative(spec, rho, vel, p)
+
+
+def random_smooth_state(spec: GridSpec, seed: int, amp: float = 1e-3, modes: int = 3,
+                        vel0=(0.0, 0.0, 0.0), step: float = 0.0, periodic: bool = False):
+    """Background (rho = 1, p = 1/gamma, u = vel0) plus seeded random Fourier modes of
+    amplitude `amp` in every primitive, optionally a planar density step of relative size `step`
+    at x = mid-domain (a contact discontinuity, to exercise the non-linear weights)."""
+    rnd = splitmix64(seed, 8 * modes * (spec.dim + 2))
+    X, Y, Z = mesh(spec)
+    coords = [X, Y, Z][: spec.dim]
+    L = [spec.hi[a] - spec.lo[a] for a in range(spec.dim)]
+    fields = []
+    it = 0
+    for v in range(spec.dim + 2):
+        f = np.zeros(X.shape)
+        for _ in range(modes):
+            ph = 0.0
+            arg = np.zeros(X.shape)
+            for a in range(spec.dim):
+                kmax = 3
+                kk = int(rnd[it] * kmax) + 1 if periodic else rnd[it] * kmax + 0.5
+                it += 1
+                arg = arg + 2.0 * math.pi * kk * (coords[a] - spec.lo[a]) / L[a]
+            ph = 2.0 * math.pi * rnd[it]
+            it += 1
+            f = f + amp * np.sin(arg + ph)
+        fields.append(f)
+    rho = 1.0 + fields[0]
+    if step != 0.0:
+        xm = 0.5 * (spec.lo[0] + spec.hi[0])
+        rho = rho * np.where(X > xm, 1.0 + step, 1.0)
+    vel = [vel0[a] + fields[1 + a] for a in range(spec.dim)]
+    p = 1.0 / spec.gamma + fields[spec.dim + 1]
+    return conservative(spec, rho, vel, p)
+
+
+def circle_markers(n: int, radius: float = 0.5, center=(0.0, 0.0), seed: int = 0,
+                   omega: float = 0.0):
+    """n equally spaced markers on a circle, theta_k = 2 pi (k + phi)/n with a seeded phase phi;
+    velocity Omega z x X (zero for a fixed body); arc-length weights dS = 2 pi R / n.
+    Returns X [2][n], U [2][n], dS [n]."""
+    phi = splitmix64(seed, 1)[0]
+    th = 2.0 * math.pi * (np.arange(n) + phi) / n
+    X = np.stack([center[0] + radius * np.cos(th), center[1] + radius * np.sin(th)])
+    U = np.stack([-omega * (X[1] - center[1]), omega * (X[0] - center[0])])
+    dS = np.full(n, 2.0 * math.pi * radius / n)
+    return X, U, dS
+
+
+def fibonacci_sphere(n: int, radius: float = 0.5, center=(0.0, 0.0, 0.0)):
+    """n golden-spiral points on a sphere with equal area weights 4 pi R^2 / n.
+    Returns X [3][n], U [3][n] (zero), dS [n]."""
+    k = np.arange(n) + 0.5
+    z = 1.0 - 2.0 * k / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    ga = math.pi * (3.0 - math.sqrt(5.0))
+    th = ga * k
+    X = np.stack([center[0] + radius * r * np.cos(th), center[1] + radius * r * np.sin(th),
+                  center[2] + radius * z])
+    U = np.zeros_like(X)
+    dS = np.full(n, 4.0 * math.pi * radius * radius / n)
+    return X, U, dS
+
+
+def ring_probes(n: int, radius: float, center=(0.0, 0.0)):
+    th = 2.0 * math.pi * np.arange(n) / n
+    return np.stack([center[0] + radius * np.cos(th), center[1] + radius * np.sin(th)])
+
+
+def penalty_defaults(h: float, dt: float, kappa: float = 0.5, rho: float = 1.0):
+    """Penalty constants of Eq. 7 (the paper gives none): a dense marker sheet feeds back a slip
+    fraction of about dt * beta * (3/8) / (rho h) per stage, so beta = kappa rho h / ((3/8) dt)
+    removes a fraction kappa of the slip per stage; alpha = k beta^2 / 4 with k = 3/(8 rho h)
+    makes the spring-dashpot slip dynamics critically damped."""
+    beta = kappa * rho * h / (0.375 * dt)
+    k = 0.375 / (rho * h)
+    alpha = k * beta * beta / 4.0
+    return alpha, beta
+
+
+# --------------------------------------------------------------------------------------------
+# The five workloads (synthetic, seeded).
+# --------------------------------------------------------------------------------------------
+
+def cylinder_pulse_2d(n: int = 256, markers: int = 160, Re: float = 1e4, scheme: int = WENO5JS,
+                      precision: int = FP64):
+    """Acoustic pulse scattered by a rigid cylinder (Sec. 3.1): [-10,10]^2, D = 1, pulse at (4,0)
+    with amplitude 1e-3 and half-width 0.2, gamma 1.4, zero-gradient boundaries."""
+    g = 1.4
+    spec = GridSpec(dim=2, n=(n, n, 1), lo=(-10.0, -10.0, 0.0), hi=(10.0, 10.0, 1.0), gamma=g,
+                    Re=Re, qinf=freestream(2, g), scheme=scheme, precision=precision,
+                    max_markers=markers)
+    h = spec.h[0]
+    dt = 0.5 / (2.0 / h)  # CFL 0.5 with alpha_x = alpha_y = c = 1 at rest (fixed from the start)
+    spec.alpha_pen, spec.beta_pen = penalty_defaults(h, dt)
+    Q = gaussian_pulse_state(spec, (4.0, 0.0))
+    X, U, dS = circle_markers(markers, 0.5, seed=0)
+    probes = np.array([[2.0, 2.0], [0.0, 2.0]])
+    return dict(spec=spec, Q=Q, X=X, U=U, dS=dS, dt=dt, steps=100, probes=probes)
+
+
+def rotating_cylinder_2d(n: int = 2048, markers: int = 1024, scheme: int = WENO5JS,
+                         precision: int = FP64):
+    """Rotating cylinder in a uniform stream (Sec. 3.3): Mach 0.2, Re 150, [-40,40]^2, 20-cell
+    sponge, surface speed 0.5 U, 360 probes on a ring r = 30."""
+    g = 1.4
+    U0 = 0.2
+    spec = GridSpec(dim=2, n=(n, n, 1), lo=(-40.0, -40.0, 0.0), hi=(40.0, 40.0, 1.0), gamma=g,
+                    Re=150.0, qinf=freestream(2, g, vel=(U0, 0.0, 0.0)), scheme=scheme,
+                    precision=precision, bc=((1, 1), (1, 1), (0, 0)), sponge_cells=20,
+                    max_markers=markers)
+    h = spec.h[0]
+    dt = 0.5 / ((1.0 + U0) / h + 1.0 / h)
+    spec.alpha_pen, spec.beta_pen = penalty_defaults(h, dt)
+    spec.sponge_sigma = 0.5 * (1.0 + U0) / h
+    Q = random_smooth_state(spec, seed=3, amp=0.0, modes=1, vel0=(U0, 0.0, 0.0))
+    omega = 0.5 * U0 / 0.5
+    X, U, dS = circle_markers(markers, 0.5, seed=0, omega=omega)
+    probes = ring_probes(360, 30.0)
+    return dict(spec=spec, Q=Q, X=X, U=U, dS=dS, dt=dt, steps=20000, probes=probes)
+
+
+def sphere_pulse_3d(n: int = 512, markers: int = 20000, Re: float = 1e4, scheme: int = TENO5,
+                    precision: int = FP64, probes: int = 1000, L: float = 8.0):
+    """Acoustic pulse scattered by a rigid sphere (Sec. 3.6 analogue): [-L,L]^3 (h = 2L/n), sphere
+    D = 1 at the origin with Fibonacci markers, Gaussian pulse (1e-3, half-width 0.2) at (2,0,0),
+    TENO5, zero-gradient boundaries, probes on a Fibonacci sphere r = 6 (scaled with L)."""
+    g = 1.4
+    spec = GridSpec(dim=3, n=(n, n, n), lo=(-L, -L, -L), hi=(L, L, L), gamma=g, Re=Re,
+                    qinf=freestream(3, g), scheme=scheme, precision=precision,
+                    max_markers=markers)
+    h = spec.h[0]
+    dt = 0.5 / (3.0 / h)
+    spec.alpha_pen, spec.beta_pen = penalty_defaults(h, dt)
+    Q = gaussian_pulse_state(spec, (2.0, 0.0, 0.0))
+    X, U, dS = fibonacci_sphere(markers, 0.5)
+    pr, _, _ = fibonacci_sphere(probes, 6.0 * L / 8.0)
+    return dict(spec=spec, Q=Q, X=X, U=U, dS=dS, dt=dt, steps=2000, probes=pr)
