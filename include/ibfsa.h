@@ -1,0 +1,155 @@
+/*
+ * ibfsa.h -- C ABI of the GB300 (sm_103a) stage right-hand side of the immersed-boundary
+ * WENO/TENO method for fluid-structure-acoustics interaction of Wang, Tian & Lai
+ * (arXiv:1905.00182, Sec. 2).
+ *
+ * What one call computes (Sec. 2):
+ *   compressible Navier-Stokes, Eq. 2-5, on a uniform Cartesian grid with cell-centred nodes
+ *   x_i = lo + (i + 1/2) h, h = (hi - lo)/n;  Q = [rho, rho u, rho v, (rho w), E];
+ *   convective fluxes split by a global Lax-Friedrichs splitting f+- = (F +- alpha_d Q)/2 with
+ *   alpha_d = max(|u_d| + c) of the stage input, reconstructed component-wise at every face by
+ *   fifth-order WENO5-JS or TENO5 (text after Eq. 5), differenced conservatively;
+ *   viscous fluxes [0, tau_{.d}, b_d] (Eq. 5, no heat flux) by fourth-order central
+ *   differences (gradients, then divergence), scaled by 1/Re;
+ *   penalty immersed boundary: U_ib = sum_j u_j delta_h(X - x_j) h^d (Eq. 8),
+ *   F = alpha_pen xi + beta_pen (U_ib - U) with xi = int (U_ib - U) dt (Eq. 7),
+ *   f = -sum_k F_k delta_h(X_k - x) dS_k (Eq. 9), delta_h from Peskin's four-point
+ *   lambda (Eq. 10-11); the fluid source is S = [0, f, f.u];
+ *   third-order TVD (SSP) Runge-Kutta of Shu & Osher on Q and xi (text after Eq. 5).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: IBFSA_OK (0) or a negative IBFSA_ERR_* code; ibfsa_last_error() gives a
+ *    thread-local message for the last failure.
+ *  - Memory: the library allocates NO device memory.  The caller allocates one workspace of
+ *    ibfsa_workspace_bytes() bytes (256-byte aligned) and owns it; all grid state lives there.
+ *    Array arguments may be device pointers or host pointers (copies use cudaMemcpyDefault);
+ *    host memory should be pinned for asynchronous copies.
+ *  - Streams: every launch and copy goes to the stream given at ibfsa_create_grid (a
+ *    cudaStream_t passed as void*, NULL = legacy default stream).  Calls are asynchronous
+ *    unless stated; only calls returning values to the host synchronise that stream.
+ *  - Layouts: state arrays are structure-of-arrays [nv][nz][ny][nx], x fastest, FP64, with
+ *    nv = dim + 2 and nz = 1 in 2D.  Marker and probe arrays are [dim][n] (coordinates of point
+ *    k at k, n + k, 2n + k).
+ *  - Errors found on the device (a marker whose four-point support leaves the interior) set
+ *    bits of a device status word, read by ibfsa_get_status(); kernels never trap.
+ */
+#ifndef IBFSA_H
+#define IBFSA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  IBFSA_OK = 0,
+  IBFSA_ERR_ARG = -1,         /* invalid argument (NULL, size, descriptor field) */
+  IBFSA_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+  IBFSA_ERR_NONFINITE = -3,   /* state holds NaN/Inf (reported by ibfsa_get_status) */
+  IBFSA_ERR_BOUNDS = -4,      /* marker/probe support outside the interior */
+  IBFSA_ERR_UNSUPPORTED = -5, /* descriptor asks for a variant this build does not provide */
+  IBFSA_ERR_WORKSPACE = -6    /* workspace too small or misaligned */
+};
+
+/* convective schemes (text after Eq. 5) */
+enum { IBFSA_WENO5JS = 0, IBFSA_TENO5 = 1 };
+/* arithmetic of the stage kernels */
+enum { IBFSA_FP64 = 0 };
+/* boundary rules per face of the box: ghost cells copy the nearest interior cell, hold the
+ * free stream, or wrap around */
+enum { IBFSA_BC_ZERO_GRAD = 0, IBFSA_BC_FREESTREAM = 1, IBFSA_BC_PERIODIC = 2 };
+/* status bits of ibfsa_get_status */
+enum { IBFSA_STATUS_BOUNDS = 1, IBFSA_STATUS_NONFINITE = 2 };
+
+typedef struct ibfsa_grid ibfsa_grid; /* opaque; created and destroyed by the library */
+
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int n[3];                /* interior cells per direction; n[2] = 1 in 2D */
+  double lo[3], hi[3];     /* domain box */
+  double gamma;            /* ratio of specific heats (ideal gas) */
+  double Re;               /* Reynolds number of Eq. 2; Re <= 0 drops the viscous terms */
+  double qinf[5];          /* free-stream conservative state (first nv entries used) */
+  int scheme;              /* IBFSA_WENO5JS | IBFSA_TENO5 */
+  int precision;           /* IBFSA_FP64 */
+  int strict_fp;           /* 1: every FP64 operation rounded separately (no fused
+                              multiply-add), divisions kept as divisions, spreading summed
+                              cell by cell in marker order -- the result is reproducible bit
+                              for bit by a sequential FP64 evaluation of the same formulas in
+                              the same order.  0: fused multiply-add and reciprocals allowed,
+                              spreading by atomics (faster; rounding differs). */
+  int bc[3][2];            /* IBFSA_BC_* for the low/high face of each direction; periodic
+                              needs both faces periodic and n >= 4 */
+  int sponge_cells;        /* width S of an absorbing layer (0 = none): L -= sigma (Q - qinf)
+                              with sigma = sponge_sigma ((S - m)/S)^3, m = cells to the wall */
+  double sponge_sigma;
+  double alpha_pen;        /* alpha of Eq. 7 */
+  double beta_pen;         /* beta of Eq. 7 */
+  int max_markers;         /* capacity for Lagrangian markers */
+  int max_probes;          /* capacity for probe points */
+} ibfsa_grid_desc;
+
+/* Bytes of device workspace a grid with this descriptor needs (for the caller to allocate). */
+int ibfsa_workspace_bytes(const ibfsa_grid_desc *desc, size_t *bytes);
+
+/* Create a grid on the current CUDA device.  d_workspace: device memory of at least
+ * ibfsa_workspace_bytes() bytes, 256-byte aligned, owned by the caller and kept alive until
+ * ibfsa_destroy_grid.  cuda_stream: cudaStream_t for all work of this grid.  The state is
+ * undefined until ibfsa_set_state; the marker count is 0 until ibfsa_set_markers. */
+int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t workspace_bytes,
+                      void *cuda_stream, ibfsa_grid **out);
+
+/* Release the host-side grid object (the workspace stays the caller's). */
+int ibfsa_destroy_grid(ibfsa_grid *g);
+
+/* Copy the interior state Q [nv][nz][ny][nx] (device or host pointer) in, or out.
+ * ibfsa_get_state synchronises the grid's stream when Q is host memory. */
+int ibfsa_set_state(ibfsa_grid *g, const double *Q);
+int ibfsa_get_state(ibfsa_grid *g, double *Q);
+
+/* Lagrangian markers of the immersed boundary (Eq. 7-9): positions X [dim][n], velocities U
+ * [dim][n] (held for the whole step) and quadrature weights dS [n] (arc length in 2D, area in
+ * 3D).  reset_integral = 1 zeroes xi = int (U_ib - U) dt; 0 keeps it (same markers, moved).
+ * Every marker's support must lie two cells inside the interior; violations set
+ * IBFSA_STATUS_BOUNDS (checked on the device, read with ibfsa_get_status). */
+int ibfsa_set_markers(ibfsa_grid *g, int n, const double *X, const double *U, const double *dS,
+                      int reset_integral);
+
+/* Penalty force F_k of Eq. 7 at the last evaluated stage, [dim][n] (device or host). */
+int ibfsa_get_marker_forces(ibfsa_grid *g, double *F);
+
+/* xi = int (U_ib - U) dt per marker, [dim][n], in or out (device or host). */
+int ibfsa_get_penalty_integral(ibfsa_grid *g, double *xi);
+int ibfsa_set_penalty_integral(ibfsa_grid *g, const double *xi);
+
+/* Right-hand side dQ/dt = L(Q) + S at the current state (Eq. 2 with the IB source of Eq. 9),
+ * written to L [nv][nz][ny][nx] (device pointer).  Also leaves the marker forces of Eq. 7. */
+int ibfsa_rhs(ibfsa_grid *g, double *L);
+
+/* Advance the state and xi by nsteps third-order SSP Runge-Kutta steps of size dt:
+ *   Q1 = Qn + dt L(Qn);  Q2 = 3/4 Qn + 1/4 (Q1 + dt L(Q1));  Qn+1 = 1/3 Qn + 2/3 (Q2 + dt L(Q2)),
+ * each stage evaluated as a Qn + b (Qs + dt L(Qs)).  Markers stay fixed during the call. */
+int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps);
+
+/* Split speeds alpha_d = max over the interior of |u_d| + c of the current state, d < dim,
+ * to the host (synchronises), for dt = CFL / sum_d (alpha_d / h_d). */
+int ibfsa_max_wavespeed(ibfsa_grid *g, double *host_alpha);
+
+/* Pressure fluctuation dp = sum_j p_j prod_d lambda((x_p - x_j)/h_d) - p_inf (the fluctuation
+ * of Sec. 3.1 sampled with the same four-point kernel as Eq. 8) at np points xp [dim][np]
+ * (device or host) into out [np] (device or host; synchronises when out is host memory). */
+int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out);
+
+/* Device status bits (IBFSA_STATUS_*) accumulated since the last call; clears them.
+ * Synchronises the grid's stream. */
+int ibfsa_get_status(ibfsa_grid *g, int *host_flags);
+
+/* Message of the last failing call on this thread. */
+const char *ibfsa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBFSA_H */

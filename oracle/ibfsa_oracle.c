@@ -498,6 +498,11 @@ static int check_desc(const orc_desc *d) {
   for (int a = 0; a < d->dim; a++)
     if (d->n[a] < 1 || !(d->hi[a] > d->lo[a])) return ORC_ERR_ARG;
   if (d->dim == 2 && d->n[2] != 1) return ORC_ERR_ARG;
+  for (int a = 0; a < d->dim; a++) {
+    int p0 = d->bc[a][0] == 2, p1 = d->bc[a][1] == 2;
+    if (p0 != p1) return ORC_ERR_ARG;          /* periodic on both faces or on neither */
+    if (p0 && d->n[a] < NG) return ORC_ERR_ARG; /* wrap-around ghosts need n >= 4 */
+  }
   return ORC_OK;
 }
 

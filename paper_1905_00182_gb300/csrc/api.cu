@@ -1,0 +1,407 @@
+// api.cu -- the C ABI of libibfsa (include/ibfsa.h): descriptor checks, workspace layout, grid
+// object, and the host sequence of stages of the third-order SSP Runge-Kutta step
+// (arXiv:1905.00182, Sec. 2, text after Eq. 5).
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "ibfsa_internal.h"
+
+namespace ibfsa {
+
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *where) {
+  return fail(IBFSA_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int check_desc(const ibfsa_grid_desc *d) {
+  if (!d) return fail(IBFSA_ERR_ARG, "descriptor is NULL");
+  if (d->dim != 2 && d->dim != 3) return fail(IBFSA_ERR_ARG, "dim must be 2 or 3 (got %d)", d->dim);
+  for (int a = 0; a < d->dim; a++) {
+    if (d->n[a] < 1) return fail(IBFSA_ERR_ARG, "n[%d] = %d must be >= 1", a, d->n[a]);
+    if (!(d->hi[a] > d->lo[a])) return fail(IBFSA_ERR_ARG, "hi[%d] must exceed lo[%d]", a, a);
+    for (int s = 0; s < 2; s++)
+      if (d->bc[a][s] < 0 || d->bc[a][s] > 2)
+        return fail(IBFSA_ERR_ARG, "bc[%d][%d] = %d is not a boundary rule", a, s, d->bc[a][s]);
+    bool p0 = d->bc[a][0] == IBFSA_BC_PERIODIC, p1 = d->bc[a][1] == IBFSA_BC_PERIODIC;
+    if (p0 != p1) return fail(IBFSA_ERR_ARG, "periodic direction %d needs both faces periodic", a);
+    if (p0 && d->n[a] < NG) return fail(IBFSA_ERR_ARG, "periodic direction %d needs n >= %d", a, NG);
+  }
+  if (d->dim == 2 && d->n[2] != 1) return fail(IBFSA_ERR_ARG, "n[2] must be 1 in 2D");
+  long long cells = 1, padded = 1;
+  for (int a = 0; a < d->dim; a++) {
+    cells *= d->n[a];
+    padded *= d->n[a] + 2 * NG;
+  }
+  if (padded * (d->dim + 2) > (1LL << 40)) return fail(IBFSA_ERR_ARG, "grid too large");
+  if (!(d->gamma > 1.0)) return fail(IBFSA_ERR_ARG, "gamma must exceed 1");
+  if (!(d->qinf[0] > 0.0)) return fail(IBFSA_ERR_ARG, "free-stream density must be positive");
+  if (d->scheme != IBFSA_WENO5JS && d->scheme != IBFSA_TENO5)
+    return fail(IBFSA_ERR_UNSUPPORTED, "scheme %d is not provided by this build", d->scheme);
+  if (d->precision != IBFSA_FP64)
+    return fail(IBFSA_ERR_UNSUPPORTED, "precision %d is not provided by this build", d->precision);
+  if (d->sponge_cells < 0 || d->max_markers < 0 || d->max_probes < 0)
+    return fail(IBFSA_ERR_ARG, "negative sponge width or capacity");
+  (void)cells;
+  return IBFSA_OK;
+}
+
+void plan_geometry(const ibfsa_grid_desc &d, Plan &p) {
+  memset(&p, 0, sizeof(p));
+  p.dim = d.dim;
+  p.nv = d.dim + 2;
+  p.N = 1;
+  p.NP = 1;
+  p.NB = 1;
+  for (int a = 0; a < 3; a++) {
+    bool act = a < d.dim;
+    p.n[a] = act ? d.n[a] : 1;
+    p.g[a] = act ? NG : 0;
+    p.P[a] = p.n[a] + 2 * p.g[a];
+    p.B[a] = act ? p.n[a] + 4 : 1;
+    p.N *= p.n[a];
+    p.NP *= p.P[a];
+    p.NB *= p.B[a];
+    p.lo[a] = d.lo[a];
+    p.h[a] = act ? (d.hi[a] - d.lo[a]) / d.n[a] : 1.0;
+    p.inv_h[a] = 1.0 / p.h[a];
+    p.h12[a] = 12.0 * p.h[a];
+    p.inv_h12[a] = 1.0 / p.h12[a];
+  }
+  p.gamma = d.gamma;
+  p.gm1 = d.gamma - 1.0;
+  p.Re = d.Re;
+  p.inv_Re = d.Re > 0.0 ? 1.0 / d.Re : 0.0;
+  for (int c = 0; c < 5; c++) p.qinf[c] = d.qinf[c];
+  double ke = 0.0;
+  for (int a = 0; a < d.dim; a++) {
+    p.prim_inf[a] = d.qinf[1 + a] / d.qinf[0];
+    ke += d.qinf[1 + a] * (d.qinf[1 + a] / d.qinf[0]);
+  }
+  p.p_inf = (d.gamma - 1.0) * (d.qinf[d.dim + 1] - 0.5 * ke);
+  p.prim_inf[3] = p.p_inf;
+  p.scheme = d.scheme;
+  for (int a = 0; a < 3; a++)
+    for (int s = 0; s < 2; s++) p.bc[a][s] = d.bc[a][s];
+  p.sponge_cells = d.sponge_cells;
+  p.sponge_sigma = d.sponge_sigma;
+  p.alpha_pen = d.alpha_pen;
+  p.beta_pen = d.beta_pen;
+  p.hprod = 1.0;
+  for (int a = 0; a < d.dim; a++) p.hprod *= p.h[a];
+  // TENO5 weights of the kept stencils: d_k delta_k / sum_j d_j delta_j, d = (0.1, 0.6, 0.3)
+  const double dlin[3] = {0.1, 0.6, 0.3};
+  for (int m = 0; m < 8; m++) {
+    double w[3], sw = 0.0;
+    for (int k = 0; k < 3; k++) {
+      w[k] = (m >> k) & 1 ? dlin[k] : 0.0;
+      sw += w[k];
+    }
+    for (int k = 0; k < 3; k++) p.teno_w[m][k] = sw > 0.0 ? w[k] / sw : 0.0;
+  }
+  p.max_markers = d.max_markers;
+}
+
+Layout layout_for(const ibfsa_grid_desc &d) {
+  Plan p;
+  plan_geometry(d, p);
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  size_t state = sizeof(double) * p.nv * (size_t)p.N;
+  size_t M = (size_t)(d.max_markers > 0 ? d.max_markers : 1);
+  size_t Pn = (size_t)(d.max_probes > 0 ? d.max_probes : 1);
+  L.Q = take(state);
+  L.Q1 = take(state);
+  L.Q2 = take(state);
+  L.L = take(state);
+  L.Qp = take(sizeof(double) * p.nv * (size_t)p.NP);
+  L.Wp = take(sizeof(double) * (p.dim + 1) * (size_t)p.NP);
+  L.V = d.Re > 0.0 ? take(sizeof(double) * p.dim * (p.dim + 1) * (size_t)p.NB) : take(0);
+  L.f = (d.strict_fp && d.max_markers > 0) ? take(sizeof(double) * p.dim * (size_t)p.N) : take(0);
+  L.X = take(sizeof(double) * p.dim * M);
+  L.U = take(sizeof(double) * p.dim * M);
+  L.dS = take(sizeof(double) * M);
+  L.F = take(sizeof(double) * p.dim * M);
+  L.xi = take(sizeof(double) * p.dim * M);
+  L.xi1 = take(sizeof(double) * p.dim * M);
+  L.xi2 = take(sizeof(double) * p.dim * M);
+  L.alpha = take(sizeof(unsigned long long) * 4);
+  L.status = take(sizeof(int) * 4);
+  L.probe_xp = take(sizeof(double) * p.dim * Pn);
+  L.probe_out = take(sizeof(double) * Pn);
+  L.total = off;
+  return L;
+}
+
+static cudaError_t run_stage(Grid *G, const StageArgs &s) {
+  return G->d.strict_fp ? strict_stage(G->p, s, G->stream) : fast_stage(G->p, s, G->stream);
+}
+
+}  // namespace ibfsa
+
+using namespace ibfsa;
+
+struct ibfsa_grid {
+  Grid g;
+};
+
+extern "C" {
+
+const char *ibfsa_last_error(void) { return g_err; }
+
+int ibfsa_workspace_bytes(const ibfsa_grid_desc *desc, size_t *bytes) {
+  int rc = check_desc(desc);
+  if (rc) return rc;
+  if (!bytes) return fail(IBFSA_ERR_ARG, "bytes is NULL");
+  *bytes = layout_for(*desc).total;
+  return IBFSA_OK;
+}
+
+int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t workspace_bytes,
+                      void *cuda_stream, ibfsa_grid **out) {
+  int rc = check_desc(desc);
+  if (rc) return rc;
+  if (!out) return fail(IBFSA_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  Layout L = layout_for(*desc);
+  if (!d_workspace || workspace_bytes < L.total)
+    return fail(IBFSA_ERR_WORKSPACE, "workspace of %zu bytes given, %zu needed", workspace_bytes,
+                L.total);
+  if (((uintptr_t)d_workspace & 255) != 0)
+    return fail(IBFSA_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  ibfsa_grid *h = new (std::nothrow) ibfsa_grid;
+  if (!h) return fail(IBFSA_ERR_ARG, "host allocation of the grid object failed");
+  Grid &G = h->g;
+  G.d = *desc;
+  plan_geometry(*desc, G.p);
+  G.stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&G.device);
+  char *w = (char *)d_workspace;
+  G.Q = (double *)(w + L.Q);
+  G.Q1 = (double *)(w + L.Q1);
+  G.Q2 = (double *)(w + L.Q2);
+  G.p.L = (double *)(w + L.L);
+  G.p.Qp = (double *)(w + L.Qp);
+  G.p.Wp = (double *)(w + L.Wp);
+  G.p.V = (double *)(w + L.V);
+  G.p.f = (double *)(w + L.f);
+  G.X = (double *)(w + L.X);
+  G.U = (double *)(w + L.U);
+  G.dS = (double *)(w + L.dS);
+  G.p.X = G.X;
+  G.p.U = G.U;
+  G.p.dS = G.dS;
+  G.p.F = (double *)(w + L.F);
+  G.xi = (double *)(w + L.xi);
+  G.xi1 = (double *)(w + L.xi1);
+  G.xi2 = (double *)(w + L.xi2);
+  G.p.alpha_bits = (unsigned long long *)(w + L.alpha);
+  G.p.status = (int *)(w + L.status);
+  G.probe_xp = (double *)(w + L.probe_xp);
+  G.probe_out = (double *)(w + L.probe_out);
+  G.max_probes = desc->max_probes;
+  G.p.nm = 0;
+  cudaError_t e = cudaMemsetAsync(G.p.status, 0, sizeof(int) * 4, G.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G.p.F, 0, L.xi - L.F, G.stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(G.xi, 0, sizeof(double) * G.p.dim * (desc->max_markers > 0 ? desc->max_markers : 1), G.stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "ibfsa_create_grid");
+  }
+  *out = h;
+  return IBFSA_OK;
+}
+
+int ibfsa_destroy_grid(ibfsa_grid *g) {
+  delete g;
+  return IBFSA_OK;
+}
+
+static bool is_host_pointer(const void *ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+int ibfsa_set_state(ibfsa_grid *g, const double *Q) {
+  if (!g || !Q) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  cudaError_t e = cudaMemcpyAsync(G.Q, Q, sizeof(double) * G.p.nv * G.p.N, cudaMemcpyDefault,
+                                  G.stream);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_set_state");
+}
+
+int ibfsa_get_state(ibfsa_grid *g, double *Q) {
+  if (!g || !Q) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  cudaError_t e = cudaMemcpyAsync(Q, G.Q, sizeof(double) * G.p.nv * G.p.N, cudaMemcpyDefault,
+                                  G.stream);
+  if (e == cudaSuccess && is_host_pointer(Q)) e = cudaStreamSynchronize(G.stream);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_get_state");
+}
+
+int ibfsa_set_markers(ibfsa_grid *g, int n, const double *X, const double *U, const double *dS,
+                      int reset_integral) {
+  if (!g) return fail(IBFSA_ERR_ARG, "NULL grid");
+  Grid &G = g->g;
+  if (n < 0 || n > G.d.max_markers)
+    return fail(IBFSA_ERR_ARG, "marker count %d outside [0, %d]", n, G.d.max_markers);
+  if (n > 0 && (!X || !U || !dS)) return fail(IBFSA_ERR_ARG, "NULL marker array");
+  int M = G.d.max_markers, dim = G.p.dim;
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < dim && e == cudaSuccess && n > 0; a++) {
+    e = cudaMemcpyAsync(G.X + (size_t)a * M, X + (size_t)a * n, sizeof(double) * n,
+                        cudaMemcpyDefault, G.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(G.U + (size_t)a * M, U + (size_t)a * n, sizeof(double) * n,
+                          cudaMemcpyDefault, G.stream);
+  }
+  if (e == cudaSuccess && n > 0)
+    e = cudaMemcpyAsync(G.dS, dS, sizeof(double) * n, cudaMemcpyDefault, G.stream);
+  if (e == cudaSuccess && reset_integral)
+    e = cudaMemsetAsync(G.xi, 0, sizeof(double) * dim * (M > 0 ? M : 1), G.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ibfsa_set_markers");
+  G.p.nm = n;
+  return IBFSA_OK;
+}
+
+static int copy_marker_array(Grid &G, double *dst_user, const double *src_ws, bool to_user) {
+  int M = G.d.max_markers, n = G.p.nm;
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < G.p.dim && e == cudaSuccess && n > 0; a++) {
+    if (to_user)
+      e = cudaMemcpyAsync(dst_user + (size_t)a * n, src_ws + (size_t)a * M, sizeof(double) * n,
+                          cudaMemcpyDefault, G.stream);
+    else
+      e = cudaMemcpyAsync((double *)src_ws + (size_t)a * M, dst_user + (size_t)a * n,
+                          sizeof(double) * n, cudaMemcpyDefault, G.stream);
+  }
+  if (e == cudaSuccess && to_user && n > 0 && is_host_pointer(dst_user))
+    e = cudaStreamSynchronize(G.stream);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "marker copy");
+}
+
+int ibfsa_get_marker_forces(ibfsa_grid *g, double *F) {
+  if (!g || !F) return fail(IBFSA_ERR_ARG, "NULL argument");
+  return copy_marker_array(g->g, F, g->g.p.F, true);
+}
+
+int ibfsa_get_penalty_integral(ibfsa_grid *g, double *xi) {
+  if (!g || !xi) return fail(IBFSA_ERR_ARG, "NULL argument");
+  return copy_marker_array(g->g, xi, g->g.xi, true);
+}
+
+int ibfsa_set_penalty_integral(ibfsa_grid *g, const double *xi) {
+  if (!g || !xi) return fail(IBFSA_ERR_ARG, "NULL argument");
+  return copy_marker_array(g->g, (double *)xi, g->g.xi, false);
+}
+
+int ibfsa_rhs(ibfsa_grid *g, double *L) {
+  if (!g || !L) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  StageArgs s{};
+  s.Qs = G.Q;
+  s.Lout = L;
+  s.xis = G.xi;
+  s.stage = -1;
+  cudaError_t e = run_stage(&G, s);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_rhs");
+}
+
+int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps) {
+  if (!g) return fail(IBFSA_ERR_ARG, "NULL grid");
+  if (nsteps < 0 || !(dt > 0.0)) return fail(IBFSA_ERR_ARG, "need dt > 0 and nsteps >= 0");
+  Grid &G = g->g;
+  // Shu-Osher coefficients: Q^(s+1) = a_s Qn + b_s (Q^(s) + dt L(Q^(s)))
+  const double A[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0}, B[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  for (int step = 0; step < nsteps; step++) {
+    const double *in[3] = {G.Q, G.Q1, G.Q2};
+    double *outs[3] = {G.Q1, G.Q2, G.Q};  // stage 3 overwrites Qn cell by cell (pointwise read)
+    const double *xin[3] = {G.xi, G.xi1, G.xi2};
+    double *xout[3] = {G.xi1, G.xi2, G.xi};
+    for (int s = 0; s < 3; s++) {
+      StageArgs a{};
+      a.Qs = in[s];
+      a.Qn = G.Q;
+      a.Qo = outs[s];
+      a.xis = xin[s];
+      a.xin = G.xi;
+      a.xio = xout[s];
+      a.a = A[s];
+      a.b = B[s];
+      a.dt = dt;
+      a.stage = s;
+      cudaError_t e = run_stage(&G, a);
+      if (e != cudaSuccess) return cuda_fail(e, "ibfsa_rk3_step");
+    }
+  }
+  return IBFSA_OK;
+}
+
+int ibfsa_max_wavespeed(ibfsa_grid *g, double *host_alpha) {
+  if (!g || !host_alpha) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  cudaError_t e = G.d.strict_fp ? strict_wavespeed(G.p, G.Q, G.stream)
+                                : fast_wavespeed(G.p, G.Q, G.stream);
+  unsigned long long bits[3] = {0, 0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bits, G.p.alpha_bits, sizeof(bits), cudaMemcpyDeviceToHost, G.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ibfsa_max_wavespeed");
+  for (int a = 0; a < G.p.dim; a++) memcpy(&host_alpha[a], &bits[a], sizeof(double));
+  return IBFSA_OK;
+}
+
+int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out) {
+  if (!g || (np > 0 && (!xp || !out))) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  if (np < 0 || np > G.max_probes)
+    return fail(IBFSA_ERR_ARG, "probe count %d outside [0, %d]", np, G.max_probes);
+  if (np == 0) return IBFSA_OK;
+  cudaError_t e = cudaMemcpyAsync(G.probe_xp, xp, sizeof(double) * G.p.dim * np,
+                                  cudaMemcpyDefault, G.stream);
+  if (e == cudaSuccess)
+    e = G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream)
+                      : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, G.probe_out, sizeof(double) * np, cudaMemcpyDefault, G.stream);
+  if (e == cudaSuccess && is_host_pointer(out)) e = cudaStreamSynchronize(G.stream);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_probe");
+}
+
+int ibfsa_get_status(ibfsa_grid *g, int *host_flags) {
+  if (!g || !host_flags) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, G.p.status, sizeof(int), cudaMemcpyDeviceToHost, G.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G.p.status, 0, sizeof(int), G.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ibfsa_get_status");
+  *host_flags = v;
+  return IBFSA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// ibfsa_internal.h -- grid object, device plan and launch interface shared by the CUDA
+// translation units of libibfsa (never by anything outside this library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ibfsa.h"
+
+namespace ibfsa {
+
+constexpr int NG = 4;  // ghost layers: a fourth-order derivative of a fourth-order derivative
+
+// Everything a kernel needs, passed by value.  Padded arrays cover [-4, n+4) in every active
+// direction (one layer of extent 1 in an inactive z), x fastest.
+struct Plan {
+  int dim, nv;
+  int n[3];       // interior extents (n[2] = 1 in 2D)
+  int P[3];       // padded extents
+  int g[3];       // ghost layers per direction (4 or 0)
+  long long N;    // interior cells
+  long long NP;   // padded cells
+  double lo[3], h[3], inv_h[3], h12[3], inv_h12[3];  // h12 = 12 h
+  double gamma, gm1, Re, inv_Re;
+  double qinf[5];
+  double prim_inf[4];  // u, v, w, p of the free stream
+  double p_inf;
+  int scheme;
+  int bc[3][2];
+  int sponge_cells;
+  double sponge_sigma;
+  double alpha_pen, beta_pen;
+  double hprod;        // product of h over active directions
+  // TENO: 1/sum of kept linear weights per cut-off mask (bit k = stencil k kept)
+  double teno_w[8][3];
+
+  // device buffers
+  double *Qp;          // padded conservative state [nv][NP]
+  double *Wp;          // padded primitives [u, v, (w), p] -> [dim+1][NP]
+  double *L;           // right-hand side accumulator [nv][N]
+  double *V;           // viscous fluxes on the box [-2, n+2): [dim][dim+1][NB]
+  int B[3];            // box extents (n + 4 per active direction)
+  long long NB;
+  double *f;           // strict mode: spread force [dim][N]
+  unsigned long long *alpha_bits;  // [3] ordered bits of the split speeds
+  int *status;
+  // markers
+  int nm;
+  int max_markers;
+  const double *X, *U, *dS;   // [dim][max_markers]
+  double *F;                  // marker force of Eq. 7 [dim][max_markers]
+};
+
+struct Grid {
+  ibfsa_grid_desc d;
+  Plan p;
+  cudaStream_t stream;
+  int device;
+  // carved workspace
+  double *Q, *Q1, *Q2;         // interior states [nv][N]
+  double *X, *U, *dS;          // markers
+  double *xi, *xi1, *xi2;      // penalty integrals [dim][max_markers]
+  double *probe_xp, *probe_out;
+  int max_probes;
+};
+
+// Workspace layout: byte offsets of every buffer for a descriptor.
+struct Layout {
+  size_t Q, Q1, Q2, Qp, Wp, L, V, f, X, U, dS, F, xi, xi1, xi2, alpha, status, probe_xp,
+      probe_out, total;
+};
+Layout layout_for(const ibfsa_grid_desc &d);
+void plan_geometry(const ibfsa_grid_desc &d, Plan &p);
+
+// Launchers, one set per arithmetic mode (strict_fp = 1 / 0), defined in the two stage TUs.
+// `stage` < 0 evaluates the right-hand side only (into Lout); otherwise it applies
+// Qo = a Qn + b (Qs + dt L(Qs)) and the same to xi.
+struct StageArgs {
+  const double *Qs;   // stage input, interior
+  const double *Qn;   // step start (stage >= 0)
+  double *Qo;         // stage output (stage >= 0)
+  double *Lout;       // right-hand side output (stage < 0)
+  const double *xis, *xin;
+  double *xio;
+  double a, b, dt;
+  int stage;
+};
+cudaError_t strict_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
+cudaError_t fast_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
+cudaError_t strict_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
+cudaError_t fast_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
+cudaError_t strict_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
+                         cudaStream_t st);
+cudaError_t fast_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
+                       cudaStream_t st);
+
+}  // namespace ibfsa

@@ -1,0 +1,744 @@
+// stage_fp64.cuh -- FP64 kernels of one Runge-Kutta stage of the IB-WENO/TENO method
+// (arXiv:1905.00182, Sec. 2).  Included twice: once with IBFSA_STRICT = 1 and --fmad=false
+// (every operation rounded separately, in the order the formulas are written below, divisions
+// kept, spreading summed in marker order), once with IBFSA_STRICT = 0 (fused multiply-add,
+// reciprocals, atomic spreading).
+//
+// Per stage:  pad (ghosts + primitives + split speeds)  ->  IB interpolation and penalty force
+//   (Eq. 7-8)  ->  convective flux differences x, y, z  ->  viscous fluxes and their divergence
+//   (Eq. 2-5)  ->  IB spreading (Eq. 9)  ->  finish (sponge, IB source, RK combination).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ibfsa_internal.h"
+
+#ifndef IBFSA_STRICT
+#error "define IBFSA_STRICT to 0 or 1"
+#endif
+
+namespace ibfsa {
+namespace IBFSA_MODE_NS {
+
+constexpr bool STRICT = IBFSA_STRICT != 0;
+constexpr int THREADS = 256;
+
+// ------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double divide(double x, double d, double inv_d) {
+  if constexpr (STRICT) return x / d;
+  else return x * inv_d;
+}
+
+// ghost rule of one direction: interior index, or -1 for a free-stream ghost
+__device__ __forceinline__ int map_index(int i, int n, int rlo, int rhi) {
+  if (i < 0) {
+    if (rlo == IBFSA_BC_ZERO_GRAD) return 0;
+    if (rlo == IBFSA_BC_PERIODIC) return n + i;
+    return -1;
+  }
+  if (i >= n) {
+    if (rhi == IBFSA_BC_ZERO_GRAD) return n - 1;
+    if (rhi == IBFSA_BC_PERIODIC) return i - n;
+    return -1;
+  }
+  return i;
+}
+
+__device__ __forceinline__ long long pad_index(const Plan &p, int i, int j, int k) {
+  return ((long long)(k + p.g[2]) * p.P[1] + (j + p.g[1])) * (long long)p.P[0] + (i + p.g[0]);
+}
+
+__device__ __forceinline__ long long int_index(const Plan &p, int i, int j, int k) {
+  return ((long long)k * p.n[1] + j) * (long long)p.n[0] + i;
+}
+
+__device__ __forceinline__ double load_alpha(const Plan &p, int a) {
+  return __longlong_as_double((long long)p.alpha_bits[a]);
+}
+
+// Peskin's four-point kernel, Eq. 11
+__device__ __forceinline__ double peskin(double r) {
+  double a = fabs(r);
+  if (a < 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+  if (a < 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+  return 0.0;
+}
+
+// first of the four support nodes of position x along direction a, and their weights
+__device__ __forceinline__ int support(const Plan &p, int a, double x, double w[4]) {
+  double s = divide(x - p.lo[a], p.h[a], p.inv_h[a]) - 0.5;
+  int j0 = (int)floor(s) - 1;
+#pragma unroll
+  for (int r = 0; r < 4; r++) w[r] = peskin(s - (double)(j0 + r));
+  return j0;
+}
+
+// ------------------------------------------------------------------------------------------
+// fifth-order reconstruction at face i+1/2 from (f_{i-2}, ..., f_{i+2})
+// ------------------------------------------------------------------------------------------
+struct Cands {
+  double q0, q1, q2, b0, b1, b2;
+};
+
+__device__ __forceinline__ Cands candidates(double a, double b, double c, double d, double e) {
+  Cands r;
+  // third-order candidates on {i-2..i}, {i-1..i+1}, {i..i+2}
+  if constexpr (STRICT) {
+    r.q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+    r.q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+    r.q2 = (2.0 * c + 5.0 * d - e) / 6.0;
+  } else {
+    const double s6 = 1.0 / 6.0;
+    r.q0 = (2.0 * a - 7.0 * b + 11.0 * c) * s6;
+    r.q1 = (-b + 5.0 * c + 2.0 * d) * s6;
+    r.q2 = (2.0 * c + 5.0 * d - e) * s6;
+  }
+  // Jiang-Shu smoothness indicators
+  double t;
+  t = a - 2.0 * b + c;       r.b0 = 13.0 / 12.0 * t * t;
+  t = a - 4.0 * b + 3.0 * c; r.b0 += 0.25 * t * t;
+  t = b - 2.0 * c + d;       r.b1 = 13.0 / 12.0 * t * t;
+  t = b - d;                 r.b1 += 0.25 * t * t;
+  t = c - 2.0 * d + e;       r.b2 = 13.0 / 12.0 * t * t;
+  t = 3.0 * c - 4.0 * d + e; r.b2 += 0.25 * t * t;
+  return r;
+}
+
+// WENO5-JS: alpha_k = d_k / (1e-6 + beta_k)^2, omega = alpha / sum alpha, d = (0.1, 0.6, 0.3)
+__device__ __forceinline__ double weno5js(double a, double b, double c, double d, double e) {
+  Cands k = candidates(a, b, c, d, e);
+  const double eps = 1e-6;
+  if constexpr (STRICT) {
+    double al0 = 0.1 / ((eps + k.b0) * (eps + k.b0));
+    double al1 = 0.6 / ((eps + k.b1) * (eps + k.b1));
+    double al2 = 0.3 / ((eps + k.b2) * (eps + k.b2));
+    double s = al0 + al1 + al2;
+    return (al0 / s) * k.q0 + (al1 / s) * k.q1 + (al2 / s) * k.q2;
+  } else {
+    // common denominator: alpha_k proportional to d_k prod_{j != k} (eps + beta_j)^2
+    double s0 = (eps + k.b0) * (eps + k.b0);
+    double s1 = (eps + k.b1) * (eps + k.b1);
+    double s2 = (eps + k.b2) * (eps + k.b2);
+    double al0 = 0.1 * (s1 * s2), al1 = 0.6 * (s0 * s2), al2 = 0.3 * (s0 * s1);
+    return (al0 * k.q0 + al1 * k.q1 + al2 * k.q2) / (al0 + al1 + al2);
+  }
+}
+
+// TENO5: gamma_k = (1 + tau5/(beta_k + 1e-40))^6, tau5 = |beta_0 - beta_2|; stencil k kept when
+// gamma_k / sum gamma >= 1e-5; omega = normalised linear weights of the kept stencils
+__device__ __forceinline__ double teno5(const Plan &p, double a, double b, double c, double d,
+                                        double e) {
+  Cands k = candidates(a, b, c, d, e);
+  const double eps = 1e-40, CT = 1e-5;
+  double tau5 = fabs(k.b0 - k.b2);
+  double g0, g1, g2;
+  int mask;
+  if constexpr (STRICT) {
+    double x, x2;
+    x = 1.0 + tau5 / (k.b0 + eps); x2 = x * x; g0 = x2 * x2 * x2;
+    x = 1.0 + tau5 / (k.b1 + eps); x2 = x * x; g1 = x2 * x2 * x2;
+    x = 1.0 + tau5 / (k.b2 + eps); x2 = x * x; g2 = x2 * x2 * x2;
+    double s = g0 + g1 + g2;
+    mask = ((g0 / s) >= CT ? 1 : 0) | ((g1 / s) >= CT ? 2 : 0) | ((g2 / s) >= CT ? 4 : 0);
+  } else {
+    double e0 = k.b0 + eps, e1 = k.b1 + eps, e2 = k.b2 + eps;
+    double r = tau5 / (e0 * e1 * e2);
+    double x, x2;
+    x = 1.0 + r * (e1 * e2); x2 = x * x; g0 = x2 * x2 * x2;
+    x = 1.0 + r * (e0 * e2); x2 = x * x; g1 = x2 * x2 * x2;
+    x = 1.0 + r * (e0 * e1); x2 = x * x; g2 = x2 * x2 * x2;
+    double th = CT * (g0 + g1 + g2);
+    mask = (g0 >= th ? 1 : 0) | (g1 >= th ? 2 : 0) | (g2 >= th ? 4 : 0);
+  }
+  const double *w = p.teno_w[mask];
+  return w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
+}
+
+template <int SCHEME>
+__device__ __forceinline__ double recon(const Plan &p, double a, double b, double c, double d,
+                                        double e) {
+  if constexpr (SCHEME == IBFSA_TENO5) return teno5(p, a, b, c, d, e);
+  else return weno5js(a, b, c, d, e);
+}
+
+// ------------------------------------------------------------------------------------------
+// pad: ghost fill by index mapping, primitives on the padded grid, split speeds
+// ------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_pad(Plan p, const double *__restrict__ Q) {
+  constexpr int NV = DIM + 2;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double wmax[3] = {0.0, 0.0, 0.0};
+  if (t < p.NP) {
+    int ix = (int)(t % p.P[0]);
+    long long r = t / p.P[0];
+    int iy = (int)(r % p.P[1]);
+    int iz = (int)(r / p.P[1]);
+    int I[3] = {ix - p.g[0], iy - p.g[1], iz - p.g[2]};
+    bool free_ghost = false, interior = true;
+    int S[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      if (a < DIM) {
+        S[a] = map_index(I[a], p.n[a], p.bc[a][0], p.bc[a][1]);
+        if (S[a] < 0) free_ghost = true;
+        if (I[a] < 0 || I[a] >= p.n[a]) interior = false;
+      } else {
+        S[a] = 0;
+      }
+    }
+    double q[NV];
+    if (free_ghost) {
+#pragma unroll
+      for (int c = 0; c < NV; c++) q[c] = p.qinf[c];
+    } else {
+      long long o = int_index(p, S[0], S[1], S[2]);
+#pragma unroll
+      for (int c = 0; c < NV; c++) q[c] = Q[c * p.N + o];
+    }
+#pragma unroll
+    for (int c = 0; c < NV; c++) p.Qp[c * p.NP + t] = q[c];
+    double rho = q[0];
+    double ke = 0.0, u[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      u[a] = q[1 + a] / rho;
+      ke += q[1 + a] * u[a];
+      p.Wp[a * p.NP + t] = u[a];
+    }
+    double pr = p.gm1 * (q[NV - 1] - 0.5 * ke);
+    p.Wp[DIM * p.NP + t] = pr;
+    if (interior) {
+      double c = sqrt(p.gamma * pr / rho);
+#pragma unroll
+      for (int a = 0; a < DIM; a++) wmax[a] = fabs(u[a]) + c;
+    }
+  }
+  // block max of the (non-negative) speeds, then one atomic per block on the ordered bits
+  __shared__ double red[3][THREADS / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) {
+    double v = wmax[a];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[a][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < DIM) {
+    double v = 0.0;
+    for (int w = 0; w < THREADS / 32; w++) v = fmax(v, red[threadIdx.x][w]);
+    if (!(v <= 1e300)) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
+    else atomicMax(&p.alpha_bits[threadIdx.x], (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// convective term along direction A: split fluxes of a tile of lines staged in shared memory,
+// one face per thread per pass, conservative difference into L
+// ------------------------------------------------------------------------------------------
+template <int A>
+struct ConvTile {
+  // A == 0: 4 lines (y/z) of 63 cells; otherwise 32 lines (consecutive x) of 15 cells
+  static constexpr int ROWS = A == 0 ? 4 : 32;
+  static constexpr int SEG = A == 0 ? 63 : 15;
+  static constexpr int LEN = SEG + 6;          // cells staged per line
+  static constexpr int FACES = SEG + 1;        // faces per line
+  static constexpr int PASSES = (ROWS * FACES + THREADS - 1) / THREADS;
+};
+
+template <int DIM, int A>
+__host__ __device__ constexpr size_t conv_smem_bytes() {
+  return sizeof(double) * 2 * (DIM + 2) * ConvTile<A>::ROWS * ConvTile<A>::LEN;
+}
+
+template <int DIM, int A, int SCHEME>
+__global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
+  constexpr int NV = DIM + 2;
+  using T = ConvTile<A>;
+  extern __shared__ double sm[];
+  double *sfp = sm;                              // [NV][ROWS][LEN]
+  double *sfm = sm + NV * T::ROWS * T::LEN;      // [NV][ROWS][LEN]
+  const double alpha = load_alpha(p, A);
+
+  // tile origin
+  int seg0, line0, other;
+  if constexpr (A == 0) {
+    seg0 = blockIdx.x * T::SEG;
+    line0 = blockIdx.y * T::ROWS;   // y of the first line
+    other = blockIdx.z;             // z
+  } else {
+    int nseg = (p.n[A] + T::SEG - 1) / T::SEG;
+    seg0 = (blockIdx.x % nseg) * T::SEG;
+    line0 = (blockIdx.x / nseg) * T::ROWS;  // x of the first line
+    other = blockIdx.y;                     // z for A = 1, y for A = 2
+  }
+  auto cell_of = [&](int row, int l, int I[3]) -> bool {
+    // row-th line of the tile, position l along A (tile-relative, may be negative)
+    if constexpr (A == 0) {
+      int y = line0 + row;
+      if (y >= p.n[1]) return false;
+      I[0] = seg0 + l;
+      I[1] = y;
+      I[2] = other;
+    } else {
+      int x = line0 + row;
+      if (x >= p.n[0]) return false;
+      I[0] = x;
+      I[A] = seg0 + l;
+      I[A == 1 ? 2 : 1] = other;
+    }
+    return true;
+  };
+
+  // 1. split fluxes f+- = (F_A(Q) +- alpha Q)/2 of the staged cells
+  for (int e = threadIdx.x; e < T::ROWS * T::LEN; e += THREADS) {
+    int row, l;
+    if constexpr (A == 0) { row = e / T::LEN; l = e % T::LEN; }
+    else { row = e % T::ROWS; l = e / T::ROWS; }
+    int I[3];
+    bool ok = cell_of(row, l - 3, I);
+    if (ok && I[A] > p.n[A] + 2) ok = false;
+    if (ok) {
+      long long s = pad_index(p, I[0], I[1], I[2]);
+      double ua = p.Wp[A * p.NP + s];
+      double pr = p.Wp[DIM * p.NP + s];
+#pragma unroll
+      for (int c = 0; c < NV; c++) {
+        double q = p.Qp[c * p.NP + s];
+        double F;
+        if (c == 0) F = p.Qp[(1 + A) * p.NP + s];
+        else if (c == NV - 1) F = (q + pr) * ua;
+        else {
+          F = q * ua;
+          if (c - 1 == A) F += pr;
+        }
+        sfp[(c * T::ROWS + row) * T::LEN + l] = 0.5 * (F + alpha * q);
+        sfm[(c * T::ROWS + row) * T::LEN + l] = 0.5 * (F - alpha * q);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NV; c++) {
+        sfp[(c * T::ROWS + row) * T::LEN + l] = 0.0;
+        sfm[(c * T::ROWS + row) * T::LEN + l] = 0.0;
+      }
+    }
+  }
+  __syncthreads();
+
+  // 2. faces m+1/2 for m = seg0-1 .. seg0+SEG-1 (tile-relative face index fi = m - seg0 + 1)
+  double Fh[T::PASSES][NV];
+#pragma unroll
+  for (int ps = 0; ps < T::PASSES; ps++) {
+    int e = threadIdx.x + ps * THREADS;
+    if (e < T::ROWS * T::FACES) {
+      int row, fi;
+      if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
+      else { row = e % T::ROWS; fi = e / T::ROWS; }
+      // staged index of cell m is (m - seg0) + 3 = fi + 2
+      int b = fi + 2;
+#pragma unroll
+      for (int c = 0; c < NV; c++) {
+        const double *fp = sfp + (c * T::ROWS + row) * T::LEN;
+        const double *fm = sfm + (c * T::ROWS + row) * T::LEN;
+        Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
+                    recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+      }
+    }
+  }
+  __syncthreads();
+  double *sh = sm;  // reuse: face fluxes [NV][ROWS][FACES]
+#pragma unroll
+  for (int ps = 0; ps < T::PASSES; ps++) {
+    int e = threadIdx.x + ps * THREADS;
+    if (e < T::ROWS * T::FACES) {
+      int row, fi;
+      if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
+      else { row = e % T::ROWS; fi = e / T::ROWS; }
+#pragma unroll
+      for (int c = 0; c < NV; c++) sh[(c * T::ROWS + row) * T::FACES + fi] = Fh[ps][c];
+    }
+  }
+  __syncthreads();
+
+  // 3. L = L - (Fhat_{m+1/2} - Fhat_{m-1/2}) / h
+  for (int e = threadIdx.x; e < T::ROWS * T::SEG; e += THREADS) {
+    int row, l;
+    if constexpr (A == 0) { row = e / T::SEG; l = e % T::SEG; }
+    else { row = e % T::ROWS; l = e / T::ROWS; }
+    int I[3];
+    if (!cell_of(row, l, I) || I[A] >= p.n[A]) continue;
+    long long o = int_index(p, I[0], I[1], I[2]);
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+      const double *hh = sh + (c * T::ROWS + row) * T::FACES;
+      double d = divide(hh[l + 1] - hh[l], p.h[A], p.inv_h[A]);
+      double prev = first ? 0.0 : p.L[c * p.N + o];
+      p.L[c * p.N + o] = prev - d;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// viscous term (Eq. 2, 5): gradients of u by 4th-order central differences on the box
+// [-2, n+2), tau_ij = du_i/dx_j + du_j/dx_i - 2/3 delta_ij div u, b_j = u_i tau_ij, then
+// (1/Re) sum_a D4_a [0, tau_{.a}, b_a]
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double d4(double fm2, double fm1, double fp1, double fp2, double h12,
+                                     double inv_h12) {
+  return divide(8.0 * (fp1 - fm1) - (fp2 - fm2), h12, inv_h12);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_visc_flux(Plan p) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.NB) return;
+  int bx = (int)(t % p.B[0]);
+  long long r = t / p.B[0];
+  int by = (int)(r % p.B[1]);
+  int bz = (int)(r / p.B[1]);
+  int I[3] = {bx - 2, DIM > 1 ? by - 2 : by, DIM > 2 ? bz - 2 : bz};
+  long long s = pad_index(p, I[0], I[1], I[2]);
+  long long stride[3] = {1, p.P[0], (long long)p.P[0] * p.P[1]};
+  double g[DIM][DIM];
+#pragma unroll
+  for (int ci = 0; ci < DIM; ci++) {
+    const double *u = p.Wp + ci * p.NP + s;
+#pragma unroll
+    for (int dj = 0; dj < DIM; dj++) {
+      long long st = stride[dj];
+      g[ci][dj] = d4(u[-2 * st], u[-st], u[st], u[2 * st], p.h12[dj], p.inv_h12[dj]);
+    }
+  }
+  double div = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) div += g[a][a];
+#pragma unroll
+  for (int a = 0; a < DIM; a++) {
+    double b = 0.0;
+#pragma unroll
+    for (int ci = 0; ci < DIM; ci++) {
+      double tau = g[ci][a] + g[a][ci];
+      if (ci == a) tau -= 2.0 / 3.0 * div;
+      p.V[(long long)(a * (DIM + 1) + ci) * p.NB + t] = tau;
+      b += p.Wp[ci * p.NP + s] * tau;
+    }
+    p.V[(long long)(a * (DIM + 1) + DIM) * p.NB + t] = b;
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_visc_div(Plan p) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.N) return;
+  int i = (int)(t % p.n[0]);
+  long long r = t / p.n[0];
+  int j = (int)(r % p.n[1]);
+  int k = (int)(r / p.n[1]);
+  long long b = ((long long)(DIM > 2 ? k + 2 : k) * p.B[1] + (DIM > 1 ? j + 2 : j)) * p.B[0] + (i + 2);
+  long long stride[3] = {1, p.B[0], (long long)p.B[0] * p.B[1]};
+#pragma unroll
+  for (int fc = 0; fc <= DIM; fc++) {
+    double sum = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      const double *F = p.V + (long long)(a * (DIM + 1) + fc) * p.NB + b;
+      long long st = stride[a];
+      sum += d4(F[-2 * st], F[-st], F[st], F[2 * st], p.h12[a], p.inv_h12[a]);
+    }
+    long long o = (long long)(fc + 1) * p.N + t;
+    p.L[o] = p.L[o] + divide(sum, p.Re, p.inv_Re);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// immersed boundary (Eq. 7-9)
+// ------------------------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ bool marker_support(const Plan &p, const double *X, int nm, int k,
+                                               int j0[3], double w[3][4]) {
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    if (a < DIM) {
+      j0[a] = support(p, a, X[a * nm + k], w[a]);
+      if (j0[a] < 0 || j0[a] + 3 > p.n[a] - 1) ok = false;
+    } else {
+      j0[a] = 0;
+      w[a][0] = 1.0; w[a][1] = 0.0; w[a][2] = 0.0; w[a][3] = 0.0;
+    }
+  }
+  return ok;
+}
+
+// U_ib = sum_j u_j prod lambda (Eq. 8), F = alpha xi + beta (U_ib - U) (Eq. 7), and the RK
+// update of xi (xi' = U_ib - U) when the stage is advanced
+template <int DIM>
+__global__ void k_ib_interp(Plan p, const double *__restrict__ xis, const double *xin,
+                            double *xio, double A, double Bc, double dt, int advance) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int nm = p.nm, M = p.max_markers;
+  if (k >= nm) return;
+  int j0[3];
+  double w[3][4];
+  if (!marker_support<DIM>(p, p.X, M, k, j0, w)) {
+    atomicOr(p.status, IBFSA_STATUS_BOUNDS);
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      p.F[a * M + k] = 0.0;
+      if (advance) xio[a * M + k] = xin[a * M + k];
+    }
+    return;
+  }
+  constexpr int C2 = DIM > 2 ? 4 : 1;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) {
+    const double *u = p.Wp + a * p.NP;
+    double acc = 0.0;
+    for (int r2 = 0; r2 < C2; r2++)
+      for (int r1 = 0; r1 < 4; r1++)
+#pragma unroll
+        for (int r0 = 0; r0 < 4; r0++)
+          acc += u[pad_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2)] *
+                 (w[0][r0] * w[1][r1] * w[2][r2]);
+    double slip = acc - p.U[a * M + k];
+    p.F[a * M + k] = p.alpha_pen * xis[a * M + k] + p.beta_pen * slip;
+    if (advance) xio[a * M + k] = A * xin[a * M + k] + Bc * (xis[a * M + k] + dt * slip);
+  }
+}
+
+// strict spreading: one block walks the markers in order; its threads own the 4^DIM support
+// cells of the current marker (distinct cells), so every cell sums its contributions in marker
+// order: f_j = f_j - F_k w dS_k / prod h  (Eq. 9)
+template <int DIM>
+__global__ void k_spread_ordered(Plan p) {
+  constexpr int C2 = DIM > 2 ? 4 : 1;
+  int r = threadIdx.x;  // 0 .. 4^DIM - 1
+  int r0 = r & 3, r1 = (r >> 2) & 3, r2 = DIM > 2 ? (r >> 4) : 0;
+  int M = p.max_markers;
+  for (int k = 0; k < p.nm; k++) {
+    int j0[3];
+    double w[3][4];
+    bool ok = marker_support<DIM>(p, p.X, M, k, j0, w);
+    if (ok && r < 4 * 4 * C2) {
+      double wt = w[0][r0] * w[1][r1] * w[2][r2];
+      long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
+#pragma unroll
+      for (int a = 0; a < DIM; a++)
+        p.f[a * p.N + o] -= p.F[a * M + k] * wt * p.dS[k] / p.hprod;
+    }
+    __syncthreads();
+  }
+}
+
+// fast spreading: one thread per (marker, support cell), atomics straight into L:
+// momentum += f, energy += f.u
+template <int DIM>
+__global__ void k_spread_atomic(Plan p) {
+  constexpr int S = DIM > 2 ? 64 : 16;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)p.nm * S) return;
+  int k = (int)(t / S), r = (int)(t % S);
+  int r0 = r & 3, r1 = (r >> 2) & 3, r2 = DIM > 2 ? (r >> 4) : 0;
+  int M = p.max_markers;
+  int j0[3];
+  double w[3][4];
+  if (!marker_support<DIM>(p, p.X, M, k, j0, w)) return;
+  double wt = w[0][r0] * w[1][r1] * w[2][r2];
+  long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
+  long long s = pad_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
+  double scale = wt * p.dS[k] / p.hprod;
+  double pw = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) {
+    double fa = -p.F[a * M + k] * scale;
+    atomicAdd(&p.L[(1 + a) * p.N + o], fa);
+    pw += fa * p.Wp[a * p.NP + s];
+  }
+  atomicAdd(&p.L[(DIM + 1) * p.N + o], pw);
+}
+
+// ------------------------------------------------------------------------------------------
+// finish: sponge, strict-mode IB source, then RHS out or RK combination a Qn + b (Qs + dt L)
+// ------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_finish(Plan p, const double *__restrict__ Qs,
+                                                    const double *Qn, double *out, double A,
+                                                    double Bc, double dt, int advance) {
+  constexpr int NV = DIM + 2;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.N) return;
+  int I[3];
+  I[0] = (int)(t % p.n[0]);
+  long long r = t / p.n[0];
+  I[1] = (int)(r % p.n[1]);
+  I[2] = (int)(r / p.n[1]);
+  double Lc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; c++) Lc[c] = p.L[c * p.N + t];
+  if (p.sponge_cells > 0) {
+    int S = p.sponge_cells;
+    int nmin = 1 << 30;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      int e = I[a] < p.n[a] - 1 - I[a] ? I[a] : p.n[a] - 1 - I[a];
+      if (e < nmin) nmin = e;
+    }
+    if (nmin < S) {
+      double rr = (double)(S - nmin) / (double)S;
+      double sig = p.sponge_sigma * rr * rr * rr;
+#pragma unroll
+      for (int c = 0; c < NV; c++) Lc[c] = Lc[c] - sig * (Qs[c * p.N + t] - p.qinf[c]);
+    }
+  }
+  if constexpr (STRICT) {
+    if (p.nm > 0) {
+      long long s = pad_index(p, I[0], I[1], I[2]);
+      double pw = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; a++) {
+        double fa = p.f[a * p.N + t];
+        Lc[1 + a] = Lc[1 + a] + fa;
+        pw += fa * p.Wp[a * p.NP + s];
+      }
+      Lc[NV - 1] = Lc[NV - 1] + pw;
+    }
+  }
+  if (!advance) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) out[c * p.N + t] = Lc[c];
+  } else {
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+      double v = A * Qn[c * p.N + t] + Bc * (Qs[c * p.N + t] + dt * Lc[c]);
+      out[c * p.N + t] = v;
+      bad |= !isfinite(v);
+    }
+    if (bad) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// probes: dp = sum_j p_j prod lambda - p_inf
+// ------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_probe(Plan p, int np, const double *__restrict__ xp, double *__restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  int j0[3];
+  double w[3][4];
+  if (!marker_support<DIM>(p, xp, np, k, j0, w)) {
+    atomicOr(p.status, IBFSA_STATUS_BOUNDS);
+    out[k] = 0.0;
+    return;
+  }
+  constexpr int C2 = DIM > 2 ? 4 : 1;
+  const double *pr = p.Wp + DIM * p.NP;
+  double acc = 0.0;
+  for (int r2 = 0; r2 < C2; r2++)
+    for (int r1 = 0; r1 < 4; r1++)
+#pragma unroll
+      for (int r0 = 0; r0 < 4; r0++)
+        acc += pr[pad_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2)] *
+               (w[0][r0] * w[1][r1] * w[2][r2]);
+  out[k] = acc - p.p_inf;
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side orchestration of one stage
+// ------------------------------------------------------------------------------------------
+inline unsigned blocks_for(long long n, int threads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+template <int DIM, int A, int SCHEME>
+cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
+  using T = ConvTile<A>;
+  constexpr size_t smem = conv_smem_bytes<DIM, A>();
+  cudaError_t e = cudaFuncSetAttribute(k_conv<DIM, A, SCHEME>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid;
+  if (A == 0) {
+    grid = dim3((p.n[0] + T::SEG - 1) / T::SEG, (p.n[1] + T::ROWS - 1) / T::ROWS, p.n[2]);
+  } else {
+    int nseg = (p.n[A] + T::SEG - 1) / T::SEG;
+    int nx = (p.n[0] + T::ROWS - 1) / T::ROWS;
+    grid = dim3(nseg * nx, A == 1 ? p.n[2] : p.n[1]);
+  }
+  k_conv<DIM, A, SCHEME><<<grid, THREADS, smem, st>>>(p, first);
+  return cudaGetLastError();
+}
+
+template <int DIM, int SCHEME>
+cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
+  cudaError_t e;
+  e = cudaMemsetAsync(p.alpha_bits, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_pad<DIM><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, s.Qs);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int advance = s.stage >= 0;
+  if (p.nm > 0) {
+    k_ib_interp<DIM><<<blocks_for(p.nm, 128), 128, 0, st>>>(p, s.xis, s.xin, s.xio, s.a, s.b,
+                                                           s.dt, advance);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = launch_conv<DIM, 0, SCHEME>(p, 1, st)) != cudaSuccess) return e;
+  if ((e = launch_conv<DIM, 1, SCHEME>(p, 0, st)) != cudaSuccess) return e;
+  if constexpr (DIM == 3) {
+    if ((e = launch_conv<DIM, 2, SCHEME>(p, 0, st)) != cudaSuccess) return e;
+  }
+  if (p.Re > 0.0) {
+    k_visc_flux<DIM><<<blocks_for(p.NB, THREADS), THREADS, 0, st>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_visc_div<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (p.nm > 0) {
+    if constexpr (STRICT) {
+      e = cudaMemsetAsync(p.f, 0, sizeof(double) * DIM * p.N, st);
+      if (e != cudaSuccess) return e;
+      k_spread_ordered<DIM><<<1, DIM > 2 ? 64 : 16, 0, st>>>(p);
+    } else {
+      constexpr int S = DIM > 2 ? 64 : 16;
+      k_spread_atomic<DIM><<<blocks_for((long long)p.nm * S, THREADS), THREADS, 0, st>>>(p);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  double *out = advance ? s.Qo : s.Lout;
+  k_finish<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p, s.Qs, s.Qn, out, s.a, s.b, s.dt,
+                                                             advance);
+  return cudaGetLastError();
+}
+
+inline cudaError_t stage_impl(const Plan &p, const StageArgs &s, cudaStream_t st) {
+  if (p.dim == 2)
+    return p.scheme == IBFSA_TENO5 ? run_stage<2, IBFSA_TENO5>(p, s, st)
+                                   : run_stage<2, IBFSA_WENO5JS>(p, s, st);
+  return p.scheme == IBFSA_TENO5 ? run_stage<3, IBFSA_TENO5>(p, s, st)
+                                 : run_stage<3, IBFSA_WENO5JS>(p, s, st);
+}
+
+inline cudaError_t wavespeed_impl(const Plan &p, const double *Q, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(p.alpha_bits, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (p.dim == 2) k_pad<2><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, Q);
+  else k_pad<3><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, Q);
+  return cudaGetLastError();
+}
+
+inline cudaError_t probe_impl(const Plan &p, const double *Q, int np, const double *xp,
+                              double *out, cudaStream_t st) {
+  cudaError_t e = wavespeed_impl(p, Q, st);  // pad + primitives of the current state
+  if (e != cudaSuccess) return e;
+  if (p.dim == 2) k_probe<2><<<blocks_for(np, 128), 128, 0, st>>>(p, np, xp, out);
+  else k_probe<3><<<blocks_for(np, 128), 128, 0, st>>>(p, np, xp, out);
+  return cudaGetLastError();
+}
+
+}  // namespace IBFSA_MODE_NS
+}  // namespace ibfsa

@@ -1,0 +1,290 @@
+"""Thin Python binding of the libibfsa C ABI (include/ibfsa.h).
+
+The functions carry the C names and only marshal arguments: every step of the stage
+right-hand side runs in the CUDA kernels of libibfsa.so.  PyTorch supplies device memory (the
+workspace) and the CUDA stream.  There is no CPU fallback: if the library is missing or no GPU
+is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libibfsa.so")
+
+IBFSA_OK = 0
+IBFSA_ERR_ARG = -1
+IBFSA_ERR_CUDA = -2
+IBFSA_ERR_NONFINITE = -3
+IBFSA_ERR_BOUNDS = -4
+IBFSA_ERR_UNSUPPORTED = -5
+IBFSA_ERR_WORKSPACE = -6
+IBFSA_STATUS_BOUNDS = 1
+IBFSA_STATUS_NONFINITE = 2
+
+# every symbol include/ibfsa.h declares
+EXPORTS = (
+    "ibfsa_workspace_bytes", "ibfsa_create_grid", "ibfsa_destroy_grid", "ibfsa_set_state",
+    "ibfsa_get_state", "ibfsa_set_markers", "ibfsa_get_marker_forces",
+    "ibfsa_get_penalty_integral", "ibfsa_set_penalty_integral", "ibfsa_rhs", "ibfsa_rk3_step",
+    "ibfsa_max_wavespeed", "ibfsa_probe", "ibfsa_get_status", "ibfsa_last_error",
+)
+
+
+class IbfsaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libibfsa error {code}: {msg}")
+        self.code = code
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("gamma", ctypes.c_double),
+        ("Re", ctypes.c_double),
+        ("qinf", ctypes.c_double * 5),
+        ("scheme", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("strict_fp", ctypes.c_int),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("sponge_cells", ctypes.c_int),
+        ("sponge_sigma", ctypes.c_double),
+        ("alpha_pen", ctypes.c_double),
+        ("beta_pen", ctypes.c_double),
+        ("max_markers", ctypes.c_int),
+        ("max_probes", ctypes.c_int),
+    ]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load libibfsa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        D = ctypes.POINTER(GridDesc)
+        L.ibfsa_workspace_bytes.argtypes = [D, ctypes.POINTER(ctypes.c_size_t)]
+        L.ibfsa_create_grid.argtypes = [D, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]
+        L.ibfsa_destroy_grid.argtypes = [_P]
+        L.ibfsa_set_state.argtypes = [_P, _P]
+        L.ibfsa_get_state.argtypes = [_P, _P]
+        L.ibfsa_set_markers.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int]
+        L.ibfsa_get_marker_forces.argtypes = [_P, _P]
+        L.ibfsa_get_penalty_integral.argtypes = [_P, _P]
+        L.ibfsa_set_penalty_integral.argtypes = [_P, _P]
+        L.ibfsa_rhs.argtypes = [_P, _P]
+        L.ibfsa_rk3_step.argtypes = [_P, ctypes.c_double, ctypes.c_int]
+        L.ibfsa_max_wavespeed.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
+        L.ibfsa_probe.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.ibfsa_get_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
+        L.ibfsa_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != IBFSA_OK:
+        raise IbfsaError(rc, lib().ibfsa_last_error().decode())
+
+
+def desc_from_spec(spec: W.GridSpec, strict: bool = False, max_probes: int = 0) -> GridDesc:
+    d = GridDesc()
+    d.dim = spec.dim
+    for a in range(3):
+        d.n[a] = int(spec.n[a])
+        d.lo[a] = float(spec.lo[a])
+        d.hi[a] = float(spec.hi[a])
+        d.bc[a][0] = int(spec.bc[a][0])
+        d.bc[a][1] = int(spec.bc[a][1])
+    d.gamma = float(spec.gamma)
+    d.Re = float(spec.Re)
+    for c in range(5):
+        d.qinf[c] = float(spec.qinf[c])
+    d.scheme = int(spec.scheme)
+    d.precision = int(spec.precision)
+    d.strict_fp = 1 if strict else 0
+    d.sponge_cells = int(spec.sponge_cells)
+    d.sponge_sigma = float(spec.sponge_sigma)
+    d.alpha_pen = float(spec.alpha_pen)
+    d.beta_pen = float(spec.beta_pen)
+    d.max_markers = int(spec.max_markers)
+    d.max_probes = int(max_probes)
+    return d
+
+
+# ---- the C entry points, same names --------------------------------------------------------
+
+def ibfsa_workspace_bytes(desc: GridDesc) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().ibfsa_workspace_bytes(ctypes.byref(desc), ctypes.byref(n)))
+    return n.value
+
+
+def ibfsa_create_grid(desc: GridDesc, workspace_ptr: int, workspace_bytes: int, stream_ptr: int):
+    h = _P()
+    _check(lib().ibfsa_create_grid(ctypes.byref(desc), _P(workspace_ptr), workspace_bytes,
+                                   _P(stream_ptr), ctypes.byref(h)))
+    return h
+
+
+def ibfsa_destroy_grid(g):
+    _check(lib().ibfsa_destroy_grid(g))
+
+
+def ibfsa_set_state(g, ptr: int):
+    _check(lib().ibfsa_set_state(g, _P(ptr)))
+
+
+def ibfsa_get_state(g, ptr: int):
+    _check(lib().ibfsa_get_state(g, _P(ptr)))
+
+
+def ibfsa_set_markers(g, n: int, X: int, U: int, dS: int, reset_integral: int = 1):
+    _check(lib().ibfsa_set_markers(g, n, _P(X), _P(U), _P(dS), reset_integral))
+
+
+def ibfsa_get_marker_forces(g, ptr: int):
+    _check(lib().ibfsa_get_marker_forces(g, _P(ptr)))
+
+
+def ibfsa_get_penalty_integral(g, ptr: int):
+    _check(lib().ibfsa_get_penalty_integral(g, _P(ptr)))
+
+
+def ibfsa_set_penalty_integral(g, ptr: int):
+    _check(lib().ibfsa_set_penalty_integral(g, _P(ptr)))
+
+
+def ibfsa_rhs(g, ptr: int):
+    _check(lib().ibfsa_rhs(g, _P(ptr)))
+
+
+def ibfsa_rk3_step(g, dt: float, nsteps: int = 1):
+    _check(lib().ibfsa_rk3_step(g, float(dt), int(nsteps)))
+
+
+def ibfsa_max_wavespeed(g):
+    out = (ctypes.c_double * 3)()
+    _check(lib().ibfsa_max_wavespeed(g, out))
+    return list(out)
+
+
+def ibfsa_probe(g, np_: int, xp: int, out: int):
+    _check(lib().ibfsa_probe(g, int(np_), _P(xp), _P(out)))
+
+
+def ibfsa_get_status(g) -> int:
+    v = ctypes.c_int(0)
+    _check(lib().ibfsa_get_status(g, ctypes.byref(v)))
+    return v.value
+
+
+# ---- convenience wrapper over torch tensors -------------------------------------------------
+
+def _dev_f64(x, device):
+    import torch
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    return x.to(device=device, dtype=torch.float64).contiguous()
+
+
+class Grid:
+    """A grid with its torch-allocated workspace on the current CUDA device and stream."""
+
+    def __init__(self, spec: W.GridSpec, strict: bool = False, max_probes: int = 0,
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libibfsa needs a CUDA device")
+        self.spec = spec
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.desc = desc_from_spec(spec, strict=strict, max_probes=max_probes)
+        self.ws_bytes = ibfsa_workspace_bytes(self.desc)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self.ws_ptr = (base + 255) & ~255
+        self.h = ibfsa_create_grid(self.desc, self.ws_ptr, self.ws_bytes, self.stream.cuda_stream)
+        self.nm = 0
+        self._state_src = None
+        self._marker_src = None
+
+    def close(self):
+        if self.h is not None:
+            ibfsa_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, Q):
+        t = _dev_f64(Q, self.device)
+        assert tuple(t.shape) == self.spec.shape()
+        ibfsa_set_state(self.h, t.data_ptr())
+        self._state_src = t  # kept alive until the next set_state (the copy is asynchronous)
+
+    def get_state(self):
+        import torch
+        out = torch.empty(self.spec.shape(), dtype=torch.float64, device=self.device)
+        ibfsa_get_state(self.h, out.data_ptr())
+        return out
+
+    def set_markers(self, X, U, dS, reset_integral=True):
+        X = _dev_f64(X, self.device)
+        U = _dev_f64(U, self.device)
+        dS = _dev_f64(dS, self.device)
+        n = X.shape[1]
+        ibfsa_set_markers(self.h, n, X.data_ptr(), U.data_ptr(), dS.data_ptr(),
+                          1 if reset_integral else 0)
+        self.nm = n
+        self._marker_src = (X, U, dS)
+
+    def marker_forces(self):
+        import torch
+        out = torch.empty((self.spec.dim, self.nm), dtype=torch.float64, device=self.device)
+        ibfsa_get_marker_forces(self.h, out.data_ptr())
+        return out
+
+    def penalty_integral(self):
+        import torch
+        out = torch.empty((self.spec.dim, self.nm), dtype=torch.float64, device=self.device)
+        ibfsa_get_penalty_integral(self.h, out.data_ptr())
+        return out
+
+    def rhs(self):
+        import torch
+        out = torch.empty(self.spec.shape(), dtype=torch.float64, device=self.device)
+        ibfsa_rhs(self.h, out.data_ptr())
+        return out
+
+    def rk3_step(self, dt, nsteps=1):
+        ibfsa_rk3_step(self.h, dt, nsteps)
+
+    def max_wavespeed(self):
+        return ibfsa_max_wavespeed(self.h)[: self.spec.dim]
+
+    def probe(self, xp):
+        import torch
+        xp = _dev_f64(xp, self.device)
+        out = torch.empty(xp.shape[1], dtype=torch.float64, device=self.device)
+        ibfsa_probe(self.h, xp.shape[1], xp.data_ptr(), out.data_ptr())
+        return out
+
+    def status(self) -> int:
+        return ibfsa_get_status(self.h)
