@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Throughput of the IB-WENO/TENO stage right-hand side (arXiv:1905.00182, Sec. 2) on one GB300.
+
+Workload: 3D acoustic pulse scattered by a rigid sphere, 512^3 cells on [-8,8]^3 (h = 1/32),
+sphere D = 1 with 20000 Fibonacci markers, Gaussian pulse 1e-3 / half-width 0.2 at (2,0,0),
+gamma 1.4, Re 1e4, TENO5, SSP-RK3 at CFL 0.5.  One step = one SSP-RK3 step = three stage
+right-hand sides (convective + viscous + penalty IB) with their RK combinations.
+
+Metric: cell-stage updates per second (cells x 3 / step time), device-timed with CUDA events on
+the library's stream, inputs resident in HBM (each state copy is 5.4 GB > 129 MB L2, so no L2
+flush is needed).  Printed as one JSON line with the dominant kernel's roofline, the HBM
+fraction of the whole stage, an end-to-end figure through the C ABI with host buffers, the
+FP64 CPU oracle timed on the host cores, and the SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N --steps K --warmup W --n 512 --scheme teno5|weno5js --strict]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+For N > 1 (torchrun) every rank runs an independent replica of the workload (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1905_00182_gb300 import workloads as W  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+SMS = 152
+FP64_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA lanes per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--markers", type=int, default=20000)
+    ap.add_argument("--scheme", default="teno5", choices=["teno5", "weno5js"])
+    ap.add_argument("--strict", action="store_true", help="strict (bit-reproducible) FP64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------------
+def workload_spec(n, markers, scheme):
+    L = 8.0 * n / 512.0
+    spec = W.GridSpec(dim=3, n=(n, n, n), lo=(-L, -L, -L), hi=(L, L, L), gamma=1.4, Re=1e4,
+                      qinf=W.freestream(3, 1.4), scheme=scheme, max_markers=markers)
+    h = spec.h[0]
+    dt = 0.5 / (3.0 / h)  # CFL 0.5 with alpha = c = 1 in every direction at rest
+    spec.alpha_pen, spec.beta_pen = W.penalty_defaults(h, dt)
+    return spec, dt
+
+
+def config_dict(args, n):
+    return {
+        "workload": f"3D acoustic pulse scattered by a rigid sphere, {n}^3 on [-8,8]^3, "
+                    f"{args.scheme.upper()}, {args.markers} markers, Re 1e4, SSP-RK3, "
+                    f"FP64 {'strict' if args.strict else 'fused-multiply-add'}",
+        "grid": [n, n, n], "scheme": args.scheme, "markers": args.markers,
+        "precision": "fp64-strict" if args.strict else "fp64",
+        "step": "one SSP-RK3 step = 3 stage right-hand sides + RK combinations",
+        "l2": "inputs larger than L2 (5.4 GB per state copy at 512^3), no flush",
+    }
+
+
+# ------------------------------------------------------------------------------------------
+# algorithmic work per cell-stage (counted from the formulas; divisions and square roots count
+# as one operation each) -- see the per-kernel breakdown in the design notes
+# ------------------------------------------------------------------------------------------
+def flops_per_cell(scheme, dim=3, viscous=True):
+    """Operations per cell and stage of each kernel class (3D unless dim = 2)."""
+    nv = dim + 2
+    # one reconstruction: candidates 16, smoothness indicators 33, non-linear weights and the
+    # weighted sum (TENO5 29, WENO5-JS 19)
+    recon = 16 + 33 + (29 if scheme == "teno5" else 19)
+    flux = dim + 3                       # physical flux of one direction
+    split = 5 * nv                       # alpha q, F +- alpha q, halves
+    faces = nv * (2 * recon + 1)         # two reconstructions and their sum per component
+    diff = 3 * nv                        # difference, / h, accumulate
+    conv = flux + split + faces + diff
+    pad = dim + (2 * dim - 1) + 3 + 3 + dim
+    visc_flux = (5 * dim * dim + (dim - 1) + dim * (3 * dim + 2)) if viscous else 0
+    visc_div = ((dim + 1) * (5 * dim + (dim - 1) + 2)) if viscous else 0
+    finish = 5 * nv
+    per = {"pad": pad, "conv_x": conv, "conv_y": conv, "conv_z": conv if dim == 3 else 0,
+           "visc_flux": visc_flux, "visc_div": visc_div, "finish": finish}
+    per["total"] = sum(per.values())
+    return per
+
+
+def bytes_per_cell_stage(dim=3):
+    # fused minimum: stage 1 reads Qn and writes Q1; stages 2, 3 read Qn and Qs, write Qo
+    nv = dim + 2
+    return (2 * nv * 8 + 3 * nv * 8 + 3 * nv * 8) / 3.0
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+def ncu_traffic(kernel_class):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1905_00182_gb300", "csrc", "stage_fp64.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = rec.get(kernel_class)
+    if not ent or ent.get("source_sha") != sha:
+        return None
+    return ent.get("bytes_per_launch_full")
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample of the workload
+# ------------------------------------------------------------------------------------------
+def oracle_sample(n_sample, steps, scheme, markers):
+    from oracle import oracle as O
+    L = 8.0 * n_sample / 512.0
+    spec, dt = workload_spec(n_sample, markers, W.TENO5 if scheme == "teno5" else W.WENO5JS)
+    Q = W.gaussian_pulse_state(spec, (min(2.0, 0.6 * L), 0.0, 0.0))
+    X, U, dS = W.fibonacci_sphere(markers, 0.5)
+    t0 = time.perf_counter()
+    O.rk3(spec, Q, dt, steps, X, U, dS)
+    el = time.perf_counter() - t0
+    return spec.cells * 3 * steps / el, el
+
+
+def cpu_baseline(args):
+    n_s = 96
+    v, el = oracle_sample(n_s, 2, args.scheme, args.markers)
+    return {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"same set-up on a {n_s}^3 grid of the same spacing (h = 1/32, "
+                      f"[-1.5,1.5]^3, pulse at (0.9,0,0)), 2 SSP-RK3 steps, single thread, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n_s = 64
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, _ = oracle_sample(n_s, 1, args.scheme, args.markers)
+        if i >= args.warmup:
+            vals.append(v)
+    value = len(vals) / sum(1.0 / v for v in vals)
+    n = args.n
+    out = {"metric": "stage-RHS cell-updates/s", "value": value, "unit": "cell-updates/s",
+           "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_dict(args, n),
+           "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1,
+                            "kind": "oracle",
+                            "sample": f"each step: one SSP-RK3 step of the set-up on a {n_s}^3 "
+                                      f"grid of the same spacing, single thread"},
+           "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1905_00182_gb300 import ibfsa as ib
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    n = args.n
+    scheme = W.TENO5 if args.scheme == "teno5" else W.WENO5JS
+    spec, dt = workload_spec(n, args.markers, scheme)
+    X, U, dS = W.fibonacci_sphere(args.markers, 0.5)
+    probes, _, _ = W.fibonacci_sphere(1000, 6.0 * n / 512.0)
+    g = ib.Grid(spec, strict=args.strict, max_probes=probes.shape[1])
+    g.set_state(W.gaussian_pulse_state_torch(spec, (2.0 * n / 512.0, 0.0, 0.0)))
+    g.set_markers(X, U, dS)
+    stream = g.stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        g.rk3_step(dt, 1)
+    torch.cuda.synchronize()
+    ib.ibfsa_profile_read(g.h)  # reset counters
+    ib.ibfsa_profile_enable(g.h, True)
+    clocks = Clocks(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.rk3_step(dt, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = ib.ibfsa_profile_read(g.h)
+    ib.ibfsa_profile_enable(g.h, False)
+    status = g.status()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = spec.cells * 3 * args.steps * world
+    value = units / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: markers in, step, probes out
+    e2e = None
+    if not args.no_e2e:
+        import ctypes
+        Xh = torch.from_numpy(np.ascontiguousarray(X)).pin_memory()
+        Uh = torch.from_numpy(np.ascontiguousarray(U)).pin_memory()
+        dSh = torch.from_numpy(np.ascontiguousarray(dS)).pin_memory()
+        xph = torch.from_numpy(np.ascontiguousarray(probes)).pin_memory()
+        outh = torch.empty(probes.shape[1], dtype=torch.float64).pin_memory()
+        k_e2e = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ib.ibfsa_set_markers(g.h, X.shape[1], Xh.data_ptr(), Uh.data_ptr(), dSh.data_ptr(), 0)
+            ib.ibfsa_rk3_step(g.h, dt, 1)
+            ib.ibfsa_probe(g.h, probes.shape[1], xph.data_ptr(), outh.data_ptr())  # synchronises
+        el = time.perf_counter() - t0
+        barrier()
+        if dist is not None:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nm = X.shape[1]
+        e2e = {"value": spec.cells * 3 * k_e2e * world / el, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": 8 * (2 * 3 * nm + nm + 3 * probes.shape[1]),
+               "d2h_bytes_per_step": 8 * probes.shape[1], "steps": k_e2e}
+        del ctypes
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = measured_peaks()
+    fl = flops_per_cell(args.scheme)
+    # dominant kernel class by device time inside the timed region
+    classes = {k: v for k, v in prof.items() if v["timed"] > 0}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    avg_ms = classes[dom]["ms"] / classes[dom]["timed"]
+    per_launch_flops = fl.get(dom, 0.0)
+    achieved = per_launch_flops * spec.cells / (avg_ms * 1e-3) / 1e12
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    peak_tf = FP64_FLOP_PER_CLK_PER_SM * SMS * sm_mhz * 1e6 / 1e12
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic,
+                "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x median SM clock of the run",
+                "flops_per_cell": per_launch_flops, "avg_launch_ms": avg_ms}
+    stage_ms = ms / world / (3 * args.steps)
+    bpc = bytes_per_cell_stage()
+    hbm_achieved = bpc * spec.cells / (stage_ms * 1e-3) / 1e9
+    hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+    gpu_launches = sum(v["launches"] for v in prof.values())
+    out = {
+        "metric": "stage-RHS cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(args, n),
+        "roofline": roofline,
+        "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hbm_achieved / hbm_peak, "bytes_per_cell_stage": bpc,
+                         "peak_kind": peak_kind},
+        "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["timed"]},
+        "flops_per_cell_stage": fl["total"],
+        "alu_frac_whole_stage": fl["total"] * spec.cells / (stage_ms * 1e-3) / 1e12 / peak_tf,
+        "clocks": clk, "gpu_launches": gpu_launches, "device_status": status,
+    }
+    if e2e is not None:
+        out["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,17 @@ int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out);
  * Synchronises the grid's stream. */
 int ibfsa_get_status(ibfsa_grid *g, int *host_flags);
 
+/* Instrumentation (not part of the method): launch counts per kernel class are always kept;
+ * with profiling enabled every launch is bracketed by CUDA events on the grid's stream.
+ * Classes, in order: 0 pad (ghosts, primitives, split speeds), 1 IB interpolation and penalty
+ * force, 2-4 convective x/y/z, 5 viscous fluxes, 6 viscous divergence, 7 IB spreading,
+ * 8 finish (sponge, source, RK combination), 9 probes.  ibfsa_profile_read synchronises the
+ * stream, copies up to nclass entries (milliseconds summed over timed launches, launches,
+ * timed launches; any pointer may be NULL) and resets the counters. */
+int ibfsa_profile_enable(ibfsa_grid *g, int enable);
+int ibfsa_profile_read(ibfsa_grid *g, int nclass, double *host_ms, long long *host_launches,
+                       long long *host_timed);
+
 /* Message of the last failing call on this thread. */
 const char *ibfsa_last_error(void);
 

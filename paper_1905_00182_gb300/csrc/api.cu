@@ -152,6 +152,33 @@ Layout layout_for(const ibfsa_grid_desc &d) {
   return L;
 }
 
+void prof_begin(Prof *pr, cudaStream_t st) {
+  if (!pr || !pr->on) return;
+  if (pr->used == Prof::POOL) prof_harvest(pr);
+  cudaEventRecord(pr->ev[2 * pr->used], st);
+}
+
+void prof_end(Prof *pr, int cls, cudaStream_t st) {
+  if (!pr) return;
+  pr->launches[cls]++;
+  if (!pr->on) return;
+  cudaEventRecord(pr->ev[2 * pr->used + 1], st);
+  pr->cls[pr->used++] = cls;
+}
+
+cudaError_t prof_harvest(Prof *pr) {
+  if (!pr || pr->used == 0) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(pr->ev[2 * pr->used - 1]);
+  for (int i = 0; i < pr->used && e == cudaSuccess; i++) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, pr->ev[2 * i], pr->ev[2 * i + 1]);
+    pr->ms[pr->cls[i]] += ms;
+    pr->timed[pr->cls[i]]++;
+  }
+  pr->used = 0;
+  return e;
+}
+
 static cudaError_t run_stage(Grid *G, const StageArgs &s) {
   return G->d.strict_fp ? strict_stage(G->p, s, G->stream) : fast_stage(G->p, s, G->stream);
 }
@@ -233,7 +260,44 @@ int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t wor
 }
 
 int ibfsa_destroy_grid(ibfsa_grid *g) {
+  if (g && g->g.prof.created)
+    for (int i = 0; i < 2 * Prof::POOL; i++) cudaEventDestroy(g->g.prof.ev[i]);
   delete g;
+  return IBFSA_OK;
+}
+
+int ibfsa_profile_enable(ibfsa_grid *g, int enable) {
+  if (!g) return fail(IBFSA_ERR_ARG, "NULL grid");
+  Prof &pr = g->g.prof;
+  if (enable && !pr.created) {
+    for (int i = 0; i < 2 * Prof::POOL; i++) {
+      cudaError_t e = cudaEventCreate(&pr.ev[i]);
+      if (e != cudaSuccess) return cuda_fail(e, "ibfsa_profile_enable");
+    }
+    pr.created = true;
+  }
+  if (!enable) {
+    cudaError_t e = prof_harvest(&pr);
+    if (e != cudaSuccess) return cuda_fail(e, "ibfsa_profile_enable");
+  }
+  pr.on = enable != 0;
+  return IBFSA_OK;
+}
+
+int ibfsa_profile_read(ibfsa_grid *g, int nclass, double *host_ms, long long *host_launches,
+                       long long *host_timed) {
+  if (!g || nclass < 0) return fail(IBFSA_ERR_ARG, "bad argument");
+  Prof &pr = g->g.prof;
+  cudaError_t e = prof_harvest(&pr);
+  if (e != cudaSuccess) return cuda_fail(e, "ibfsa_profile_read");
+  for (int c = 0; c < nclass && c < K_NCLASS; c++) {
+    if (host_ms) host_ms[c] = pr.ms[c];
+    if (host_launches) host_launches[c] = pr.launches[c];
+    if (host_timed) host_timed[c] = pr.timed[c];
+    pr.ms[c] = 0.0;
+    pr.launches[c] = 0;
+    pr.timed[c] = 0;
+  }
   return IBFSA_OK;
 }
 
@@ -327,6 +391,7 @@ int ibfsa_rhs(ibfsa_grid *g, double *L) {
   s.Lout = L;
   s.xis = G.xi;
   s.stage = -1;
+  s.prof = &G.prof;
   cudaError_t e = run_stage(&G, s);
   return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_rhs");
 }
@@ -354,6 +419,7 @@ int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps) {
       a.b = B[s];
       a.dt = dt;
       a.stage = s;
+      a.prof = &G.prof;
       cudaError_t e = run_stage(&G, a);
       if (e != cudaSuccess) return cuda_fail(e, "ibfsa_rk3_step");
     }
@@ -384,8 +450,8 @@ int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out) {
   cudaError_t e = cudaMemcpyAsync(G.probe_xp, xp, sizeof(double) * G.p.dim * np,
                                   cudaMemcpyDefault, G.stream);
   if (e == cudaSuccess)
-    e = G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream)
-                      : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream);
+    e = G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
+                      : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, G.probe_out, sizeof(double) * np, cudaMemcpyDefault, G.stream);
   if (e == cudaSuccess && is_host_pointer(out)) e = cudaStreamSynchronize(G.stream);

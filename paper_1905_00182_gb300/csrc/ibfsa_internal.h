@@ -51,6 +51,29 @@ struct Plan {
   double *F;                  // marker force of Eq. 7 [dim][max_markers]
 };
 
+// Kernel classes for launch counting and CUDA-event timing (instrumentation only).
+enum KClass {
+  K_PAD = 0, K_INTERP, K_CONV_X, K_CONV_Y, K_CONV_Z, K_VISC_FLUX, K_VISC_DIV, K_SPREAD, K_FINISH,
+  K_PROBE, K_NCLASS
+};
+
+// Launch counters (always on) and, when enabled, event pairs around every launch on the grid's
+// stream; harvested (one synchronisation) when the pool fills or when read.
+struct Prof {
+  static constexpr int POOL = 1024;
+  bool on = false;
+  bool created = false;
+  long long launches[K_NCLASS] = {};
+  long long timed[K_NCLASS] = {};
+  double ms[K_NCLASS] = {};
+  cudaEvent_t ev[2 * POOL];
+  int cls[POOL];
+  int used = 0;
+};
+void prof_begin(Prof *pr, cudaStream_t st);
+void prof_end(Prof *pr, int cls, cudaStream_t st);
+cudaError_t prof_harvest(Prof *pr);
+
 struct Grid {
   ibfsa_grid_desc d;
   Plan p;
@@ -62,6 +85,7 @@ struct Grid {
   double *xi, *xi1, *xi2;      // penalty integrals [dim][max_markers]
   double *probe_xp, *probe_out;
   int max_probes;
+  Prof prof;
 };
 
 // Workspace layout: byte offsets of every buffer for a descriptor.
@@ -71,6 +95,7 @@ struct Layout {
 };
 Layout layout_for(const ibfsa_grid_desc &d);
 void plan_geometry(const ibfsa_grid_desc &d, Plan &p);
+
 
 // Launchers, one set per arithmetic mode (strict_fp = 1 / 0), defined in the two stage TUs.
 // `stage` < 0 evaluates the right-hand side only (into Lout); otherwise it applies
@@ -84,14 +109,15 @@ struct StageArgs {
   double *xio;
   double a, b, dt;
   int stage;
+  Prof *prof;
 };
 cudaError_t strict_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
 cudaError_t fast_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
 cudaError_t strict_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t fast_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t strict_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
-                         cudaStream_t st);
+                         cudaStream_t st, Prof *pr);
 cudaError_t fast_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
-                       cudaStream_t st);
+                       cudaStream_t st, Prof *pr);
 
 }  // namespace ibfsa

@@ -677,41 +677,65 @@ cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
 template <int DIM, int SCHEME>
 cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   cudaError_t e;
+  Prof *pr = s.prof;
   e = cudaMemsetAsync(p.alpha_bits, 0, 3 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  prof_begin(pr, st);
   k_pad<DIM><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, s.Qs);
+  prof_end(pr, K_PAD, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int advance = s.stage >= 0;
   if (p.nm > 0) {
+    prof_begin(pr, st);
     k_ib_interp<DIM><<<blocks_for(p.nm, 128), 128, 0, st>>>(p, s.xis, s.xin, s.xio, s.a, s.b,
                                                            s.dt, advance);
+    prof_end(pr, K_INTERP, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if ((e = launch_conv<DIM, 0, SCHEME>(p, 1, st)) != cudaSuccess) return e;
-  if ((e = launch_conv<DIM, 1, SCHEME>(p, 0, st)) != cudaSuccess) return e;
+  prof_begin(pr, st);
+  e = launch_conv<DIM, 0, SCHEME>(p, 1, st);
+  prof_end(pr, K_CONV_X, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(pr, st);
+  e = launch_conv<DIM, 1, SCHEME>(p, 0, st);
+  prof_end(pr, K_CONV_Y, st);
+  if (e != cudaSuccess) return e;
   if constexpr (DIM == 3) {
-    if ((e = launch_conv<DIM, 2, SCHEME>(p, 0, st)) != cudaSuccess) return e;
+    prof_begin(pr, st);
+    e = launch_conv<DIM, 2, SCHEME>(p, 0, st);
+    prof_end(pr, K_CONV_Z, st);
+    if (e != cudaSuccess) return e;
   }
   if (p.Re > 0.0) {
+    prof_begin(pr, st);
     k_visc_flux<DIM><<<blocks_for(p.NB, THREADS), THREADS, 0, st>>>(p);
+    prof_end(pr, K_VISC_FLUX, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    prof_begin(pr, st);
     k_visc_div<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p);
+    prof_end(pr, K_VISC_DIV, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (p.nm > 0) {
     if constexpr (STRICT) {
       e = cudaMemsetAsync(p.f, 0, sizeof(double) * DIM * p.N, st);
       if (e != cudaSuccess) return e;
+      prof_begin(pr, st);
       k_spread_ordered<DIM><<<1, DIM > 2 ? 64 : 16, 0, st>>>(p);
+      prof_end(pr, K_SPREAD, st);
     } else {
       constexpr int S = DIM > 2 ? 64 : 16;
+      prof_begin(pr, st);
       k_spread_atomic<DIM><<<blocks_for((long long)p.nm * S, THREADS), THREADS, 0, st>>>(p);
+      prof_end(pr, K_SPREAD, st);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   double *out = advance ? s.Qo : s.Lout;
+  prof_begin(pr, st);
   k_finish<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p, s.Qs, s.Qn, out, s.a, s.b, s.dt,
                                                              advance);
+  prof_end(pr, K_FINISH, st);
   return cudaGetLastError();
 }
 
@@ -732,11 +756,15 @@ inline cudaError_t wavespeed_impl(const Plan &p, const double *Q, cudaStream_t s
 }
 
 inline cudaError_t probe_impl(const Plan &p, const double *Q, int np, const double *xp,
-                              double *out, cudaStream_t st) {
+                              double *out, cudaStream_t st, Prof *pr) {
+  prof_begin(pr, st);
   cudaError_t e = wavespeed_impl(p, Q, st);  // pad + primitives of the current state
+  prof_end(pr, K_PAD, st);
   if (e != cudaSuccess) return e;
+  prof_begin(pr, st);
   if (p.dim == 2) k_probe<2><<<blocks_for(np, 128), 128, 0, st>>>(p, np, xp, out);
   else k_probe<3><<<blocks_for(np, 128), 128, 0, st>>>(p, np, xp, out);
+  prof_end(pr, K_PROBE, st);
   return cudaGetLastError();
 }
 

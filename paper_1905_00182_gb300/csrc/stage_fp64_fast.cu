@@ -11,7 +11,7 @@ cudaError_t fast_wavespeed(const Plan &p, const double *Q, cudaStream_t st) {
   return fast_ns::wavespeed_impl(p, Q, st);
 }
 cudaError_t fast_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
-                       cudaStream_t st) {
-  return fast_ns::probe_impl(p, Q, np, xp, out, st);
+                        cudaStream_t st, Prof *pr) {
+  return fast_ns::probe_impl(p, Q, np, xp, out, st, pr);
 }
 }  // namespace ibfsa

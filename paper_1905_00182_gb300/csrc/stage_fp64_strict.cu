@@ -12,7 +12,7 @@ cudaError_t strict_wavespeed(const Plan &p, const double *Q, cudaStream_t st) {
   return strict_ns::wavespeed_impl(p, Q, st);
 }
 cudaError_t strict_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
-                         cudaStream_t st) {
-  return strict_ns::probe_impl(p, Q, np, xp, out, st);
+                         cudaStream_t st, Prof *pr) {
+  return strict_ns::probe_impl(p, Q, np, xp, out, st, pr);
 }
 }  // namespace ibfsa

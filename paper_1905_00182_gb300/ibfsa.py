@@ -33,7 +33,11 @@ EXPORTS = (
     "ibfsa_get_state", "ibfsa_set_markers", "ibfsa_get_marker_forces",
     "ibfsa_get_penalty_integral", "ibfsa_set_penalty_integral", "ibfsa_rhs", "ibfsa_rk3_step",
     "ibfsa_max_wavespeed", "ibfsa_probe", "ibfsa_get_status", "ibfsa_last_error",
+    "ibfsa_profile_enable", "ibfsa_profile_read",
 )
+
+KERNEL_CLASSES = ("pad", "ib_interp", "conv_x", "conv_y", "conv_z", "visc_flux", "visc_div",
+                  "ib_spread", "finish", "probe")
 
 
 class IbfsaError(RuntimeError):
@@ -91,6 +95,8 @@ def lib():
         L.ibfsa_probe.argtypes = [_P, ctypes.c_int, _P, _P]
         L.ibfsa_get_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
         L.ibfsa_last_error.restype = ctypes.c_char_p
+        L.ibfsa_profile_enable.argtypes = [_P, ctypes.c_int]
+        L.ibfsa_profile_read.argtypes = [_P, ctypes.c_int, _P, _P, _P]
         _lib = L
     return _lib
 
@@ -190,6 +196,21 @@ def ibfsa_get_status(g) -> int:
     v = ctypes.c_int(0)
     _check(lib().ibfsa_get_status(g, ctypes.byref(v)))
     return v.value
+
+
+def ibfsa_profile_enable(g, enable: bool):
+    _check(lib().ibfsa_profile_enable(g, 1 if enable else 0))
+
+
+def ibfsa_profile_read(g):
+    n = len(KERNEL_CLASSES)
+    ms = (ctypes.c_double * n)()
+    launches = (ctypes.c_longlong * n)()
+    timed = (ctypes.c_longlong * n)()
+    _check(lib().ibfsa_profile_read(g, n, ctypes.cast(ms, _P), ctypes.cast(launches, _P),
+                                    ctypes.cast(timed, _P)))
+    return {k: dict(ms=ms[i], launches=launches[i], timed=timed[i])
+            for i, k in enumerate(KERNEL_CLASSES)}
 
 
 # ---- convenience wrapper over torch tensors -------------------------------------------------

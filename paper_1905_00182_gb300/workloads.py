@@ -274,3 +274,28 @@ def sphere_pulse_3d(n: int = 512, markers: int = 20000, Re: float = 1e4, scheme:
     X, U, dS = fibonacci_sphere(markers, 0.5)
     pr, _, _ = fibonacci_sphere(probes, 6.0 * L / 8.0)
     return dict(spec=spec, Q=Q, X=X, U=U, dS=dS, dt=dt, steps=2000, probes=pr)
+
+
+def gaussian_pulse_state_torch(spec: GridSpec, center, amp: float = 1e-3, halfwidth: float = 0.2,
+                               device="cuda", rho0: float = 1.0, p0: Optional[float] = None):
+    """gaussian_pulse_state generated directly in device memory (same field, fluid at rest),
+    for grids too large to build on the host first."""
+    import torch
+    if p0 is None:
+        p0 = 1.0 / spec.gamma
+    f64 = torch.float64
+    xs = [spec.lo[a] + (torch.arange(spec.n[a], dtype=f64, device=device) + 0.5) * spec.h[a]
+          for a in range(spec.dim)]
+    Q = torch.zeros(spec.shape(), dtype=f64, device=device)
+    Q[0] = rho0
+    if spec.dim == 2:
+        r2 = (xs[0][None, :] - center[0]) ** 2 + (xs[1][:, None] - center[1]) ** 2
+        p = p0 + amp * torch.exp(-math.log(2.0) * r2 / halfwidth ** 2)
+        Q[spec.nv - 1, 0] = p / (spec.gamma - 1.0)
+        return Q
+    for k in range(spec.n[2]):  # plane by plane keeps the temporaries small
+        r2 = ((xs[0][None, :] - center[0]) ** 2 + (xs[1][:, None] - center[1]) ** 2
+              + (xs[2][k] - center[2]) ** 2)
+        p = p0 + amp * torch.exp(-math.log(2.0) * r2 / halfwidth ** 2)
+        Q[spec.nv - 1, k] = p / (spec.gamma - 1.0)
+    return Q
