@@ -156,6 +156,30 @@ int ibfsa_profile_enable(ibfsa_grid *g, int enable);
 int ibfsa_profile_read(ibfsa_grid *g, int nclass, double *host_ms, long long *host_launches,
                        long long *host_timed);
 
+/* Allocation-free right-hand side.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- plug-ins whose host application owns the whole
+ * device-memory budget, latency-critical loops that must not pay the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree, and foreign-language front ends that can only pass
+ * pointers they were given.  It computes what ibfsa_rhs computes for a grid with this
+ * descriptor, state Q [nv][nz][ny][nx], n_markers markers (X, U [dim][n_markers], dS
+ * [n_markers], xi [dim][n_markers]) into L [nv][nz][ny][nx], and the marker forces of Eq. 7
+ * into F [dim][n_markers] when F is not NULL; all pointers are device memory owned by the
+ * caller.  status (device int, may be NULL) receives the IBFSA_STATUS_* bits of this call.
+ * No grid object and no workspace: its scratch (padded state, primitives, viscous fluxes, split
+ * speeds) lives in one static device array of IBFSA_NOALLOC_SCRATCH_BYTES that every GPU loading
+ * this library holds until the process exits.  Grids whose scratch would exceed it are
+ * rejected with IBFSA_ERR_WORKSPACE (about 50^3 cells in 3D with viscosity, 550^2 in 2D).
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a device
+ * looks up the device address of that array (cudaGetSymbolAddress, with the device current)
+ * and caches it; make that first call before any stream capture.  Every call shares the array
+ * and it keeps the previous call's contents (what must start at zero is cleared by each call);
+ * calls whose work overlaps on the GPU -- different streams, or different host threads -- race
+ * on it and must be serialised by the caller.  Asynchronous on cuda_stream. */
+#define IBFSA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int ibfsa_rhs_noalloc(const ibfsa_grid_desc *desc, const double *Q, int n_markers,
+                      const double *X, const double *U, const double *dS, const double *xi,
+                      double *L, double *F, int *status, void *cuda_stream);
+
 /* Message of the last failing call on this thread. */
 const char *ibfsa_last_error(void);
 

@@ -22,6 +22,8 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
+void record_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 static int cuda_fail(cudaError_t e, const char *where) {
   return fail(IBFSA_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }

@@ -94,6 +94,7 @@ struct Layout {
       probe_out, total;
 };
 Layout layout_for(const ibfsa_grid_desc &d);
+void record_error(const char *msg);  // sets the thread-local message of ibfsa_last_error
 void plan_geometry(const ibfsa_grid_desc &d, Plan &p);
 
 

@@ -33,7 +33,7 @@ EXPORTS = (
     "ibfsa_get_state", "ibfsa_set_markers", "ibfsa_get_marker_forces",
     "ibfsa_get_penalty_integral", "ibfsa_set_penalty_integral", "ibfsa_rhs", "ibfsa_rk3_step",
     "ibfsa_max_wavespeed", "ibfsa_probe", "ibfsa_get_status", "ibfsa_last_error",
-    "ibfsa_profile_enable", "ibfsa_profile_read",
+    "ibfsa_profile_enable", "ibfsa_profile_read", "ibfsa_rhs_noalloc",
 )
 
 KERNEL_CLASSES = ("pad", "ib_interp", "conv_x", "conv_y", "conv_z", "visc_flux", "visc_div",
@@ -97,6 +97,7 @@ def lib():
         L.ibfsa_last_error.restype = ctypes.c_char_p
         L.ibfsa_profile_enable.argtypes = [_P, ctypes.c_int]
         L.ibfsa_profile_read.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+        L.ibfsa_rhs_noalloc.argtypes = [D, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]
         _lib = L
     return _lib
 
@@ -211,6 +212,15 @@ def ibfsa_profile_read(g):
                                     ctypes.cast(timed, _P)))
     return {k: dict(ms=ms[i], launches=launches[i], timed=timed[i])
             for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def ibfsa_rhs_noalloc(desc: GridDesc, Q: int, n_markers: int, X: int, U: int, dS: int, xi: int,
+                      L: int, F: int = 0, status: int = 0, stream: int = 0):
+    """Right-hand side without a grid or workspace (device pointers in and out); see the
+    header for who needs it and its scratch limit."""
+    _check(lib().ibfsa_rhs_noalloc(ctypes.byref(desc), _P(Q), int(n_markers), _P(X), _P(U),
+                                   _P(dS), _P(xi), _P(L), _P(F or None), _P(status or None),
+                                   _P(stream)))
 
 
 # ---- convenience wrapper over torch tensors -------------------------------------------------
