@@ -54,8 +54,11 @@ enum {
 
 /* convective schemes (text after Eq. 5) */
 enum { IBFSA_WENO5JS = 0, IBFSA_TENO5 = 1 };
-/* arithmetic of the stage kernels */
-enum { IBFSA_FP64 = 0 };
+/* arithmetic of the stage kernels: FP64 throughout, or the perturbation form -- the stencil
+ * arithmetic (split fluxes, reconstruction, viscous terms, right-hand side) in FP32 on
+ * q' = Q - qinf and on primitive perturbations, expanded so that no O(1) free-stream terms
+ * cancel, while the RK state, its combination, the IB markers and the probes stay FP64 */
+enum { IBFSA_FP64 = 0, IBFSA_FP32_PERTURB = 1 };
 /* boundary rules per face of the box: ghost cells copy the nearest interior cell, hold the
  * free stream, or wrap around */
 enum { IBFSA_BC_ZERO_GRAD = 0, IBFSA_BC_FREESTREAM = 1, IBFSA_BC_PERIODIC = 2 };
@@ -72,7 +75,7 @@ typedef struct {
   double Re;               /* Reynolds number of Eq. 2; Re <= 0 drops the viscous terms */
   double qinf[5];          /* free-stream conservative state (first nv entries used) */
   int scheme;              /* IBFSA_WENO5JS | IBFSA_TENO5 */
-  int precision;           /* IBFSA_FP64 */
+  int precision;           /* IBFSA_FP64 | IBFSA_FP32_PERTURB */
   int strict_fp;           /* 1: every FP64 operation rounded separately (no fused
                               multiply-add), divisions kept as divisions, spreading summed
                               cell by cell in marker order -- the result is reproducible bit

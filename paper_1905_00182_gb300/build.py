@@ -23,6 +23,7 @@ UNITS = {
     "api.cu": [],
     "stage_fp64_strict.cu": ["--fmad=false"],
     "stage_fp64_fast.cu": ["--fmad=true"],
+    "stage_fp32.cu": ["--fmad=true"],
     "noalloc.cu": [],
 }
 

@@ -54,8 +54,10 @@ static int check_desc(const ibfsa_grid_desc *d) {
   if (!(d->qinf[0] > 0.0)) return fail(IBFSA_ERR_ARG, "free-stream density must be positive");
   if (d->scheme != IBFSA_WENO5JS && d->scheme != IBFSA_TENO5)
     return fail(IBFSA_ERR_UNSUPPORTED, "scheme %d is not provided by this build", d->scheme);
-  if (d->precision != IBFSA_FP64)
+  if (d->precision != IBFSA_FP64 && d->precision != IBFSA_FP32_PERTURB)
     return fail(IBFSA_ERR_UNSUPPORTED, "precision %d is not provided by this build", d->precision);
+  if (d->precision == IBFSA_FP32_PERTURB && d->strict_fp)
+    return fail(IBFSA_ERR_UNSUPPORTED, "strict_fp applies to the FP64 arithmetic only");
   if (d->sponge_cells < 0 || d->max_markers < 0 || d->max_probes < 0)
     return fail(IBFSA_ERR_ARG, "negative sponge width or capacity");
   (void)cells;
@@ -116,6 +118,20 @@ void plan_geometry(const ibfsa_grid_desc &d, Plan &p) {
     for (int k = 0; k < 3; k++) p.teno_w[m][k] = sw > 0.0 ? w[k] / sw : 0.0;
   }
   p.max_markers = d.max_markers;
+  for (int m = 0; m < 8; m++)
+    for (int k = 0; k < 3; k++) p.teno_w32[m][k] = (float)p.teno_w[m][k];
+  for (int a = 0; a < 3; a++) {
+    p.inv_h32[a] = (float)p.inv_h[a];
+    p.inv_h12_32[a] = (float)p.inv_h12[a];
+    p.u_inf32[a] = a < d.dim ? (float)p.prim_inf[a] : 0.f;
+    p.m_inf32[a] = a < d.dim ? (float)d.qinf[1 + a] : 0.f;
+  }
+  p.inv_Re32 = (float)p.inv_Re;
+  p.rho_inf32 = (float)d.qinf[0];
+  p.p_inf32 = (float)p.p_inf;
+  p.H_inf32 = (float)(d.qinf[d.dim + 1] + p.p_inf);
+  p.gamma32 = (float)d.gamma;
+  p.gm1_32 = (float)(d.gamma - 1.0);
 }
 
 Layout layout_for(const ibfsa_grid_desc &d) {
@@ -134,10 +150,12 @@ Layout layout_for(const ibfsa_grid_desc &d) {
   L.Q = take(state);
   L.Q1 = take(state);
   L.Q2 = take(state);
-  L.L = take(state);
-  L.Qp = take(sizeof(double) * p.nv * (size_t)p.NP);
-  L.Wp = take(sizeof(double) * (p.dim + 1) * (size_t)p.NP);
-  L.V = d.Re > 0.0 ? take(sizeof(double) * p.dim * (p.dim + 1) * (size_t)p.NB) : take(0);
+  // the FP32 perturbation form keeps the right-hand side and the padded stencil inputs in FP32
+  size_t el = d.precision == IBFSA_FP32_PERTURB ? sizeof(float) : sizeof(double);
+  L.L = take(el * p.nv * (size_t)p.N);
+  L.Qp = take(el * p.nv * (size_t)p.NP);
+  L.Wp = take(el * (p.dim + 1) * (size_t)p.NP);
+  L.V = d.Re > 0.0 ? take(el * p.dim * (p.dim + 1) * (size_t)p.NB) : take(0);
   L.f = (d.strict_fp && d.max_markers > 0) ? take(sizeof(double) * p.dim * (size_t)p.N) : take(0);
   L.X = take(sizeof(double) * p.dim * M);
   L.U = take(sizeof(double) * p.dim * M);
@@ -182,6 +200,7 @@ cudaError_t prof_harvest(Prof *pr) {
 }
 
 static cudaError_t run_stage(Grid *G, const StageArgs &s) {
+  if (G->d.precision == IBFSA_FP32_PERTURB) return fp32_stage(G->p, s, G->stream);
   return G->d.strict_fp ? strict_stage(G->p, s, G->stream) : fast_stage(G->p, s, G->stream);
 }
 
@@ -232,6 +251,10 @@ int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t wor
   G.p.Qp = (double *)(w + L.Qp);
   G.p.Wp = (double *)(w + L.Wp);
   G.p.V = (double *)(w + L.V);
+  G.p.Qp32 = (float *)(w + L.Qp);
+  G.p.Wp32 = (float *)(w + L.Wp);
+  G.p.V32 = (float *)(w + L.V);
+  G.p.L32 = (float *)(w + L.L);
   G.p.f = (double *)(w + L.f);
   G.X = (double *)(w + L.X);
   G.U = (double *)(w + L.U);
@@ -432,8 +455,9 @@ int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps) {
 int ibfsa_max_wavespeed(ibfsa_grid *g, double *host_alpha) {
   if (!g || !host_alpha) return fail(IBFSA_ERR_ARG, "NULL argument");
   Grid &G = g->g;
-  cudaError_t e = G.d.strict_fp ? strict_wavespeed(G.p, G.Q, G.stream)
-                                : fast_wavespeed(G.p, G.Q, G.stream);
+  cudaError_t e = G.d.precision == IBFSA_FP32_PERTURB ? fp32_wavespeed(G.p, G.Q, G.stream)
+                  : G.d.strict_fp                       ? strict_wavespeed(G.p, G.Q, G.stream)
+                                                        : fast_wavespeed(G.p, G.Q, G.stream);
   unsigned long long bits[3] = {0, 0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(bits, G.p.alpha_bits, sizeof(bits), cudaMemcpyDeviceToHost, G.stream);
@@ -452,8 +476,10 @@ int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out) {
   cudaError_t e = cudaMemcpyAsync(G.probe_xp, xp, sizeof(double) * G.p.dim * np,
                                   cudaMemcpyDefault, G.stream);
   if (e == cudaSuccess)
-    e = G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
-                      : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof);
+    e = G.d.precision == IBFSA_FP32_PERTURB
+            ? fp32_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
+        : G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
+                        : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, G.probe_out, sizeof(double) * np, cudaMemcpyDefault, G.stream);
   if (e == cudaSuccess && is_host_pointer(out)) e = cudaStreamSynchronize(G.stream);

@@ -33,6 +33,10 @@ struct Plan {
   double hprod;        // product of h over active directions
   // TENO: 1/sum of kept linear weights per cut-off mask (bit k = stencil k kept)
   double teno_w[8][3];
+  // single-precision copies for the FP32 perturbation form
+  float teno_w32[8][3];
+  float inv_h32[3], inv_h12_32[3], inv_Re32;
+  float rho_inf32, p_inf32, H_inf32, gamma32, gm1_32, u_inf32[3], m_inf32[3];
 
   // device buffers
   double *Qp;          // padded conservative state [nv][NP]
@@ -42,6 +46,9 @@ struct Plan {
   int B[3];            // box extents (n + 4 per active direction)
   long long NB;
   double *f;           // strict mode: spread force [dim][N]
+  // FP32 perturbation form: the same buffers viewed as float (q - q_inf, primitive
+  // perturbations [u', v', w', p'], viscous fluxes, right-hand side)
+  float *Qp32, *Wp32, *V32, *L32;
   unsigned long long *alpha_bits;  // [3] ordered bits of the split speeds
   int *status;
   // markers
@@ -116,6 +123,10 @@ cudaError_t strict_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
 cudaError_t fast_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
 cudaError_t strict_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t fast_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
+cudaError_t fp32_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
+cudaError_t fp32_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
+cudaError_t fp32_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
+                       cudaStream_t st, Prof *pr);
 cudaError_t strict_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
                          cudaStream_t st, Prof *pr);
 cudaError_t fast_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,

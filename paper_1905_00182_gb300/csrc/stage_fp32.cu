@@ -1,0 +1,688 @@
+// stage_fp32.cu -- the perturbation form of one Runge-Kutta stage (arXiv:1905.00182, Sec. 2):
+// the stencil arithmetic in FP32 on q' = Q - q_inf and on primitive perturbations, expanded so
+// that no O(1) free-stream term ever cancels, while the RK state and its combination, the IB
+// markers (Eq. 7-9) and the probes stay FP64.
+//
+// Perturbation algebra (u = u_inf + u', m_inf = rho_inf u_inf, H_inf = E_inf + p_inf):
+//   u'_a = (m'_a - rho' u_inf_a) / rho
+//   p'   = (gamma - 1) (E' - (m' . u + m_inf . u') / 2)
+//   F'_d = [m'_d,  m'_i u_d + m_inf_i u'_d + p' delta_id,  (E' + p') u_d + H_inf u'_d]
+// The split f+-' = (F'_d +- alpha_d q')/2 differs from f+- by a constant, and both candidate
+// polynomials and smoothness indicators are invariant under constant shifts, so the
+// reconstructed flux differences are those of the full fluxes.  Gradients of u equal those of
+// u', and b_j = (u_inf + u')_i tau_ij.
+//
+// TENO5 in FP32: eps = 1e-40 is below the FP32 normal range, so eps = 1e-30 is used, and the
+// cut-off is evaluated on gamma_k / gamma_max = ((1 + r_k)/(1 + r_max))^6 (r = tau5/(beta + eps)),
+// which keeps every quantity in [0, 1] without changing the decision gamma_k >= C_T sum gamma.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ibfsa_internal.h"
+
+namespace ibfsa {
+namespace fp32_ns {
+
+constexpr int THREADS = 256;
+
+struct Free {
+  float rho, p, H, gamma, gm1;
+  float u[3], m[3];
+};
+
+__device__ __forceinline__ Free free_stream(const Plan &p) {
+  Free f;
+  f.rho = p.rho_inf32;
+  f.p = p.p_inf32;
+  f.H = p.H_inf32;
+  f.gamma = p.gamma32;
+  f.gm1 = p.gm1_32;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    f.u[a] = p.u_inf32[a];
+    f.m[a] = p.m_inf32[a];
+  }
+  return f;
+}
+
+__device__ __forceinline__ int map_index(int i, int n, int rlo, int rhi) {
+  if (i < 0) {
+    if (rlo == IBFSA_BC_ZERO_GRAD) return 0;
+    if (rlo == IBFSA_BC_PERIODIC) return n + i;
+    return -1;
+  }
+  if (i >= n) {
+    if (rhi == IBFSA_BC_ZERO_GRAD) return n - 1;
+    if (rhi == IBFSA_BC_PERIODIC) return i - n;
+    return -1;
+  }
+  return i;
+}
+
+__device__ __forceinline__ long long pad_index(const Plan &p, int i, int j, int k) {
+  return ((long long)(k + p.g[2]) * p.P[1] + (j + p.g[1])) * (long long)p.P[0] + (i + p.g[0]);
+}
+
+__device__ __forceinline__ long long int_index(const Plan &p, int i, int j, int k) {
+  return ((long long)k * p.n[1] + j) * (long long)p.n[0] + i;
+}
+
+// Peskin's four-point kernel, Eq. 11 (FP64: the IB and the probes stay in double precision)
+__device__ __forceinline__ double peskin(double r) {
+  double a = fabs(r);
+  if (a < 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) * 0.125;
+  if (a < 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) * 0.125;
+  return 0.0;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool point_support(const Plan &p, const double *X, int stride, int k,
+                                              int j0[3], double w[3][4]) {
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    if (a < DIM) {
+      double s = (X[a * stride + k] - p.lo[a]) * p.inv_h[a] - 0.5;
+      j0[a] = (int)floor(s) - 1;
+#pragma unroll
+      for (int r = 0; r < 4; r++) w[a][r] = peskin(s - (double)(j0[a] + r));
+      if (j0[a] < 0 || j0[a] + 3 > p.n[a] - 1) ok = false;
+    } else {
+      j0[a] = 0;
+      w[a][0] = 1.0; w[a][1] = 0.0; w[a][2] = 0.0; w[a][3] = 0.0;
+    }
+  }
+  return ok;
+}
+
+// ------------------------------------------------------------------------------------------
+// FP32 reconstructions at face i+1/2 from (f_{i-2}, ..., f_{i+2})
+// ------------------------------------------------------------------------------------------
+struct Cands {
+  float q0, q1, q2, b0, b1, b2;
+};
+
+__device__ __forceinline__ Cands candidates(float a, float b, float c, float d, float e) {
+  Cands r;
+  const float s6 = 1.f / 6.f;
+  r.q0 = (2.f * a - 7.f * b + 11.f * c) * s6;
+  r.q1 = (-b + 5.f * c + 2.f * d) * s6;
+  r.q2 = (2.f * c + 5.f * d - e) * s6;
+  const float k13 = 13.f / 12.f;
+  float t, u;
+  t = a - 2.f * b + c; u = a - 4.f * b + 3.f * c; r.b0 = k13 * t * t + 0.25f * u * u;
+  t = b - 2.f * c + d; u = b - d;                 r.b1 = k13 * t * t + 0.25f * u * u;
+  t = c - 2.f * d + e; u = 3.f * c - 4.f * d + e; r.b2 = k13 * t * t + 0.25f * u * u;
+  return r;
+}
+
+__device__ __forceinline__ float weno5js(float a, float b, float c, float d, float e) {
+  Cands k = candidates(a, b, c, d, e);
+  const float eps = 1e-6f;
+  float s0 = (eps + k.b0) * (eps + k.b0);
+  float s1 = (eps + k.b1) * (eps + k.b1);
+  float s2 = (eps + k.b2) * (eps + k.b2);
+  float al0 = 0.1f * (s1 * s2), al1 = 0.6f * (s0 * s2), al2 = 0.3f * (s0 * s1);
+  return __fdividef(al0 * k.q0 + al1 * k.q1 + al2 * k.q2, al0 + al1 + al2);
+}
+
+__device__ __forceinline__ float teno5(const Plan &tw, float a, float b, float c, float d,
+                                       float e) {
+  Cands k = candidates(a, b, c, d, e);
+  const float eps = 1e-30f, CT = 1e-5f;
+  float tau = fabsf(k.b0 - k.b2);
+  float r0 = __fdividef(tau, k.b0 + eps);
+  float r1 = __fdividef(tau, k.b1 + eps);
+  float r2 = __fdividef(tau, k.b2 + eps);
+  float inv = __fdividef(1.f, 1.f + fmaxf(r0, fmaxf(r1, r2)));
+  float t, t2, g0, g1, g2;
+  t = (1.f + r0) * inv; t2 = t * t; g0 = t2 * t2 * t2;
+  t = (1.f + r1) * inv; t2 = t * t; g1 = t2 * t2 * t2;
+  t = (1.f + r2) * inv; t2 = t * t; g2 = t2 * t2 * t2;
+  float th = CT * (g0 + g1 + g2);
+  int mask = (g0 >= th ? 1 : 0) | (g1 >= th ? 2 : 0) | (g2 >= th ? 4 : 0);
+  const float *w = tw.teno_w32[mask];
+  return w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
+}
+
+template <int SCHEME>
+__device__ __forceinline__ float recon(const Plan &tw, float a, float b, float c, float d,
+                                       float e) {
+  if constexpr (SCHEME == IBFSA_TENO5) return teno5(tw, a, b, c, d, e);
+  else return weno5js(a, b, c, d, e);
+}
+
+// ------------------------------------------------------------------------------------------
+// pad: q' = Q - q_inf (subtracted in FP64, then rounded to FP32), primitive perturbations,
+// split speeds of the stage input
+// ------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_pad32(Plan p, const double *__restrict__ Q) {
+  constexpr int NV = DIM + 2;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float wmax[3] = {0.f, 0.f, 0.f};
+  if (t < p.NP) {
+    Free fs = free_stream(p);
+    int ix = (int)(t % p.P[0]);
+    long long r = t / p.P[0];
+    int iy = (int)(r % p.P[1]);
+    int iz = (int)(r / p.P[1]);
+    int I[3] = {ix - p.g[0], iy - p.g[1], iz - p.g[2]};
+    bool free_ghost = false, interior = true;
+    int S[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      if (a < DIM) {
+        S[a] = map_index(I[a], p.n[a], p.bc[a][0], p.bc[a][1]);
+        if (S[a] < 0) free_ghost = true;
+        if (I[a] < 0 || I[a] >= p.n[a]) interior = false;
+      } else {
+        S[a] = 0;
+      }
+    }
+    float q[NV];
+    if (free_ghost) {
+#pragma unroll
+      for (int c = 0; c < NV; c++) q[c] = 0.f;
+    } else {
+      long long o = int_index(p, S[0], S[1], S[2]);
+#pragma unroll
+      for (int c = 0; c < NV; c++) q[c] = (float)(Q[c * p.N + o] - p.qinf[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NV; c++) p.Qp32[c * p.NP + t] = q[c];
+    float rho = fs.rho + q[0];
+    float inv_rho = 1.f / rho;
+    float ke2 = 0.f;  // m'.u + m_inf.u'
+    float u[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      float up = (q[1 + a] - q[0] * fs.u[a]) * inv_rho;
+      u[a] = fs.u[a] + up;
+      ke2 += q[1 + a] * u[a] + fs.m[a] * up;
+      p.Wp32[a * p.NP + t] = up;
+    }
+    float pp = fs.gm1 * (q[NV - 1] - 0.5f * ke2);
+    p.Wp32[DIM * p.NP + t] = pp;
+    if (interior) {
+      float c = sqrtf(fs.gamma * (fs.p + pp) * inv_rho);
+#pragma unroll
+      for (int a = 0; a < DIM; a++) wmax[a] = fabsf(u[a]) + c;
+    }
+  }
+  __shared__ float red[3][THREADS / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) {
+    float v = wmax[a];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[a][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < DIM) {
+    float v = 0.f;
+    for (int w = 0; w < THREADS / 32; w++) v = fmaxf(v, red[threadIdx.x][w]);
+    if (!(v <= 1e30f)) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
+    else atomicMax(&p.alpha_bits[threadIdx.x], (unsigned long long)__double_as_longlong((double)v));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// convective term along A: split flux perturbations of a tile of line segments in shared
+// memory, faces of the tile (only those that exist), conservative difference into L
+// ------------------------------------------------------------------------------------------
+template <int A>
+struct Tile {
+  static constexpr int ROWS = A == 0 ? 4 : 32;
+  static constexpr int SEG = A == 0 ? 63 : 15;
+  static constexpr int LEN = SEG + 6;
+  static constexpr int FACES = SEG + 1;
+};
+
+template <int DIM, int A>
+constexpr size_t conv_smem() {
+  return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN;
+}
+
+template <int DIM, int A, int SCHEME>
+__global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
+  constexpr int NV = DIM + 2;
+  using T = Tile<A>;
+  extern __shared__ float smf[];
+  float *sfp = smf;
+  float *sfm = smf + NV * T::ROWS * T::LEN;
+  const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
+  Free fs = free_stream(p);
+  const Plan &tw = p;
+
+  int seg0, line0, other;
+  if constexpr (A == 0) {
+    seg0 = blockIdx.x * T::SEG;
+    line0 = blockIdx.y * T::ROWS;
+    other = blockIdx.z;
+  } else {
+    int nseg = (p.n[A] + T::SEG - 1) / T::SEG;
+    seg0 = (blockIdx.x % nseg) * T::SEG;
+    line0 = (blockIdx.x / nseg) * T::ROWS;
+    other = blockIdx.y;
+  }
+  const int ncell = min(T::SEG, p.n[A] - seg0);   // cells of this tile along A
+  const int nface = ncell + 1;
+  const int nrow = A == 0 ? min(T::ROWS, p.n[1] - line0) : min(T::ROWS, p.n[0] - line0);
+  auto cell_of = [&](int row, int l, int I[3]) {
+    if constexpr (A == 0) {
+      I[0] = seg0 + l; I[1] = line0 + row; I[2] = other;
+    } else {
+      I[0] = line0 + row; I[A] = seg0 + l; I[A == 1 ? 2 : 1] = other;
+    }
+  };
+
+  // 1. f+-' of the staged cells (seg0-3 .. seg0+ncell+2)
+  const int nlen = ncell + 6;
+  for (int e = threadIdx.x; e < nrow * nlen; e += THREADS) {
+    int row, l;
+    if constexpr (A == 0) { row = e / nlen; l = e % nlen; }
+    else { row = e % nrow; l = e / nrow; }
+    int I[3];
+    cell_of(row, l - 3, I);
+    long long s = pad_index(p, I[0], I[1], I[2]);
+    float up = p.Wp32[A * p.NP + s];
+    float pp = p.Wp32[DIM * p.NP + s];
+    float ua = fs.u[A] + up;
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+      float q = p.Qp32[c * p.NP + s];
+      float F;
+      if (c == 0) F = p.Qp32[(1 + A) * p.NP + s];
+      else if (c == NV - 1) F = (q + pp) * ua + fs.H * up;
+      else {
+        F = q * ua + fs.m[c - 1] * up;
+        if (c - 1 == A) F += pp;
+      }
+      float aq = alpha * q;
+      sfp[(c * T::ROWS + row) * T::LEN + l] = 0.5f * (F + aq);
+      sfm[(c * T::ROWS + row) * T::LEN + l] = 0.5f * (F - aq);
+    }
+  }
+  __syncthreads();
+
+  // 2. faces m+1/2, m = seg0-1 .. seg0+ncell-1 (tile face index fi = m - seg0 + 1)
+  constexpr int MAXP = (T::ROWS * T::FACES + THREADS - 1) / THREADS;
+  float Fh[MAXP][NV];
+  const int nf_total = nrow * nface;
+#pragma unroll
+  for (int ps = 0; ps < MAXP; ps++) {
+    int e = threadIdx.x + ps * THREADS;
+    if (e < nf_total) {
+      int row, fi;
+      if constexpr (A == 0) { row = e / nface; fi = e % nface; }
+      else { row = e % nrow; fi = e / nrow; }
+      int b = fi + 2;
+#pragma unroll
+      for (int c = 0; c < NV; c++) {
+        const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
+        const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
+        Fh[ps][c] = recon<SCHEME>(tw, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
+                    recon<SCHEME>(tw, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+      }
+    }
+  }
+  __syncthreads();
+  float *sh = smf;
+#pragma unroll
+  for (int ps = 0; ps < MAXP; ps++) {
+    int e = threadIdx.x + ps * THREADS;
+    if (e < nf_total) {
+      int row, fi;
+      if constexpr (A == 0) { row = e / nface; fi = e % nface; }
+      else { row = e % nrow; fi = e / nrow; }
+#pragma unroll
+      for (int c = 0; c < NV; c++) sh[(c * T::ROWS + row) * T::FACES + fi] = Fh[ps][c];
+    }
+  }
+  __syncthreads();
+
+  // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / h
+  const float inv_h = p.inv_h32[A];
+  for (int e = threadIdx.x; e < nrow * ncell; e += THREADS) {
+    int row, l;
+    if constexpr (A == 0) { row = e / ncell; l = e % ncell; }
+    else { row = e % nrow; l = e / nrow; }
+    int I[3];
+    cell_of(row, l, I);
+    long long o = int_index(p, I[0], I[1], I[2]);
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+      const float *hh = sh + (c * T::ROWS + row) * T::FACES;
+      float d = (hh[l + 1] - hh[l]) * inv_h;
+      float prev = first ? 0.f : p.L32[c * p.N + o];
+      p.L32[c * p.N + o] = prev - d;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// viscous term on the velocity perturbations
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float d4f(float fm2, float fm1, float fp1, float fp2, float inv_h12) {
+  return (8.f * (fp1 - fm1) - (fp2 - fm2)) * inv_h12;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_visc_flux32(Plan p) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.NB) return;
+  Free fs = free_stream(p);
+  int bx = (int)(t % p.B[0]);
+  long long r = t / p.B[0];
+  int by = (int)(r % p.B[1]);
+  int bz = (int)(r / p.B[1]);
+  int I[3] = {bx - 2, DIM > 1 ? by - 2 : by, DIM > 2 ? bz - 2 : bz};
+  long long s = pad_index(p, I[0], I[1], I[2]);
+  long long stride[3] = {1, p.P[0], (long long)p.P[0] * p.P[1]};
+  float g[DIM][DIM];
+#pragma unroll
+  for (int ci = 0; ci < DIM; ci++) {
+    const float *u = p.Wp32 + ci * p.NP + s;
+#pragma unroll
+    for (int dj = 0; dj < DIM; dj++) {
+      long long st = stride[dj];
+      g[ci][dj] = d4f(u[-2 * st], u[-st], u[st], u[2 * st], p.inv_h12_32[dj]);
+    }
+  }
+  float div = 0.f;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) div += g[a][a];
+#pragma unroll
+  for (int a = 0; a < DIM; a++) {
+    float b = 0.f;
+#pragma unroll
+    for (int ci = 0; ci < DIM; ci++) {
+      float tau = g[ci][a] + g[a][ci];
+      if (ci == a) tau -= (2.f / 3.f) * div;
+      p.V32[(long long)(a * (DIM + 1) + ci) * p.NB + t] = tau;
+      b += (fs.u[ci] + p.Wp32[ci * p.NP + s]) * tau;
+    }
+    p.V32[(long long)(a * (DIM + 1) + DIM) * p.NB + t] = b;
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_visc_div32(Plan p) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.N) return;
+  int i = (int)(t % p.n[0]);
+  long long r = t / p.n[0];
+  int j = (int)(r % p.n[1]);
+  int k = (int)(r / p.n[1]);
+  long long b = ((long long)(DIM > 2 ? k + 2 : k) * p.B[1] + (DIM > 1 ? j + 2 : j)) * p.B[0] + (i + 2);
+  long long stride[3] = {1, p.B[0], (long long)p.B[0] * p.B[1]};
+  const float inv_Re = p.inv_Re32;
+#pragma unroll
+  for (int fc = 0; fc <= DIM; fc++) {
+    float sum = 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      const float *F = p.V32 + (long long)(a * (DIM + 1) + fc) * p.NB + b;
+      long long st = stride[a];
+      sum += d4f(F[-2 * st], F[-st], F[st], F[2 * st], p.inv_h12_32[a]);
+    }
+    long long o = (long long)(fc + 1) * p.N + t;
+    p.L32[o] += sum * inv_Re;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// immersed boundary in FP64 from the FP64 stage state
+// ------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_ib_interp64(Plan p, const double *__restrict__ Qs,
+                              const double *__restrict__ xis, const double *xin, double *xio,
+                              double A, double Bc, double dt, int advance) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int nm = p.nm, M = p.max_markers;
+  if (k >= nm) return;
+  int j0[3];
+  double w[3][4];
+  if (!point_support<DIM>(p, p.X, M, k, j0, w)) {
+    atomicOr(p.status, IBFSA_STATUS_BOUNDS);
+    for (int a = 0; a < DIM; a++) {
+      p.F[a * M + k] = 0.0;
+      if (advance) xio[a * M + k] = xin[a * M + k];
+    }
+    return;
+  }
+  constexpr int C2 = DIM > 2 ? 4 : 1;
+  double acc[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; a++) acc[a] = 0.0;
+  for (int r2 = 0; r2 < C2; r2++)
+    for (int r1 = 0; r1 < 4; r1++)
+      for (int r0 = 0; r0 < 4; r0++) {
+        long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
+        double wt = w[0][r0] * w[1][r1] * w[2][r2];
+        double inv_rho = 1.0 / Qs[o];
+#pragma unroll
+        for (int a = 0; a < DIM; a++) acc[a] += Qs[(1 + a) * p.N + o] * inv_rho * wt;
+      }
+#pragma unroll
+  for (int a = 0; a < DIM; a++) {
+    double slip = acc[a] - p.U[a * M + k];
+    p.F[a * M + k] = p.alpha_pen * xis[a * M + k] + p.beta_pen * slip;
+    if (advance) xio[a * M + k] = A * xin[a * M + k] + Bc * (xis[a * M + k] + dt * slip);
+  }
+}
+
+template <int DIM>
+__global__ void k_spread32(Plan p, const double *__restrict__ Qs) {
+  constexpr int S = DIM > 2 ? 64 : 16;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)p.nm * S) return;
+  int k = (int)(t / S), r = (int)(t % S);
+  int r0 = r & 3, r1 = (r >> 2) & 3, r2 = DIM > 2 ? (r >> 4) : 0;
+  int M = p.max_markers;
+  int j0[3];
+  double w[3][4];
+  if (!point_support<DIM>(p, p.X, M, k, j0, w)) return;
+  double scale = w[0][r0] * w[1][r1] * w[2][r2] * p.dS[k] / p.hprod;
+  long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
+  double inv_rho = 1.0 / Qs[o];
+  double pw = 0.0;
+#pragma unroll
+  for (int a = 0; a < DIM; a++) {
+    double fa = -p.F[a * M + k] * scale;
+    atomicAdd(&p.L32[(1 + a) * p.N + o], (float)fa);
+    pw += fa * Qs[(1 + a) * p.N + o] * inv_rho;
+  }
+  atomicAdd(&p.L32[(DIM + 1) * p.N + o], (float)pw);
+}
+
+// ------------------------------------------------------------------------------------------
+// finish: FP32 right-hand side + FP64 sponge, then RHS out or FP64 RK combination
+// ------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const double *__restrict__ Qs,
+                                                      const double *Qn, double *out, double A,
+                                                      double Bc, double dt, int advance) {
+  constexpr int NV = DIM + 2;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.N) return;
+  double Lc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; c++) Lc[c] = (double)p.L32[c * p.N + t];
+  if (p.sponge_cells > 0) {
+    int I[3];
+    I[0] = (int)(t % p.n[0]);
+    long long r = t / p.n[0];
+    I[1] = (int)(r % p.n[1]);
+    I[2] = (int)(r / p.n[1]);
+    int S = p.sponge_cells, nmin = 1 << 30;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      int e = min(I[a], p.n[a] - 1 - I[a]);
+      nmin = min(nmin, e);
+    }
+    if (nmin < S) {
+      double rr = (double)(S - nmin) / (double)S;
+      double sig = p.sponge_sigma * rr * rr * rr;
+#pragma unroll
+      for (int c = 0; c < NV; c++) Lc[c] -= sig * (Qs[c * p.N + t] - p.qinf[c]);
+    }
+  }
+  if (!advance) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) out[c * p.N + t] = Lc[c];
+  } else {
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+      double v = A * Qn[c * p.N + t] + Bc * (Qs[c * p.N + t] + dt * Lc[c]);
+      out[c * p.N + t] = v;
+      bad |= !isfinite(v);
+    }
+    if (bad) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
+  }
+}
+
+template <int DIM>
+__global__ void k_probe64(Plan p, const double *__restrict__ Q, int np,
+                          const double *__restrict__ xp, double *__restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  int j0[3];
+  double w[3][4];
+  if (!point_support<DIM>(p, xp, np, k, j0, w)) {
+    atomicOr(p.status, IBFSA_STATUS_BOUNDS);
+    out[k] = 0.0;
+    return;
+  }
+  constexpr int C2 = DIM > 2 ? 4 : 1;
+  double acc = 0.0;
+  for (int r2 = 0; r2 < C2; r2++)
+    for (int r1 = 0; r1 < 4; r1++)
+      for (int r0 = 0; r0 < 4; r0++) {
+        long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
+        double rho = Q[o], ke = 0.0;
+        for (int a = 0; a < DIM; a++) {
+          double m = Q[(1 + a) * p.N + o];
+          ke += m * (m / rho);
+        }
+        double pr = p.gm1 * (Q[(DIM + 1) * p.N + o] - 0.5 * ke);
+        acc += pr * (w[0][r0] * w[1][r1] * w[2][r2]);
+      }
+  out[k] = acc - p.p_inf;
+}
+
+// ------------------------------------------------------------------------------------------
+inline unsigned blocks_for(long long n, int threads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+template <int DIM, int A, int SCHEME>
+cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
+  using T = Tile<A>;
+  constexpr size_t smem = conv_smem<DIM, A>();
+  cudaError_t e = cudaFuncSetAttribute(k_conv32<DIM, A, SCHEME>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid;
+  if (A == 0) {
+    grid = dim3((p.n[0] + T::SEG - 1) / T::SEG, (p.n[1] + T::ROWS - 1) / T::ROWS, p.n[2]);
+  } else {
+    int nseg = (p.n[A] + T::SEG - 1) / T::SEG;
+    int nx = (p.n[0] + T::ROWS - 1) / T::ROWS;
+    grid = dim3(nseg * nx, A == 1 ? p.n[2] : p.n[1]);
+  }
+  k_conv32<DIM, A, SCHEME><<<grid, THREADS, smem, st>>>(p, first);
+  return cudaGetLastError();
+}
+
+template <int DIM, int SCHEME>
+cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
+  cudaError_t e;
+  Prof *pr = s.prof;
+  e = cudaMemsetAsync(p.alpha_bits, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  prof_begin(pr, st);
+  k_pad32<DIM><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, s.Qs);
+  prof_end(pr, K_PAD, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int advance = s.stage >= 0;
+  if (p.nm > 0) {
+    prof_begin(pr, st);
+    k_ib_interp64<DIM><<<blocks_for(p.nm, 128), 128, 0, st>>>(p, s.Qs, s.xis, s.xin, s.xio, s.a,
+                                                             s.b, s.dt, advance);
+    prof_end(pr, K_INTERP, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  prof_begin(pr, st);
+  e = launch_conv<DIM, 0, SCHEME>(p, 1, st);
+  prof_end(pr, K_CONV_X, st);
+  if (e != cudaSuccess) return e;
+  prof_begin(pr, st);
+  e = launch_conv<DIM, 1, SCHEME>(p, 0, st);
+  prof_end(pr, K_CONV_Y, st);
+  if (e != cudaSuccess) return e;
+  if constexpr (DIM == 3) {
+    prof_begin(pr, st);
+    e = launch_conv<DIM, 2, SCHEME>(p, 0, st);
+    prof_end(pr, K_CONV_Z, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (p.Re > 0.0) {
+    prof_begin(pr, st);
+    k_visc_flux32<DIM><<<blocks_for(p.NB, THREADS), THREADS, 0, st>>>(p);
+    prof_end(pr, K_VISC_FLUX, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    prof_begin(pr, st);
+    k_visc_div32<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p);
+    prof_end(pr, K_VISC_DIV, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (p.nm > 0) {
+    constexpr int S = DIM > 2 ? 64 : 16;
+    prof_begin(pr, st);
+    k_spread32<DIM><<<blocks_for((long long)p.nm * S, THREADS), THREADS, 0, st>>>(p, s.Qs);
+    prof_end(pr, K_SPREAD, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  double *out = advance ? s.Qo : s.Lout;
+  prof_begin(pr, st);
+  k_finish32<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p, s.Qs, s.Qn, out, s.a, s.b,
+                                                               s.dt, advance);
+  prof_end(pr, K_FINISH, st);
+  return cudaGetLastError();
+}
+
+}  // namespace fp32_ns
+
+cudaError_t fp32_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
+  using namespace fp32_ns;
+  if (p.dim == 2)
+    return p.scheme == IBFSA_TENO5 ? run_stage<2, IBFSA_TENO5>(p, s, st)
+                                   : run_stage<2, IBFSA_WENO5JS>(p, s, st);
+  return p.scheme == IBFSA_TENO5 ? run_stage<3, IBFSA_TENO5>(p, s, st)
+                                 : run_stage<3, IBFSA_WENO5JS>(p, s, st);
+}
+
+cudaError_t fp32_wavespeed(const Plan &p, const double *Q, cudaStream_t st) {
+  using namespace fp32_ns;
+  cudaError_t e = cudaMemsetAsync(p.alpha_bits, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (p.dim == 2) k_pad32<2><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, Q);
+  else k_pad32<3><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, Q);
+  return cudaGetLastError();
+}
+
+cudaError_t fp32_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
+                       cudaStream_t st, Prof *pr) {
+  using namespace fp32_ns;
+  prof_begin(pr, st);
+  if (p.dim == 2) k_probe64<2><<<blocks_for(np, 128), 128, 0, st>>>(p, Q, np, xp, out);
+  else k_probe64<3><<<blocks_for(np, 128), 128, 0, st>>>(p, Q, np, xp, out);
+  prof_end(pr, K_PROBE, st);
+  return cudaGetLastError();
+}
+
+}  // namespace ibfsa
