@@ -36,7 +36,8 @@ from paper_1905_00182_gb300 import workloads as W  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
 SMS = 152
-FP64_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA lanes per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz)
+FP64_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per SM per clock (measured 1.19 TFLOP/s at ~2.0 GHz)
+FP32_FLOP_PER_CLK_PER_SM = 256  # 128 FP32 FMA lanes per SM per clock
 
 
 def parse():
@@ -48,7 +49,11 @@ def parse():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--markers", type=int, default=20000)
     ap.add_argument("--scheme", default="teno5", choices=["teno5", "weno5js"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="fp32: perturbation form (FP64 RK state, markers, probes); fp64: plain")
     ap.add_argument("--strict", action="store_true", help="strict (bit-reproducible) FP64")
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the FP64 comparison run of the fp32 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -68,12 +73,17 @@ def workload_spec(n, markers, scheme):
 
 
 def config_dict(args, n):
+    if getattr(args, "precision", "fp64") == "fp32":
+        form = "FP32 perturbation form (FP64 RK state, markers, probes)"
+        prec = "fp32-perturbation"
+    else:
+        form = f"FP64 {'strict' if args.strict else 'fused-multiply-add'}"
+        prec = "fp64-strict" if args.strict else "fp64"
     return {
         "workload": f"3D acoustic pulse scattered by a rigid sphere, {n}^3 on [-8,8]^3, "
-                    f"{args.scheme.upper()}, {args.markers} markers, Re 1e4, SSP-RK3, "
-                    f"FP64 {'strict' if args.strict else 'fused-multiply-add'}",
+                    f"{args.scheme.upper()}, {args.markers} markers, Re 1e4, SSP-RK3, {form}",
         "grid": [n, n, n], "scheme": args.scheme, "markers": args.markers,
-        "precision": "fp64-strict" if args.strict else "fp64",
+        "precision": prec,
         "step": "one SSP-RK3 step = 3 stage right-hand sides + RK combinations",
         "l2": "inputs larger than L2 (5.4 GB per state copy at 512^3), no flush",
     }
@@ -164,7 +174,7 @@ def measured_peaks():
         return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
 
 
-def ncu_traffic(kernel_class):
+def ncu_traffic(kernel_class, precision):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
     kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -173,9 +183,10 @@ def ncu_traffic(kernel_class):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_1905_00182_gb300", "csrc", "stage_fp64.cuh")
+    name = "stage_fp32.cu" if precision == "fp32" else "stage_fp64.cuh"
+    src = os.path.join(ROOT, "paper_1905_00182_gb300", "csrc", name)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    ent = rec.get(kernel_class)
+    ent = rec.get(f"{precision}:{kernel_class}")
     if not ent or ent.get("source_sha") != sha:
         return None
     return ent.get("bytes_per_launch_full")
@@ -232,6 +243,49 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
+def make_grid(ib, args, precision, strict=False):
+    n = args.n
+    scheme = W.TENO5 if args.scheme == "teno5" else W.WENO5JS
+    spec, dt = workload_spec(n, args.markers, scheme)
+    spec.precision = precision
+    X, U, dS = W.fibonacci_sphere(args.markers, 0.5)
+    probes, _, _ = W.fibonacci_sphere(1000, 6.0 * n / 512.0)
+    g = ib.Grid(spec, strict=strict, max_probes=probes.shape[1])
+    g.set_state(W.gaussian_pulse_state_torch(spec, (2.0 * n / 512.0, 0.0, 0.0)))
+    g.set_markers(X, U, dS)
+    return g, spec, dt, (X, U, dS), probes
+
+
+def timed_steps(ib, g, dt, steps, barrier, profile):
+    """device time (ms) of `steps` SSP-RK3 steps on the grid's stream, and the per-kernel
+    profile of those steps"""
+    import torch
+    if profile:
+        ib.ibfsa_profile_read(g.h)
+        ib.ibfsa_profile_enable(g.h, True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    for _ in range(steps):
+        g.rk3_step(dt, 1)
+    e1.record(g.stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = None
+    if profile:
+        prof = ib.ibfsa_profile_read(g.h)
+        ib.ibfsa_profile_enable(g.h, False)
+    return e0.elapsed_time(e1), prof
+
+
+def pressure(spec, Q):
+    nv = spec.nv
+    ke = sum(Q[1 + a] * Q[1 + a] for a in range(spec.dim)) / Q[0]
+    return (spec.gamma - 1.0) * (Q[nv - 1] - 0.5 * ke)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1905_00182_gb300 import ibfsa as ib
@@ -241,52 +295,37 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    n = args.n
-    scheme = W.TENO5 if args.scheme == "teno5" else W.WENO5JS
-    spec, dt = workload_spec(n, args.markers, scheme)
-    X, U, dS = W.fibonacci_sphere(args.markers, 0.5)
-    probes, _, _ = W.fibonacci_sphere(1000, 6.0 * n / 512.0)
-    g = ib.Grid(spec, strict=args.strict, max_probes=probes.shape[1])
-    g.set_state(W.gaussian_pulse_state_torch(spec, (2.0 * n / 512.0, 0.0, 0.0)))
-    g.set_markers(X, U, dS)
-    stream = g.stream
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    fp32 = args.precision == "fp32"
+    prec = W.FP32_PERTURB if fp32 else W.FP64
+    g, spec, dt, (X, U, dS), probes = make_grid(ib, args, prec, strict=args.strict and not fp32)
     for _ in range(args.warmup):
         g.rk3_step(dt, 1)
     torch.cuda.synchronize()
-    ib.ibfsa_profile_read(g.h)  # reset counters
-    ib.ibfsa_profile_enable(g.h, True)
     clocks = Clocks(local_rank)
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        g.rk3_step(dt, 1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    ms, prof = timed_steps(ib, g, dt, args.steps, barrier, profile=True)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    prof = ib.ibfsa_profile_read(g.h)
-    ib.ibfsa_profile_enable(g.h, False)
     status = g.status()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     units = spec.cells * 3 * args.steps * world
     value = units / (ms * 1e-3)
+    steps_done = args.warmup + args.steps
+    p_head = pressure(spec, g.get_state()) if (fp32 and args.compare) else None
 
-    # end to end through the C ABI with host buffers: markers in, step, probes out
+    # end to end through the C ABI with host buffers: markers in, one step, probes out
     e2e = None
     if not args.no_e2e:
-        import ctypes
         Xh = torch.from_numpy(np.ascontiguousarray(X)).pin_memory()
         Uh = torch.from_numpy(np.ascontiguousarray(U)).pin_memory()
         dSh = torch.from_numpy(np.ascontiguousarray(dS)).pin_memory()
@@ -300,17 +339,38 @@ def run_ours(args, rank, world, local_rank):
             ib.ibfsa_set_markers(g.h, X.shape[1], Xh.data_ptr(), Uh.data_ptr(), dSh.data_ptr(), 0)
             ib.ibfsa_rk3_step(g.h, dt, 1)
             ib.ibfsa_probe(g.h, probes.shape[1], xph.data_ptr(), outh.data_ptr())  # synchronises
-        el = time.perf_counter() - t0
-        barrier()
-        if dist is not None:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0)
         nm = X.shape[1]
         e2e = {"value": spec.cells * 3 * k_e2e * world / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": 8 * (2 * 3 * nm + nm + 3 * probes.shape[1]),
                "d2h_bytes_per_step": 8 * probes.shape[1], "steps": k_e2e}
-        del ctypes
+    gpu_launches = sum(v["launches"] for v in prof.values())
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+
+    # the plain FP64 form on the same workload: its throughput, and the pressure-field error
+    # of the FP32 form after the same number of steps from the same initial state
+    compare = None
+    if fp32 and args.compare:
+        g64, _, _, _, _ = make_grid(ib, args, W.FP64)
+        k64 = 2
+        for _ in range(steps_done - k64):
+            g64.rk3_step(dt, 1)
+        ms64, prof64 = timed_steps(ib, g64, dt, k64, barrier, profile=True)
+        ms64 = max_over_ranks(ms64)
+        p64 = pressure(spec, g64.get_state())
+        pinf = 1.0 / spec.gamma
+        err = float(torch.linalg.vector_norm(p_head - p64) / torch.linalg.vector_norm(p64 - pinf))
+        v64 = spec.cells * 3 * k64 * world / (ms64 * 1e-3)
+        compare = {"fp64_value": v64, "fp64_ms_per_step": ms64 / k64,
+                   "fp32_speedup_vs_fp64": value / v64,
+                   "fp32_vs_fp64_pressure_rel_l2": err, "steps_compared": steps_done,
+                   "fp64_kernel_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items()
+                                               if v["timed"]}}
+        g64.close()
+        del g64, p_head, p64
+        torch.cuda.empty_cache()
 
     if rank != 0:
         if dist is not None:
@@ -319,29 +379,32 @@ def run_ours(args, rank, world, local_rank):
 
     peaks, peak_kind = measured_peaks()
     fl = flops_per_cell(args.scheme)
-    # dominant kernel class by device time inside the timed region
     classes = {k: v for k, v in prof.items() if v["timed"] > 0}
     dom = max(classes, key=lambda k: classes[k]["ms"])
     avg_ms = classes[dom]["ms"] / classes[dom]["timed"]
     per_launch_flops = fl.get(dom, 0.0)
     achieved = per_launch_flops * spec.cells / (avg_ms * 1e-3) / 1e12
     sm_mhz = clk["sm_mhz"] or 2070.0
-    peak_tf = FP64_FLOP_PER_CLK_PER_SM * SMS * sm_mhz * 1e6 / 1e12
-    traffic = ncu_traffic(dom)
+    if fp32:
+        peak_tf = FP32_FLOP_PER_CLK_PER_SM * SMS * sm_mhz * 1e6 / 1e12
+        note = "FP32 pipe: 256 flop/clk/SM (128 FMA lanes) x 152 SMs x median SM clock of the run"
+    else:
+        peak_tf = FP64_FLOP_PER_CLK_PER_SM * SMS * sm_mhz * 1e6 / 1e12
+        note = "FP64 pipe: 4 flop/clk/SM x 152 SMs x median SM clock of the run"
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": traffic,
-                "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x median SM clock of the run",
+                "unit": "TFLOP/s", "frac": achieved / peak_tf,
+                "traffic": ncu_traffic(dom, args.precision), "peak_note": note,
                 "flops_per_cell": per_launch_flops, "avg_launch_ms": avg_ms}
     stage_ms = ms / world / (3 * args.steps)
     bpc = bytes_per_cell_stage()
     hbm_achieved = bpc * spec.cells / (stage_ms * 1e-3) / 1e9
     hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
-    gpu_launches = sum(v["launches"] for v in prof.values())
     out = {
         "metric": "stage-RHS cell-updates/s", "value": value, "unit": "cell-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(args, n),
+        "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
+        "config": config_dict(args, args.n),
         "roofline": roofline,
         "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": hbm_achieved / hbm_peak, "bytes_per_cell_stage": bpc,
@@ -351,6 +414,8 @@ def run_ours(args, rank, world, local_rank):
         "alu_frac_whole_stage": fl["total"] * spec.cells / (stage_ms * 1e-3) / 1e12 / peak_tf,
         "clocks": clk, "gpu_launches": gpu_launches, "device_status": status,
     }
+    if compare is not None:
+        out["forms"] = compare
     if e2e is not None:
         out["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:

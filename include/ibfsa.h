@@ -168,6 +168,7 @@ int ibfsa_profile_read(ibfsa_grid *g, int nclass, double *host_ms, long long *ho
  * [n_markers], xi [dim][n_markers]) into L [nv][nz][ny][nx], and the marker forces of Eq. 7
  * into F [dim][n_markers] when F is not NULL; all pointers are device memory owned by the
  * caller.  status (device int, may be NULL) receives the IBFSA_STATUS_* bits of this call.
+ * The descriptor must ask for IBFSA_FP64 arithmetic (strict or fast).
  * No grid object and no workspace: its scratch (padded state, primitives, viscous fluxes, split
  * speeds) lives in one static device array of IBFSA_NOALLOC_SCRATCH_BYTES that every GPU loading
  * this library holds until the process exits.  Grids whose scratch would exceed it are

@@ -148,8 +148,14 @@ Layout layout_for(const ibfsa_grid_desc &d) {
   size_t M = (size_t)(d.max_markers > 0 ? d.max_markers : 1);
   size_t Pn = (size_t)(d.max_probes > 0 ? d.max_probes : 1);
   L.Q = take(state);
-  L.Q1 = take(state);
-  L.Q2 = take(state);
+  if (d.precision == IBFSA_FP32_PERTURB) {
+    // FP32 form: [qn32 | d1] and d2, FP32 each (the FP64 stage states are not needed)
+    L.Q1 = take(2 * sizeof(float) * p.nv * (size_t)p.N);
+    L.Q2 = take(sizeof(float) * p.nv * (size_t)p.N);
+  } else {
+    L.Q1 = take(state);
+    L.Q2 = take(state);
+  }
   // the FP32 perturbation form keeps the right-hand side and the padded stencil inputs in FP32
   size_t el = d.precision == IBFSA_FP32_PERTURB ? sizeof(float) : sizeof(double);
   L.L = take(el * p.nv * (size_t)p.N);
@@ -200,7 +206,14 @@ cudaError_t prof_harvest(Prof *pr) {
 }
 
 static cudaError_t run_stage(Grid *G, const StageArgs &s) {
-  if (G->d.precision == IBFSA_FP32_PERTURB) return fp32_stage(G->p, s, G->stream);
+  if (G->d.precision == IBFSA_FP32_PERTURB) {
+    if (!G->qn32_valid) {
+      cudaError_t e = fp32_refresh(G->p, G->Q, G->stream);
+      if (e != cudaSuccess) return e;
+      G->qn32_valid = true;
+    }
+    return fp32_stage(G->p, s, G->stream);
+  }
   return G->d.strict_fp ? strict_stage(G->p, s, G->stream) : fast_stage(G->p, s, G->stream);
 }
 
@@ -247,6 +260,10 @@ int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t wor
   G.Q = (double *)(w + L.Q);
   G.Q1 = (double *)(w + L.Q1);
   G.Q2 = (double *)(w + L.Q2);
+  G.p.qn32 = (float *)(w + L.Q1);
+  G.p.d1 = G.p.qn32 + (size_t)G.p.nv * G.p.N;
+  G.p.d2 = (float *)(w + L.Q2);
+  G.qn32_valid = false;
   G.p.L = (double *)(w + L.L);
   G.p.Qp = (double *)(w + L.Qp);
   G.p.Wp = (double *)(w + L.Wp);
@@ -340,6 +357,7 @@ int ibfsa_set_state(ibfsa_grid *g, const double *Q) {
   Grid &G = g->g;
   cudaError_t e = cudaMemcpyAsync(G.Q, Q, sizeof(double) * G.p.nv * G.p.N, cudaMemcpyDefault,
                                   G.stream);
+  G.qn32_valid = false;
   return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_set_state");
 }
 
@@ -413,6 +431,7 @@ int ibfsa_rhs(ibfsa_grid *g, double *L) {
   Grid &G = g->g;
   StageArgs s{};
   s.Qs = G.Q;
+  s.Qn = G.Q;
   s.Lout = L;
   s.xis = G.xi;
   s.stage = -1;

@@ -49,6 +49,9 @@ struct Plan {
   // FP32 perturbation form: the same buffers viewed as float (q - q_inf, primitive
   // perturbations [u', v', w', p'], viscous fluxes, right-hand side)
   float *Qp32, *Wp32, *V32, *L32;
+  // the FP32 form carries the stage values of a step as FP32 increments over the FP64 state:
+  // qn32 = (float)(Qn - q_inf), d1 = Q1 - Qn, d2 = Q2 - Qn
+  float *qn32, *d1, *d2;
   unsigned long long *alpha_bits;  // [3] ordered bits of the split speeds
   int *status;
   // markers
@@ -92,6 +95,7 @@ struct Grid {
   double *xi, *xi1, *xi2;      // penalty integrals [dim][max_markers]
   double *probe_xp, *probe_out;
   int max_probes;
+  bool qn32_valid;  // FP32 form: qn32 matches Qn
   Prof prof;
 };
 
@@ -125,6 +129,7 @@ cudaError_t strict_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t fast_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t fp32_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
 cudaError_t fp32_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
+cudaError_t fp32_refresh(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t fp32_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
                        cudaStream_t st, Prof *pr);
 cudaError_t strict_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,

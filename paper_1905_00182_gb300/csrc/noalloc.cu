@@ -76,6 +76,8 @@ extern "C" int ibfsa_rhs_noalloc(const ibfsa_grid_desc *desc, const double *Q, i
   size_t ws = 0;
   int rc = ibfsa_workspace_bytes(desc, &ws);
   if (rc) return rc;  // ibfsa_last_error() already names the offending field
+  if (desc->precision != IBFSA_FP64)
+    return fail(IBFSA_ERR_UNSUPPORTED, "ibfsa_rhs_noalloc evaluates the FP64 arithmetic only");
   if (n_markers < 0) return fail(IBFSA_ERR_ARG, "negative marker count");
   if (n_markers > 0 && (!X || !U || !dS || !xi))
     return fail(IBFSA_ERR_ARG, "NULL marker array with %d markers", n_markers);

@@ -12,6 +12,12 @@
 // reconstructed flux differences are those of the full fluxes.  Gradients of u equal those of
 // u', and b_j = (u_inf + u')_i tau_ij.
 //
+// Stage values inside a step are FP32 increments over the FP64 state: with a_s + b_s = 1,
+//   Q^(s+1) - Qn = b_s (Q^(s) - Qn + dt L(Q^(s))),
+// so d1 = dt L(Qn), d2 = (d1 + dt L(Q1))/4 and the step ends with Qn += 2/3 (d2 + dt L(Q2)),
+// added in FP64 -- the only FP64 arithmetic of the bulk.  qn32 = (float)(Qn - q_inf) is
+// refreshed from the FP64 state at the end of every step, so stencil inputs never drift.
+//
 // TENO5 in FP32: eps = 1e-40 is below the FP32 normal range, so eps = 1e-30 is used, and the
 // cut-off is evaluated on gamma_k / gamma_max = ((1 + r_k)/(1 + r_max))^6 (r = tau5/(beta + eps)),
 // which keeps every quantity in [0, 1] without changing the decision gamma_k >= C_T sum gamma.
@@ -158,7 +164,7 @@ __device__ __forceinline__ float recon(const Plan &tw, float a, float b, float c
 // split speeds of the stage input
 // ------------------------------------------------------------------------------------------
 template <int DIM>
-__global__ void __launch_bounds__(THREADS) k_pad32(Plan p, const double *__restrict__ Q) {
+__global__ void __launch_bounds__(THREADS) k_pad32(Plan p, const float *__restrict__ din) {
   constexpr int NV = DIM + 2;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float wmax[3] = {0.f, 0.f, 0.f};
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(THREADS) k_pad32(Plan p, const double *__restr
     } else {
       long long o = int_index(p, S[0], S[1], S[2]);
 #pragma unroll
-      for (int c = 0; c < NV; c++) q[c] = (float)(Q[c * p.N + o] - p.qinf[c]);
+      for (int c = 0; c < NV; c++) q[c] = p.qn32[c * p.N + o] + (din ? din[c * p.N + o] : 0.f);
     }
 #pragma unroll
     for (int c = 0; c < NV; c++) p.Qp32[c * p.NP + t] = q[c];
@@ -436,8 +442,15 @@ __global__ void __launch_bounds__(THREADS) k_visc_div32(Plan p) {
 // ------------------------------------------------------------------------------------------
 // immersed boundary in FP64 from the FP64 stage state
 // ------------------------------------------------------------------------------------------
+// FP64 value of component c of the stage state at interior cell o: Qn + increment
+__device__ __forceinline__ double stage_q(const Plan &p, const double *__restrict__ Qn,
+                                          const float *__restrict__ din, int c, long long o) {
+  double v = Qn[c * p.N + o];
+  return din ? v + (double)din[c * p.N + o] : v;
+}
+
 template <int DIM>
-__global__ void k_ib_interp64(Plan p, const double *__restrict__ Qs,
+__global__ void k_ib_interp64(Plan p, const double *__restrict__ Qn, const float *__restrict__ din,
                               const double *__restrict__ xis, const double *xin, double *xio,
                               double A, double Bc, double dt, int advance) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,9 +475,9 @@ __global__ void k_ib_interp64(Plan p, const double *__restrict__ Qs,
       for (int r0 = 0; r0 < 4; r0++) {
         long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
         double wt = w[0][r0] * w[1][r1] * w[2][r2];
-        double inv_rho = 1.0 / Qs[o];
+        double inv_rho = 1.0 / stage_q(p, Qn, din, 0, o);
 #pragma unroll
-        for (int a = 0; a < DIM; a++) acc[a] += Qs[(1 + a) * p.N + o] * inv_rho * wt;
+        for (int a = 0; a < DIM; a++) acc[a] += stage_q(p, Qn, din, 1 + a, o) * inv_rho * wt;
       }
 #pragma unroll
   for (int a = 0; a < DIM; a++) {
@@ -475,7 +488,7 @@ __global__ void k_ib_interp64(Plan p, const double *__restrict__ Qs,
 }
 
 template <int DIM>
-__global__ void k_spread32(Plan p, const double *__restrict__ Qs) {
+__global__ void k_spread32(Plan p, const double *__restrict__ Qn, const float *__restrict__ din) {
   constexpr int S = DIM > 2 ? 64 : 16;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)p.nm * S) return;
@@ -487,30 +500,33 @@ __global__ void k_spread32(Plan p, const double *__restrict__ Qs) {
   if (!point_support<DIM>(p, p.X, M, k, j0, w)) return;
   double scale = w[0][r0] * w[1][r1] * w[2][r2] * p.dS[k] / p.hprod;
   long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
-  double inv_rho = 1.0 / Qs[o];
+  double inv_rho = 1.0 / stage_q(p, Qn, din, 0, o);
   double pw = 0.0;
 #pragma unroll
   for (int a = 0; a < DIM; a++) {
     double fa = -p.F[a * M + k] * scale;
     atomicAdd(&p.L32[(1 + a) * p.N + o], (float)fa);
-    pw += fa * Qs[(1 + a) * p.N + o] * inv_rho;
+    pw += fa * stage_q(p, Qn, din, 1 + a, o) * inv_rho;
   }
   atomicAdd(&p.L32[(DIM + 1) * p.N + o], (float)pw);
 }
 
 // ------------------------------------------------------------------------------------------
-// finish: FP32 right-hand side + FP64 sponge, then RHS out or FP64 RK combination
+// finish: sponge on the FP32 right-hand side, then
+//   mode 0: L out (FP64 copy);  mode 1: dout = b (din + dt L);
+//   mode 2: Qn += b (din + dt L) in FP64 and qn32 = (float)(Qn - q_inf)
 // ------------------------------------------------------------------------------------------
 template <int DIM>
-__global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const double *__restrict__ Qs,
-                                                      const double *Qn, double *out, double A,
-                                                      double Bc, double dt, int advance) {
+__global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__restrict__ din,
+                                                      float *__restrict__ dout, double *Qn,
+                                                      double *__restrict__ Lout, float Bc,
+                                                      float dt, int mode) {
   constexpr int NV = DIM + 2;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.N) return;
-  double Lc[NV];
+  float Lc[NV];
 #pragma unroll
-  for (int c = 0; c < NV; c++) Lc[c] = (double)p.L32[c * p.N + t];
+  for (int c = 0; c < NV; c++) Lc[c] = p.L32[c * p.N + t];
   if (p.sponge_cells > 0) {
     int I[3];
     I[0] = (int)(t % p.n[0]);
@@ -519,30 +535,49 @@ __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const double *__re
     I[2] = (int)(r / p.n[1]);
     int S = p.sponge_cells, nmin = 1 << 30;
 #pragma unroll
-    for (int a = 0; a < DIM; a++) {
-      int e = min(I[a], p.n[a] - 1 - I[a]);
-      nmin = min(nmin, e);
-    }
+    for (int a = 0; a < DIM; a++) nmin = min(nmin, min(I[a], p.n[a] - 1 - I[a]));
     if (nmin < S) {
-      double rr = (double)(S - nmin) / (double)S;
-      double sig = p.sponge_sigma * rr * rr * rr;
+      float rr = (float)(S - nmin) / (float)S;
+      float sig = (float)p.sponge_sigma * rr * rr * rr;
 #pragma unroll
-      for (int c = 0; c < NV; c++) Lc[c] -= sig * (Qs[c * p.N + t] - p.qinf[c]);
+      for (int c = 0; c < NV; c++) {
+        float qp = p.qn32[c * p.N + t] + (din ? din[c * p.N + t] : 0.f);
+        Lc[c] -= sig * qp;
+      }
     }
   }
-  if (!advance) {
+  if (mode == 0) {
 #pragma unroll
-    for (int c = 0; c < NV; c++) out[c * p.N + t] = Lc[c];
+    for (int c = 0; c < NV; c++) Lout[c * p.N + t] = (double)Lc[c];
+    return;
+  }
+  bool bad = false;
+  float inc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; c++) {
+    inc[c] = Bc * ((din ? din[c * p.N + t] : 0.f) + dt * Lc[c]);
+    bad |= !isfinite(inc[c]);
+  }
+  if (mode == 1) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) dout[c * p.N + t] = inc[c];
   } else {
-    bool bad = false;
 #pragma unroll
     for (int c = 0; c < NV; c++) {
-      double v = A * Qn[c * p.N + t] + Bc * (Qs[c * p.N + t] + dt * Lc[c]);
-      out[c * p.N + t] = v;
-      bad |= !isfinite(v);
+      double q = Qn[c * p.N + t] + (double)inc[c];
+      Qn[c * p.N + t] = q;
+      p.qn32[c * p.N + t] = (float)(q - p.qinf[c]);
     }
-    if (bad) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
   }
+  if (bad) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(THREADS) k_refresh32(Plan p, const double *__restrict__ Q) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.N) return;
+#pragma unroll
+  for (int c = 0; c < DIM + 2; c++) p.qn32[c * p.N + t] = (float)(Q[c * p.N + t] - p.qinf[c]);
 }
 
 template <int DIM>
@@ -604,15 +639,19 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   Prof *pr = s.prof;
   e = cudaMemsetAsync(p.alpha_bits, 0, 3 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  // stage increments: none at the step start, d1 after stage 1, d2 after stage 2
+  const float *din = s.stage == 1 ? p.d1 : s.stage == 2 ? p.d2 : nullptr;
+  float *dout = s.stage == 0 ? p.d1 : s.stage == 1 ? p.d2 : nullptr;
+  const double *Qn = s.Qn;
   prof_begin(pr, st);
-  k_pad32<DIM><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, s.Qs);
+  k_pad32<DIM><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, din);
   prof_end(pr, K_PAD, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int advance = s.stage >= 0;
   if (p.nm > 0) {
     prof_begin(pr, st);
-    k_ib_interp64<DIM><<<blocks_for(p.nm, 128), 128, 0, st>>>(p, s.Qs, s.xis, s.xin, s.xio, s.a,
-                                                             s.b, s.dt, advance);
+    k_ib_interp64<DIM><<<blocks_for(p.nm, 128), 128, 0, st>>>(p, Qn, din, s.xis, s.xin, s.xio,
+                                                             s.a, s.b, s.dt, advance);
     prof_end(pr, K_INTERP, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -643,14 +682,14 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   if (p.nm > 0) {
     constexpr int S = DIM > 2 ? 64 : 16;
     prof_begin(pr, st);
-    k_spread32<DIM><<<blocks_for((long long)p.nm * S, THREADS), THREADS, 0, st>>>(p, s.Qs);
+    k_spread32<DIM><<<blocks_for((long long)p.nm * S, THREADS), THREADS, 0, st>>>(p, Qn, din);
     prof_end(pr, K_SPREAD, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  double *out = advance ? s.Qo : s.Lout;
+  int mode = !advance ? 0 : (s.stage < 2 ? 1 : 2);
   prof_begin(pr, st);
-  k_finish32<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p, s.Qs, s.Qn, out, s.a, s.b,
-                                                               s.dt, advance);
+  k_finish32<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(
+      p, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
   prof_end(pr, K_FINISH, st);
   return cudaGetLastError();
 }
@@ -666,12 +705,21 @@ cudaError_t fp32_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
                                  : run_stage<3, IBFSA_WENO5JS>(p, s, st);
 }
 
+cudaError_t fp32_refresh(const Plan &p, const double *Q, cudaStream_t st) {
+  using namespace fp32_ns;
+  if (p.dim == 2) k_refresh32<2><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p, Q);
+  else k_refresh32<3><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p, Q);
+  return cudaGetLastError();
+}
+
 cudaError_t fp32_wavespeed(const Plan &p, const double *Q, cudaStream_t st) {
   using namespace fp32_ns;
-  cudaError_t e = cudaMemsetAsync(p.alpha_bits, 0, 3 * sizeof(unsigned long long), st);
+  cudaError_t e = fp32_refresh(p, Q, st);
   if (e != cudaSuccess) return e;
-  if (p.dim == 2) k_pad32<2><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, Q);
-  else k_pad32<3><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, Q);
+  e = cudaMemsetAsync(p.alpha_bits, 0, 3 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (p.dim == 2) k_pad32<2><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, nullptr);
+  else k_pad32<3><<<blocks_for(p.NP, THREADS), THREADS, 0, st>>>(p, nullptr);
   return cudaGetLastError();
 }
 
