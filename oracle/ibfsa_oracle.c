@@ -509,9 +509,28 @@ static int check_desc(const orc_desc *d) {
 /* L = L_conv + L_visc - sponge + S at state Q (interior [nv][nz][ny][nx]).  F and rate
  * (each [dim][nm], may be NULL) receive the marker force of Eq. 7 and U_ib - U.
  * alpha_out (may be NULL) receives the three split speeds. */
+static int rhs_impl(const orc_desc *d, const double *Q, int nm, const double *X,
+                    const double *U, const double *dS, const double *xi, double *L, double *F,
+                    double *rate, double *alpha_out, const double *alpha_in);
+
 int orc_rhs(const orc_desc *d, const double *Q, int nm, const double *X, const double *U,
             const double *dS, const double *xi, double *L, double *F, double *rate,
             double *alpha_out) {
+  return rhs_impl(d, Q, nm, X, U, dS, xi, L, F, rate, alpha_out, NULL);
+}
+
+/* The same right-hand side with the split speeds given (alpha_in[3]) instead of taken from Q:
+ * the speeds are a maximum over the whole domain, so a crop of a large state reproduces the
+ * right-hand side at its centre only when it is handed the full state's speeds. */
+int orc_rhs_given_alpha(const orc_desc *d, const double *Q, int nm, const double *X,
+                        const double *U, const double *dS, const double *xi, double *L,
+                        const double *alpha_in) {
+  return rhs_impl(d, Q, nm, X, U, dS, xi, L, NULL, NULL, NULL, alpha_in);
+}
+
+static int rhs_impl(const orc_desc *d, const double *Q, int nm, const double *X,
+                    const double *U, const double *dS, const double *xi, double *L, double *F,
+                    double *rate, double *alpha_out, const double *alpha_in) {
   int rc = check_desc(d);
   if (rc) return rc;
   pgrid G;
@@ -526,6 +545,8 @@ int orc_rhs(const orc_desc *d, const double *Q, int nm, const double *X, const d
   primitives(&G, d, W, rho, u, p);
   double alpha[3];
   wavespeeds(&G, d, rho, u, p, alpha);
+  if (alpha_in)
+    for (int a = 0; a < 3; a++) alpha[a] = alpha_in[a];
   if (alpha_out) for (int a = 0; a < 3; a++) alpha_out[a] = alpha[a];
   for (size_t o = 0; o < (size_t)G.nv * Nu; o++) L[o] = 0.0;
   convective(&G, d, W, u, p, alpha, L);

@@ -64,6 +64,8 @@ def lib():
             getattr(_lib, f).argtypes = [_D]
         _lib.orc_rhs.argtypes = [ctypes.POINTER(OrcDesc), _D, ctypes.c_int, _D, _D, _D, _D, _D, _D,
                                  _D, _D]
+        _lib.orc_rhs_given_alpha.argtypes = [ctypes.POINTER(OrcDesc), _D, ctypes.c_int, _D, _D,
+                                             _D, _D, _D, _D]
         _lib.orc_rk3.argtypes = [ctypes.POINTER(OrcDesc), _D, ctypes.c_int, _D, _D, _D, _D,
                                  ctypes.c_double, ctypes.c_int]
         _lib.orc_probe.argtypes = [ctypes.POINTER(OrcDesc), _D, ctypes.c_int, _D, _D]
@@ -145,6 +147,20 @@ def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False):
         raise RuntimeError(f"oracle rhs failed: {rc}")
     if return_markers:
         return L, F[:, :nm], rate[:, :nm], alpha
+    return L
+
+
+def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None):
+    """Right-hand side with the split speeds alpha[3] supplied (for crops of a large state)."""
+    Q = _f64(Q)
+    nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
+    L = np.zeros_like(Q)
+    a = _f64(np.asarray(alpha, dtype=np.float64).reshape(3))
+    d = desc(spec)
+    rc = lib().orc_rhs_given_alpha(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi),
+                                   _p(L), _p(a))
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle rhs failed: {rc}")
     return L
 
 

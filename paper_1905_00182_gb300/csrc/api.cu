@@ -49,7 +49,8 @@ static int check_desc(const ibfsa_grid_desc *d) {
     cells *= d->n[a];
     padded *= d->n[a] + 2 * NG;
   }
-  if (padded * (d->dim + 2) > (1LL << 40)) return fail(IBFSA_ERR_ARG, "grid too large");
+  // offsets inside one component array are 32-bit in the kernels
+  if (padded >= (1LL << 31)) return fail(IBFSA_ERR_ARG, "grid too large (padded cells >= 2^31)");
   if (!(d->gamma > 1.0)) return fail(IBFSA_ERR_ARG, "gamma must exceed 1");
   if (!(d->qinf[0] > 0.0)) return fail(IBFSA_ERR_ARG, "free-stream density must be positive");
   if (d->scheme != IBFSA_WENO5JS && d->scheme != IBFSA_TENO5)

@@ -248,19 +248,21 @@ struct Tile {
 
 template <int DIM, int A>
 constexpr size_t conv_smem() {
-  return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN;
+  return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN;  // >= face-flux area
 }
 
 template <int DIM, int A, int SCHEME>
 __global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
   constexpr int NV = DIM + 2;
   using T = Tile<A>;
+  // face fluxes are stored with an odd row stride when a warp walks the rows (A != 0), so the
+  // 32 lanes hit 32 different banks
+  constexpr int FST = A == 0 ? T::FACES : T::FACES + 1;
   extern __shared__ float smf[];
   float *sfp = smf;
   float *sfm = smf + NV * T::ROWS * T::LEN;
   const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
   Free fs = free_stream(p);
-  const Plan &tw = p;
 
   int seg0, line0, other;
   if constexpr (A == 0) {
@@ -276,31 +278,43 @@ __global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
   const int ncell = min(T::SEG, p.n[A] - seg0);   // cells of this tile along A
   const int nface = ncell + 1;
   const int nrow = A == 0 ? min(T::ROWS, p.n[1] - line0) : min(T::ROWS, p.n[0] - line0);
-  auto cell_of = [&](int row, int l, int I[3]) {
-    if constexpr (A == 0) {
-      I[0] = seg0 + l; I[1] = line0 + row; I[2] = other;
-    } else {
-      I[0] = line0 + row; I[A] = seg0 + l; I[A == 1 ? 2 : 1] = other;
-    }
-  };
+  // 32-bit offsets inside one component array: padded cell (row, l) and interior cell (row, l)
+  const int PX = p.P[0], PXY = p.P[0] * p.P[1];
+  const int NX = p.n[0], NXY = p.n[0] * p.n[1];
+  int pbase, prs, pas, ibase, irs, ias;
+  if constexpr (A == 0) {
+    pbase = (other + p.g[2]) * PXY + (line0 + p.g[1]) * PX + (seg0 + p.g[0]);
+    prs = PX; pas = 1;
+    ibase = other * NXY + line0 * NX + seg0;
+    irs = NX; ias = 1;
+  } else {
+    int y = A == 1 ? seg0 : other, z = A == 1 ? other : seg0;
+    pbase = (z + p.g[2]) * PXY + (y + p.g[1]) * PX + (line0 + p.g[0]);
+    prs = 1; pas = A == 1 ? PX : PXY;
+    ibase = z * NXY + y * NX + line0;
+    irs = 1; ias = A == 1 ? NX : NXY;
+  }
+  const float *Qc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; c++) Qc[c] = p.Qp32 + (size_t)c * p.NP;
+  const float *Wa = p.Wp32 + (size_t)A * p.NP;
+  const float *Wpr = p.Wp32 + (size_t)DIM * p.NP;
 
   // 1. f+-' of the staged cells (seg0-3 .. seg0+ncell+2)
-  const int nlen = ncell + 6;
-  for (int e = threadIdx.x; e < nrow * nlen; e += THREADS) {
+  for (int e = threadIdx.x; e < T::ROWS * T::LEN; e += THREADS) {
     int row, l;
-    if constexpr (A == 0) { row = e / nlen; l = e % nlen; }
-    else { row = e % nrow; l = e / nrow; }
-    int I[3];
-    cell_of(row, l - 3, I);
-    long long s = pad_index(p, I[0], I[1], I[2]);
-    float up = p.Wp32[A * p.NP + s];
-    float pp = p.Wp32[DIM * p.NP + s];
+    if constexpr (A == 0) { row = e / T::LEN; l = e - row * T::LEN; }
+    else { row = e % T::ROWS; l = e / T::ROWS; }
+    if (row >= nrow || l >= ncell + 6) continue;
+    int s = pbase + row * prs + (l - 3) * pas;
+    float up = Wa[s];
+    float pp = Wpr[s];
     float ua = fs.u[A] + up;
 #pragma unroll
     for (int c = 0; c < NV; c++) {
-      float q = p.Qp32[c * p.NP + s];
+      float q = Qc[c][s];
       float F;
-      if (c == 0) F = p.Qp32[(1 + A) * p.NP + s];
+      if (c == 0) F = Qc[1 + A][s];
       else if (c == NV - 1) F = (q + pp) * ua + fs.H * up;
       else {
         F = q * ua + fs.m[c - 1] * up;
@@ -316,21 +330,20 @@ __global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
   // 2. faces m+1/2, m = seg0-1 .. seg0+ncell-1 (tile face index fi = m - seg0 + 1)
   constexpr int MAXP = (T::ROWS * T::FACES + THREADS - 1) / THREADS;
   float Fh[MAXP][NV];
-  const int nf_total = nrow * nface;
 #pragma unroll
   for (int ps = 0; ps < MAXP; ps++) {
     int e = threadIdx.x + ps * THREADS;
-    if (e < nf_total) {
-      int row, fi;
-      if constexpr (A == 0) { row = e / nface; fi = e % nface; }
-      else { row = e % nrow; fi = e / nrow; }
+    int row, fi;
+    if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
+    else { row = e % T::ROWS; fi = e / T::ROWS; }
+    if (e < T::ROWS * T::FACES && row < nrow && fi < nface) {
       int b = fi + 2;
 #pragma unroll
       for (int c = 0; c < NV; c++) {
         const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
         const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
-        Fh[ps][c] = recon<SCHEME>(tw, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
-                    recon<SCHEME>(tw, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+        Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
+                    recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
       }
     }
   }
@@ -339,31 +352,30 @@ __global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
 #pragma unroll
   for (int ps = 0; ps < MAXP; ps++) {
     int e = threadIdx.x + ps * THREADS;
-    if (e < nf_total) {
-      int row, fi;
-      if constexpr (A == 0) { row = e / nface; fi = e % nface; }
-      else { row = e % nrow; fi = e / nrow; }
+    int row, fi;
+    if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
+    else { row = e % T::ROWS; fi = e / T::ROWS; }
+    if (e < T::ROWS * T::FACES && row < nrow && fi < nface) {
 #pragma unroll
-      for (int c = 0; c < NV; c++) sh[(c * T::ROWS + row) * T::FACES + fi] = Fh[ps][c];
+      for (int c = 0; c < NV; c++) sh[(c * T::ROWS + row) * FST + fi] = Fh[ps][c];
     }
   }
   __syncthreads();
 
   // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / h
   const float inv_h = p.inv_h32[A];
-  for (int e = threadIdx.x; e < nrow * ncell; e += THREADS) {
+  for (int e = threadIdx.x; e < T::ROWS * T::SEG; e += THREADS) {
     int row, l;
-    if constexpr (A == 0) { row = e / ncell; l = e % ncell; }
-    else { row = e % nrow; l = e / nrow; }
-    int I[3];
-    cell_of(row, l, I);
-    long long o = int_index(p, I[0], I[1], I[2]);
+    if constexpr (A == 0) { row = e / T::SEG; l = e - row * T::SEG; }
+    else { row = e % T::ROWS; l = e / T::ROWS; }
+    if (row >= nrow || l >= ncell) continue;
+    int o = ibase + row * irs + l * ias;
 #pragma unroll
     for (int c = 0; c < NV; c++) {
-      const float *hh = sh + (c * T::ROWS + row) * T::FACES;
+      const float *hh = sh + (c * T::ROWS + row) * FST;
       float d = (hh[l + 1] - hh[l]) * inv_h;
-      float prev = first ? 0.f : p.L32[c * p.N + o];
-      p.L32[c * p.N + o] = prev - d;
+      float *Lc = p.L32 + (size_t)c * p.N;
+      Lc[o] = (first ? 0.f : Lc[o]) - d;
     }
   }
 }

@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
     }
   }
   __syncthreads();
-  double *sh = sm;  // reuse: face fluxes [NV][ROWS][FACES]
+  constexpr int FST = A == 0 ? T::FACES : T::FACES + 1;  // odd stride when lanes walk rows
+  double *sh = sm;  // reuse: face fluxes [NV][ROWS][FST]
 #pragma unroll
   for (int ps = 0; ps < T::PASSES; ps++) {
     int e = threadIdx.x + ps * THREADS;
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
       if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
       else { row = e % T::ROWS; fi = e / T::ROWS; }
 #pragma unroll
-      for (int c = 0; c < NV; c++) sh[(c * T::ROWS + row) * T::FACES + fi] = Fh[ps][c];
+      for (int c = 0; c < NV; c++) sh[(c * T::ROWS + row) * FST + fi] = Fh[ps][c];
     }
   }
   __syncthreads();
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
     long long o = int_index(p, I[0], I[1], I[2]);
 #pragma unroll
     for (int c = 0; c < NV; c++) {
-      const double *hh = sh + (c * T::ROWS + row) * T::FACES;
+      const double *hh = sh + (c * T::ROWS + row) * FST;
       double d = divide(hh[l + 1] - hh[l], p.h[A], p.inv_h[A]);
       double prev = first ? 0.0 : p.L[c * p.N + o];
       p.L[c * p.N + o] = prev - d;

@@ -1,0 +1,79 @@
+"""The 2D workloads at their full sizes as parity cases.
+
+* rotating cylinder in a Mach 0.2 stream (2048^2 on [-40,40]^2, Re 150, 20-cell sponge,
+  free-stream ghosts, 1024 markers moving with Omega x X): strict FP64 right-hand side and one
+  SSP-RK3 step bit for bit against the oracle, and the FP32 form over 20 steps against FP64;
+* acoustic pulse scattered by a cylinder (256^2): WENO5-JS and TENO5 both, strict, 10 steps.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1905_00182_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _ib():
+    from paper_1905_00182_gb300 import ibfsa
+    ibfsa.lib()
+    return ibfsa
+
+
+def test_rotating_cylinder_full_size_strict():
+    w = W.rotating_cylinder_2d()
+    ib = _ib()
+    g = ib.Grid(w["spec"], strict=True, max_probes=360)
+    g.set_state(w["Q"])
+    g.set_markers(w["X"], w["U"], w["dS"])
+    L = g.rhs().cpu().numpy()
+    F = g.marker_forces().cpu().numpy()
+    Lo, Fo, _, _ = O.rhs(w["spec"], w["Q"], w["X"], w["U"], w["dS"], return_markers=True)
+    np.testing.assert_array_equal(L, Lo)
+    np.testing.assert_array_equal(F, Fo)
+    assert np.max(np.abs(F)) > 0.0  # the moving wall does work on the fluid
+    g.rk3_step(w["dt"], 1)
+    Q = g.get_state().cpu().numpy()
+    xi = g.penalty_integral().cpu().numpy()
+    dp = g.probe(w["probes"]).cpu().numpy()
+    assert g.status() == 0
+    Qo, xio = O.rk3(w["spec"], w["Q"], w["dt"], 1, w["X"], w["U"], w["dS"])
+    np.testing.assert_array_equal(Q, Qo)
+    np.testing.assert_array_equal(xi, xio)
+    np.testing.assert_array_equal(dp, O.probe(w["spec"], Qo, w["probes"]))
+
+
+def test_rotating_cylinder_fp32_form_within_1e3():
+    w = W.rotating_cylinder_2d()
+    ib = _ib()
+    fields = {}
+    for prec in (W.FP64, W.FP32_PERTURB):
+        g = ib.Grid(dataclasses.replace(w["spec"], precision=prec))
+        g.set_state(w["Q"])
+        g.set_markers(w["X"], w["U"], w["dS"])
+        g.rk3_step(w["dt"], 20)
+        assert g.status() == 0
+        Q = g.get_state()
+        spec = w["spec"]
+        ke = (Q[1] ** 2 + Q[2] ** 2) / Q[0]
+        fields[prec] = ((spec.gamma - 1.0) * (Q[3] - 0.5 * ke)).cpu().numpy()
+        g.close()
+    pinf = 1.0 / w["spec"].gamma
+    rel = np.linalg.norm(fields[W.FP32_PERTURB] - fields[W.FP64]) / np.linalg.norm(fields[W.FP64] - pinf)
+    assert rel <= 1e-3, rel
+
+
+@pytest.mark.parametrize("scheme", [W.WENO5JS, W.TENO5])
+def test_cylinder_pulse_both_schemes_strict(scheme):
+    w = W.cylinder_pulse_2d(scheme=scheme)
+    ib = _ib()
+    g = ib.Grid(w["spec"], strict=True)
+    g.set_state(w["Q"])
+    g.set_markers(w["X"], w["U"], w["dS"])
+    g.rk3_step(w["dt"], 10)
+    Q = g.get_state().cpu().numpy()
+    Qo, _ = O.rk3(w["spec"], w["Q"], w["dt"], 10, w["X"], w["U"], w["dS"])
+    np.testing.assert_array_equal(Q, Qo)
