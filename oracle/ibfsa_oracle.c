@@ -31,8 +31,8 @@
  * exact force conservation, linear reproduction of WENO/TENO on equal smoothness indicators,
  * TENO's ENO cut-off on a step, fifth-order convergence of the reconstruction, fourth-order
  * convergence of the viscous operator against the continuous PDE, free-stream preservation,
- * entropy-wave exact solution, third-order RK3, and the image solution of a plane acoustic
- * pulse reflected by a rigid wall of markers.
+ * entropy-wave exact solution, third-order RK3, convergence of the Sec. 3.1 pulse to the exact
+ * linear-acoustics solution, and penalty enforcement of no slip.
  */
 #include <math.h>
 #include <stdint.h>
