@@ -159,6 +159,37 @@ int ibfsa_profile_enable(ibfsa_grid *g, int enable);
 int ibfsa_profile_read(ibfsa_grid *g, int nclass, double *host_ms, long long *host_launches,
                        long long *host_timed);
 
+/* ---- Learned reconstruction weights (the learned-weight variant of the fifth-order
+ * reconstruction of Sec. 2, text after Eq. 5) ------------------------------------------------
+ * A network maps the normalised five-point stencil x = (v - v_2)/amp, amp = max_j |v_j - v_2|,
+ * of one split-flux component to the three weights of the third-order candidates:
+ * 5 -> 32 -> 32 -> 32 (gelu, tanh form) -> 3 -> softmax; face = v_2 + amp sum_k w_k qhat_k.
+ * Parameters: one float vector of IBFSA_MLP_NPARAM = 2403 entries [W1 (32x5, row = output
+ * unit), b1, W2 (32x32), b2, W3 (32x32), b3, W4 (3x32), b4].  Inference and training run on the
+ * tensor cores with every parameter and activation rounded to bfloat16 and FP32 accumulation.
+ * A training state (ibfsa_mlp_state_bytes() bytes of caller-allocated device memory, 16-byte
+ * aligned) holds FP32 master parameters, Adam moments, the last gradient and loss, and the
+ * packed bfloat16 image the kernels read.  Stencils are float [n][5] (upwind-ordered: the
+ * reconstruction is at the face between entries 2 and 3), targets float [n] (the face value),
+ * device memory.  Loss = mean over the batch of (sum_k w_k qhat_k - (target - v_2)/amp)^2;
+ * stencils with amp = 0 contribute nothing. */
+#define IBFSA_MLP_NPARAM 2403
+size_t ibfsa_mlp_state_bytes(void);
+/* Set the master parameters (params: 2403 floats, device or host) and zero the Adam moments. */
+int ibfsa_mlp_init(void *d_state, const float *params, void *cuda_stream);
+/* One Adam step (lr > 0; beta 0.9 / 0.999, eps 1e-8, step = 1, 2, ...) on the gradient of the
+ * batch; with lr = 0 only the gradient and the loss are computed (parameters unchanged). */
+int ibfsa_mlp_train_step(void *d_state, int n, const float *d_stencils, const float *d_targets,
+                         float lr, int step, void *cuda_stream);
+/* Copy master parameters, last gradient and last loss out (any pointer may be NULL; host or
+ * device memory); synchronises the stream. */
+int ibfsa_mlp_read(const void *d_state, float *params, float *grad, float *loss,
+                   void *cuda_stream);
+/* Inference on n stencils: face values [n], weights [n][3] and, with targets, the mean loss
+ * (each output may be NULL; device memory). */
+int ibfsa_mlp_eval(const void *d_state, int n, const float *d_stencils, const float *d_targets,
+                   float *d_face, float *d_omega, float *d_loss, void *cuda_stream);
+
 /* Allocation-free right-hand side.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- plug-ins whose host application owns the whole
  * device-memory budget, latency-critical loops that must not pay the implicit device-wide

@@ -24,6 +24,7 @@ UNITS = {
     "stage_fp64_strict.cu": ["--fmad=false"],
     "stage_fp64_fast.cu": ["--fmad=true"],
     "stage_fp32.cu": ["--fmad=true"],
+    "mlp.cu": ["--fmad=true"],
     "noalloc.cu": [],
 }
 

@@ -34,7 +34,10 @@ EXPORTS = (
     "ibfsa_get_penalty_integral", "ibfsa_set_penalty_integral", "ibfsa_rhs", "ibfsa_rk3_step",
     "ibfsa_max_wavespeed", "ibfsa_probe", "ibfsa_get_status", "ibfsa_last_error",
     "ibfsa_profile_enable", "ibfsa_profile_read", "ibfsa_rhs_noalloc",
+    "ibfsa_mlp_state_bytes", "ibfsa_mlp_init", "ibfsa_mlp_train_step", "ibfsa_mlp_read",
+    "ibfsa_mlp_eval",
 )
+MLP_NPARAM = 2403
 
 KERNEL_CLASSES = ("pad", "ib_interp", "conv_x", "conv_y", "conv_z", "visc_flux", "visc_div",
                   "ib_spread", "finish", "probe")
@@ -97,6 +100,12 @@ def lib():
         L.ibfsa_last_error.restype = ctypes.c_char_p
         L.ibfsa_profile_enable.argtypes = [_P, ctypes.c_int]
         L.ibfsa_profile_read.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+        L.ibfsa_mlp_state_bytes.restype = ctypes.c_size_t
+        L.ibfsa_mlp_state_bytes.argtypes = []
+        L.ibfsa_mlp_init.argtypes = [_P, _P, _P]
+        L.ibfsa_mlp_train_step.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.c_int, _P]
+        L.ibfsa_mlp_read.argtypes = [_P, _P, _P, _P, _P]
+        L.ibfsa_mlp_eval.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]
         L.ibfsa_rhs_noalloc.argtypes = [D, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]
         _lib = L
     return _lib
@@ -221,6 +230,83 @@ def ibfsa_rhs_noalloc(desc: GridDesc, Q: int, n_markers: int, X: int, U: int, dS
     _check(lib().ibfsa_rhs_noalloc(ctypes.byref(desc), _P(Q), int(n_markers), _P(X), _P(U),
                                    _P(dS), _P(xi), _P(L), _P(F or None), _P(status or None),
                                    _P(stream)))
+
+
+def ibfsa_mlp_state_bytes() -> int:
+    return int(lib().ibfsa_mlp_state_bytes())
+
+
+def ibfsa_mlp_init(state: int, params: int, stream: int = 0):
+    _check(lib().ibfsa_mlp_init(_P(state), _P(params), _P(stream)))
+
+
+def ibfsa_mlp_train_step(state: int, n: int, stencils: int, targets: int, lr: float, step: int,
+                         stream: int = 0):
+    _check(lib().ibfsa_mlp_train_step(_P(state), int(n), _P(stencils), _P(targets), float(lr),
+                                      int(step), _P(stream)))
+
+
+def ibfsa_mlp_read(state: int, params: int = 0, grad: int = 0, loss: int = 0, stream: int = 0):
+    _check(lib().ibfsa_mlp_read(_P(state), _P(params or None), _P(grad or None),
+                                _P(loss or None), _P(stream)))
+
+
+def ibfsa_mlp_eval(state: int, n: int, stencils: int, targets: int = 0, face: int = 0,
+                   omega: int = 0, loss: int = 0, stream: int = 0):
+    _check(lib().ibfsa_mlp_eval(_P(state), int(n), _P(stencils), _P(targets or None),
+                                _P(face or None), _P(omega or None), _P(loss or None),
+                                _P(stream)))
+
+
+class MLP:
+    """Training state of the learned weights in device memory (torch-allocated)."""
+
+    def __init__(self, params):
+        import torch
+        self.nbytes = ibfsa_mlp_state_bytes()
+        self.buf = torch.zeros(self.nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+        self.ptr = (self.buf.data_ptr() + 255) & ~255
+        p = torch.as_tensor(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+        ibfsa_mlp_init(self.ptr, p.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        self.step = 0
+
+    def train_step(self, stencils, targets, lr):
+        import torch
+        self.step += 1
+        ibfsa_mlp_train_step(self.ptr, stencils.shape[0], stencils.data_ptr(),
+                             targets.data_ptr(), lr, self.step,
+                             torch.cuda.current_stream().cuda_stream)
+
+    def gradient(self, stencils, targets):
+        import torch
+        ibfsa_mlp_train_step(self.ptr, stencils.shape[0], stencils.data_ptr(),
+                             targets.data_ptr(), 0.0, max(1, self.step),
+                             torch.cuda.current_stream().cuda_stream)
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = np.zeros(1, np.float32)
+        ibfsa_mlp_read(self.ptr, 0, g.ctypes.data, loss.ctypes.data,
+                       torch.cuda.current_stream().cuda_stream)
+        return float(loss[0]), g
+
+    def params(self):
+        import torch
+        p = np.zeros(MLP_NPARAM, np.float32)
+        loss = np.zeros(1, np.float32)
+        ibfsa_mlp_read(self.ptr, p.ctypes.data, 0, loss.ctypes.data,
+                       torch.cuda.current_stream().cuda_stream)
+        return p, float(loss[0])
+
+    def eval(self, stencils, targets=None):
+        import torch
+        n = stencils.shape[0]
+        face = torch.empty(n, dtype=torch.float32, device="cuda")
+        omega = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        ibfsa_mlp_eval(self.ptr, n, stencils.data_ptr(),
+                       targets.data_ptr() if targets is not None else 0, face.data_ptr(),
+                       omega.data_ptr(), loss.data_ptr() if targets is not None else 0,
+                       torch.cuda.current_stream().cuda_stream)
+        return face, omega, (float(loss.item()) if targets is not None else None)
 
 
 # ---- convenience wrapper over torch tensors -------------------------------------------------

@@ -299,3 +299,23 @@ def gaussian_pulse_state_torch(spec: GridSpec, center, amp: float = 1e-3, halfwi
         p = p0 + amp * torch.exp(-math.log(2.0) * r2 / halfwidth ** 2)
         Q[spec.nv - 1, k] = p / (spec.gamma - 1.0)
     return Q
+
+
+MLP_SIZES = [(32, 5), (32,), (32, 32), (32,), (32, 32), (32,), (3, 32), (3,)]
+MLP_NPARAM = sum(int(np.prod(s)) for s in MLP_SIZES)
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the learned-weight network, one flat float32 vector
+    [W1 (32x5), b1, W2, b2, W3, b3, W4 (3x32), b4]: scaled normal weights, zero biases except
+    b4 = log(0.1, 0.6, 0.3), so the untrained network starts near the linear weights."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in MLP_SIZES:
+        if len(s) == 2:
+            parts.append(rng.standard_normal(s) * math.sqrt(1.0 / s[1]))
+        else:
+            parts.append(np.zeros(s))
+    parts[6] = parts[6] * 0.1
+    parts[7] = np.log(np.array([0.1, 0.6, 0.3]))
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
