@@ -52,8 +52,10 @@ enum {
   IBFSA_ERR_WORKSPACE = -6    /* workspace too small or misaligned */
 };
 
-/* convective schemes (text after Eq. 5) */
-enum { IBFSA_WENO5JS = 0, IBFSA_TENO5 = 1 };
+/* convective schemes (text after Eq. 5); IBFSA_MLP_TENO5 = the learned-weight variant: TENO5
+ * decides where the flow is smooth, and there the weights come from the network attached with
+ * ibfsa_set_mlp (FP32 perturbation arithmetic only) */
+enum { IBFSA_WENO5JS = 0, IBFSA_TENO5 = 1, IBFSA_MLP_TENO5 = 2 };
 /* arithmetic of the stage kernels: FP64 throughout, or the perturbation form -- the stencil
  * arithmetic (split fluxes, reconstruction, viscous terms, right-hand side) in FP32 on
  * q' = Q - qinf and on primitive perturbations, expanded so that no O(1) free-stream terms
@@ -74,7 +76,7 @@ typedef struct {
   double gamma;            /* ratio of specific heats (ideal gas) */
   double Re;               /* Reynolds number of Eq. 2; Re <= 0 drops the viscous terms */
   double qinf[5];          /* free-stream conservative state (first nv entries used) */
-  int scheme;              /* IBFSA_WENO5JS | IBFSA_TENO5 */
+  int scheme;              /* IBFSA_WENO5JS | IBFSA_TENO5 | IBFSA_MLP_TENO5 */
   int precision;           /* IBFSA_FP64 | IBFSA_FP32_PERTURB */
   int strict_fp;           /* 1: every FP64 operation rounded separately (no fused
                               multiply-add), divisions kept as divisions, spreading summed
@@ -189,6 +191,24 @@ int ibfsa_mlp_read(const void *d_state, float *params, float *grad, float *loss,
  * (each output may be NULL; device memory). */
 int ibfsa_mlp_eval(const void *d_state, int n, const float *d_stencils, const float *d_targets,
                    float *d_face, float *d_omega, float *d_loss, void *cuda_stream);
+
+/* Attach the learned weights of a training state to a grid (IBFSA_MLP_TENO5): a
+ * reconstruction uses the network when TENO5 keeps all three stencils and the stencil's
+ * amplitude max_j |v_j - v_2| exceeds 1e-9 (split-flux perturbation units); otherwise TENO5's
+ * weights.  The image is copied (asynchronously), the state may be freed afterwards. */
+int ibfsa_set_mlp(ibfsa_grid *g, const void *d_state);
+/* Reconstructions that used the network and all reconstructions evaluated since the last call
+ * (host array of two counts; synchronises). */
+int ibfsa_mlp_stats(ibfsa_grid *g, unsigned long long *host_counts);
+/* Training stencils from the grid's current state (FP32 perturbation grids): random faces,
+ * directions, components and split-flux signs; kept when the learned form would use the
+ * network there (TENO5 keeps all three stencils, amplitude above the floor).  Writes up to n_max
+ * stencils [n][5] (upwind-ordered) and targets [n]: the face value of the ninth-order
+ * upwind-biased reconstruction of the same split flux from the 9 cells on its upwind side
+ * (exact for polynomials of degree 8), and the number of stencils accepted (device int; the
+ * first min(count, n_max) were written).  attempts: candidate faces drawn per thread. */
+int ibfsa_mlp_sample(ibfsa_grid *g, int n_max, unsigned long long seed, int attempts,
+                     float *d_stencils, float *d_targets, int *d_count);
 
 /* Allocation-free right-hand side.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- plug-ins whose host application owns the whole

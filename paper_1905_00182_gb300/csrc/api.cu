@@ -53,8 +53,10 @@ static int check_desc(const ibfsa_grid_desc *d) {
   if (padded >= (1LL << 31)) return fail(IBFSA_ERR_ARG, "grid too large (padded cells >= 2^31)");
   if (!(d->gamma > 1.0)) return fail(IBFSA_ERR_ARG, "gamma must exceed 1");
   if (!(d->qinf[0] > 0.0)) return fail(IBFSA_ERR_ARG, "free-stream density must be positive");
-  if (d->scheme != IBFSA_WENO5JS && d->scheme != IBFSA_TENO5)
+  if (d->scheme != IBFSA_WENO5JS && d->scheme != IBFSA_TENO5 && d->scheme != IBFSA_MLP_TENO5)
     return fail(IBFSA_ERR_UNSUPPORTED, "scheme %d is not provided by this build", d->scheme);
+  if (d->scheme == IBFSA_MLP_TENO5 && d->precision != IBFSA_FP32_PERTURB)
+    return fail(IBFSA_ERR_UNSUPPORTED, "the learned weights run in the FP32 perturbation form");
   if (d->precision != IBFSA_FP64 && d->precision != IBFSA_FP32_PERTURB)
     return fail(IBFSA_ERR_UNSUPPORTED, "precision %d is not provided by this build", d->precision);
   if (d->precision == IBFSA_FP32_PERTURB && d->strict_fp)
@@ -175,6 +177,8 @@ Layout layout_for(const ibfsa_grid_desc &d) {
   L.status = take(sizeof(int) * 4);
   L.probe_xp = take(sizeof(double) * p.dim * Pn);
   L.probe_out = take(sizeof(double) * Pn);
+  L.mlp_img = take(d.scheme == IBFSA_MLP_TENO5 ? mlp_image_bytes() : 0);
+  L.mlp_counts = take(sizeof(unsigned long long) * 4);
   L.total = off;
   return L;
 }
@@ -207,6 +211,7 @@ cudaError_t prof_harvest(Prof *pr) {
 }
 
 static cudaError_t run_stage(Grid *G, const StageArgs &s) {
+  if (G->d.scheme == IBFSA_MLP_TENO5 && !G->mlp_set) return cudaErrorInvalidValue;
   if (G->d.precision == IBFSA_FP32_PERTURB) {
     if (!G->qn32_valid) {
       cudaError_t e = fp32_refresh(G->p, G->Q, G->stream);
@@ -289,8 +294,14 @@ int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t wor
   G.probe_xp = (double *)(w + L.probe_xp);
   G.probe_out = (double *)(w + L.probe_out);
   G.max_probes = desc->max_probes;
+  G.p.mlp_img = (const unsigned char *)(w + L.mlp_img);
+  G.p.mlp_counts = (unsigned long long *)(w + L.mlp_counts);
+  G.p.mlp_floor = 1e-9f;
+  G.mlp_set = false;
   G.p.nm = 0;
   cudaError_t e = cudaMemsetAsync(G.p.status, 0, sizeof(int) * 4, G.stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(G.p.mlp_counts, 0, sizeof(unsigned long long) * 4, G.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(G.p.F, 0, L.xi - L.F, G.stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(G.xi, 0, sizeof(double) * G.p.dim * (desc->max_markers > 0 ? desc->max_markers : 1), G.stream);
@@ -437,6 +448,8 @@ int ibfsa_rhs(ibfsa_grid *g, double *L) {
   s.xis = G.xi;
   s.stage = -1;
   s.prof = &G.prof;
+  if (G.d.scheme == IBFSA_MLP_TENO5 && !G.mlp_set)
+    return fail(IBFSA_ERR_ARG, "IBFSA_MLP_TENO5 grid without weights: call ibfsa_set_mlp");
   cudaError_t e = run_stage(&G, s);
   return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_rhs");
 }
@@ -445,6 +458,8 @@ int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps) {
   if (!g) return fail(IBFSA_ERR_ARG, "NULL grid");
   if (nsteps < 0 || !(dt > 0.0)) return fail(IBFSA_ERR_ARG, "need dt > 0 and nsteps >= 0");
   Grid &G = g->g;
+  if (G.d.scheme == IBFSA_MLP_TENO5 && !G.mlp_set)
+    return fail(IBFSA_ERR_ARG, "IBFSA_MLP_TENO5 grid without weights: call ibfsa_set_mlp");
   // Shu-Osher coefficients: Q^(s+1) = a_s Qn + b_s (Q^(s) + dt L(Q^(s)))
   const double A[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0}, B[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
   for (int step = 0; step < nsteps; step++) {
@@ -504,6 +519,42 @@ int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out) {
     e = cudaMemcpyAsync(out, G.probe_out, sizeof(double) * np, cudaMemcpyDefault, G.stream);
   if (e == cudaSuccess && is_host_pointer(out)) e = cudaStreamSynchronize(G.stream);
   return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_probe");
+}
+
+int ibfsa_set_mlp(ibfsa_grid *g, const void *d_state) {
+  if (!g || !d_state) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  if (G.d.scheme != IBFSA_MLP_TENO5)
+    return fail(IBFSA_ERR_ARG, "the grid's scheme is not IBFSA_MLP_TENO5");
+  cudaError_t e = cudaMemcpyAsync((void *)G.p.mlp_img, (const char *)d_state + mlp_image_offset(),
+                                  mlp_image_bytes(), cudaMemcpyDeviceToDevice, G.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ibfsa_set_mlp");
+  G.mlp_set = true;
+  return IBFSA_OK;
+}
+
+int ibfsa_mlp_stats(ibfsa_grid *g, unsigned long long *host_counts) {
+  if (!g || !host_counts) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  cudaError_t e = cudaMemcpyAsync(host_counts, G.p.mlp_counts, 2 * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, G.stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(G.p.mlp_counts, 0, 2 * sizeof(unsigned long long), G.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G.stream);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_mlp_stats");
+}
+
+int ibfsa_mlp_sample(ibfsa_grid *g, int n_max, unsigned long long seed, int attempts,
+                     float *d_stencils, float *d_targets, int *d_count) {
+  if (!g || n_max < 0 || attempts < 1 || !d_stencils || !d_targets || !d_count)
+    return fail(IBFSA_ERR_ARG, "bad argument");
+  Grid &G = g->g;
+  if (G.d.precision != IBFSA_FP32_PERTURB)
+    return fail(IBFSA_ERR_UNSUPPORTED, "sampling reads the FP32 perturbation form");
+  cudaError_t e = fp32_mlp_sample(G.p, G.Q, n_max, seed, attempts, d_stencils, d_targets,
+                                  d_count, G.stream);
+  G.qn32_valid = true;
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_mlp_sample");
 }
 
 int ibfsa_get_status(ibfsa_grid *g, int *host_flags) {

@@ -52,6 +52,11 @@ struct Plan {
   // the FP32 form carries the stage values of a step as FP32 increments over the FP64 state:
   // qn32 = (float)(Qn - q_inf), d1 = Q1 - Qn, d2 = Q2 - Qn
   float *qn32, *d1, *d2;
+  // learned weights (scheme IBFSA_MLP_TENO5): packed bf16 image, counters of the
+  // reconstructions that used the network / all reconstructions evaluated, guard floor
+  const unsigned char *mlp_img;
+  unsigned long long *mlp_counts;
+  float mlp_floor;
   unsigned long long *alpha_bits;  // [3] ordered bits of the split speeds
   int *status;
   // markers
@@ -96,13 +101,14 @@ struct Grid {
   double *probe_xp, *probe_out;
   int max_probes;
   bool qn32_valid;  // FP32 form: qn32 matches Qn
+  bool mlp_set;     // learned weights attached (ibfsa_set_mlp)
   Prof prof;
 };
 
 // Workspace layout: byte offsets of every buffer for a descriptor.
 struct Layout {
   size_t Q, Q1, Q2, Qp, Wp, L, V, f, X, U, dS, F, xi, xi1, xi2, alpha, status, probe_xp,
-      probe_out, total;
+      probe_out, mlp_img, mlp_counts, total;
 };
 Layout layout_for(const ibfsa_grid_desc &d);
 void record_error(const char *msg);  // sets the thread-local message of ibfsa_last_error
@@ -130,6 +136,11 @@ cudaError_t fast_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t fp32_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
 cudaError_t fp32_wavespeed(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t fp32_refresh(const Plan &p, const double *Q, cudaStream_t st);
+cudaError_t fp32_mlp_sample(const Plan &p, const double *Q, int n_max, unsigned long long seed,
+                            int attempts, float *stencils, float *targets, int *count,
+                            cudaStream_t st);
+size_t mlp_image_offset();   // byte offset of the packed image inside a training state
+size_t mlp_image_bytes();
 cudaError_t fp32_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
                        cudaStream_t st, Prof *pr);
 cudaError_t strict_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,

@@ -156,8 +156,9 @@ __device__ __forceinline__ bool load_row(const float *S, const float *T, int n, 
   float amp = normalise(v, x);
   candidates(x, q);
   tn = 0.f;
-  if (ok && T) tn = amp > 0.f ? (T[m] - v[2]) / amp : 0.f;
-  return ok && amp > 0.f;
+  bool live = amp > 1e-30f;  // the same cut as normalise: no overflow from denormal amplitudes
+  if (ok && T && live) tn = (T[m] - v[2]) / amp;
+  return ok && live;
 }
 
 __global__ void __launch_bounds__(32 * TRAIN_WARPS, 1)
@@ -389,6 +390,10 @@ __global__ void __launch_bounds__(256) k_eval(const unsigned char *__restrict__ 
 }
 
 }  // namespace mlp
+
+size_t mlp_image_offset() { return mlp::OFF_IMAGE_BYTES; }
+size_t mlp_image_bytes() { return mlp::PACKED_BYTES; }
+
 }  // namespace ibfsa
 
 using namespace ibfsa;

@@ -160,7 +160,7 @@ __device__ __forceinline__ float normalise(const float v[5], float x[5]) {
   float amp = 0.f;
 #pragma unroll
   for (int j = 0; j < 5; j++) amp = fmaxf(amp, fabsf(v[j] - v[2]));
-  float inv = amp > 0.f ? 1.f / amp : 0.f;
+  float inv = amp > 1e-30f ? 1.f / amp : 0.f;  // no overflow from denormal amplitudes
 #pragma unroll
   for (int j = 0; j < 5; j++) x[j] = (v[j] - v[2]) * inv;
   return amp;
@@ -171,6 +171,67 @@ __device__ __forceinline__ void candidates(const float x[5], float q[3]) {
   q[0] = (2.f * x[0] - 7.f * x[1] + 11.f * x[2]) * s6;
   q[1] = (-x[1] + 5.f * x[2] + 2.f * x[3]) * s6;
   q[2] = (2.f * x[2] + 5.f * x[3] - x[4]) * s6;
+}
+
+}  // namespace mlp
+}  // namespace ibfsa
+
+namespace ibfsa {
+namespace mlp {
+
+// inference only: softmax weights of rows g (wa) and g+8 (wb) in lanes t == 0
+__device__ __forceinline__ void infer_tile(const unsigned char *img, const float xa[5],
+                                           const float xb[5], int g, int t, float wa[3],
+                                           float wb[3]) {
+  float z[4][4], z4[4];
+  uint32_t A0[1][4], A[2][4];
+  input_fragment(xa, xb, t, A0);
+  dense32<1>(z, A0, img, OFF_W1, 16, OFF_B1, g, t);
+  gelu_pack(z, A);
+  dense32<2>(z, A, img, OFF_W2, 32, OFF_B2, g, t);
+  gelu_pack(z, A);
+  dense32<2>(z, A, img, OFF_W3, 32, OFF_B3, g, t);
+  gelu_pack(z, A);
+  logits(z4, A, img, g, t);
+  float l2a = __shfl_down_sync(0xffffffffu, z4[0], 1);
+  float l2b = __shfl_down_sync(0xffffffffu, z4[2], 1);
+  float ma = fmaxf(z4[0], fmaxf(z4[1], l2a)), mb = fmaxf(z4[2], fmaxf(z4[3], l2b));
+  float ea0 = __expf(z4[0] - ma), ea1 = __expf(z4[1] - ma), ea2 = __expf(l2a - ma);
+  float eb0 = __expf(z4[2] - mb), eb1 = __expf(z4[3] - mb), eb2 = __expf(l2b - mb);
+  float ia = 1.f / (ea0 + ea1 + ea2), ib = 1.f / (eb0 + eb1 + eb2);
+  wa[0] = ea0 * ia; wa[1] = ea1 * ia; wa[2] = ea2 * ia;
+  wb[0] = eb0 * ib; wb[1] = eb1 * ib; wb[2] = eb2 * ib;
+}
+
+// Weights for one stencil per lane, evaluated by the whole warp on the tensor cores (two
+// 16-row tiles: lanes 0..15 and 16..31).  x: this lane's normalised stencil; active: whether
+// this lane wants the network (tiles with no active lane are skipped).  Must be called by all
+// 32 lanes.  Active lanes get the network's three weights in w; the others keep w.
+__device__ __forceinline__ void warp_weights(const unsigned char *img, const float x[5],
+                                             bool active, float w[3]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  unsigned any = __ballot_sync(0xffffffffu, active);
+#pragma unroll
+  for (int T = 0; T < 2; T++) {
+    if (((any >> (16 * T)) & 0xffffu) == 0u) continue;  // warp-uniform
+    float xa[5], xb[5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+      xa[j] = __shfl_sync(0xffffffffu, x[j], 16 * T + g);
+      xb[j] = __shfl_sync(0xffffffffu, x[j], 16 * T + g + 8);
+    }
+    float wa[3], wb[3];
+    infer_tile(img, xa, xb, g, t, wa, wb);
+    // row r of tile T belongs to lane 16 T + r; lane 4 (r mod 8) holds it (wa for r < 8)
+    int r = lane - 16 * T;
+    int src = 4 * (r & 7);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      float va = __shfl_sync(0xffffffffu, wa[k], src);
+      float vb = __shfl_sync(0xffffffffu, wb[k], src);
+      if (active && r >= 0 && r < 16) w[k] = r < 8 ? va : vb;
+    }
+  }
 }
 
 }  // namespace mlp

@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include "ibfsa_internal.h"
+#include "mlp_tile.cuh"
 
 namespace ibfsa {
 namespace fp32_ns {
@@ -131,6 +132,21 @@ __device__ __forceinline__ float weno5js(float a, float b, float c, float d, flo
   float s2 = (eps + k.b2) * (eps + k.b2);
   float al0 = 0.1f * (s1 * s2), al1 = 0.6f * (s0 * s2), al2 = 0.3f * (s0 * s1);
   return __fdividef(al0 * k.q0 + al1 * k.q1 + al2 * k.q2, al0 + al1 + al2);
+}
+
+__device__ __forceinline__ int teno_mask(const Cands &k) {
+  const float eps = 1e-30f, CT = 1e-5f;
+  float tau = fabsf(k.b0 - k.b2);
+  float r0 = __fdividef(tau, k.b0 + eps);
+  float r1 = __fdividef(tau, k.b1 + eps);
+  float r2 = __fdividef(tau, k.b2 + eps);
+  float inv = __fdividef(1.f, 1.f + fmaxf(r0, fmaxf(r1, r2)));
+  float t, t2, g0, g1, g2;
+  t = (1.f + r0) * inv; t2 = t * t; g0 = t2 * t2 * t2;
+  t = (1.f + r1) * inv; t2 = t * t; g1 = t2 * t2 * t2;
+  t = (1.f + r2) * inv; t2 = t * t; g2 = t2 * t2 * t2;
+  float th = CT * (g0 + g1 + g2);
+  return (g0 >= th ? 1 : 0) | (g1 >= th ? 2 : 0) | (g2 >= th ? 4 : 0);
 }
 
 __device__ __forceinline__ float teno5(const Plan &tw, float a, float b, float c, float d,
@@ -251,6 +267,27 @@ constexpr size_t conv_smem() {
   return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN;  // >= face-flux area
 }
 
+// learned weights: reconstruction of one stencil with the TENO5 guard; every lane of the warp
+// must call it (the network runs warp-wide on the tensor cores)
+__device__ __forceinline__ float recon_mlp(const Plan &p, const unsigned char *img, bool valid,
+                                           float a, float b, float c, float d, float e,
+                                           unsigned &used, unsigned &seen) {
+  Cands k = candidates(a, b, c, d, e);
+  int mask = teno_mask(k);
+  float v[5] = {a, b, c, d, e}, x[5];
+  float amp = mlp::normalise(v, x);
+  bool elig = valid && mask == 7 && amp > p.mlp_floor;
+  const float *tw = p.teno_w32[mask];
+  float w[3] = {tw[0], tw[1], tw[2]};
+  mlp::warp_weights(img, x, elig, w);
+  unsigned ball = __ballot_sync(0xffffffffu, elig), vb = __ballot_sync(0xffffffffu, valid);
+  used += __popc(ball);
+  seen += __popc(vb);
+  // delta form: constant stencils are reproduced exactly whatever the weights
+  return elig ? c + w[0] * (k.q0 - c) + w[1] * (k.q1 - c) + w[2] * (k.q2 - c)
+              : w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
+}
+
 template <int DIM, int A, int SCHEME>
 __global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
   constexpr int NV = DIM + 2;
@@ -300,6 +337,11 @@ __global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
   const float *Wa = p.Wp32 + (size_t)A * p.NP;
   const float *Wpr = p.Wp32 + (size_t)DIM * p.NP;
 
+  if constexpr (SCHEME == IBFSA_MLP_TENO5) {
+    uint4 *dst = reinterpret_cast<uint4 *>(smf + 2 * NV * T::ROWS * T::LEN);
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.mlp_img);
+    for (int i = threadIdx.x; i < mlp::PACKED_BYTES / 16; i += THREADS) dst[i] = src[i];
+  }
   // 1. f+-' of the staged cells (seg0-3 .. seg0+ncell+2)
   for (int e = threadIdx.x; e < T::ROWS * T::LEN; e += THREADS) {
     int row, l;
@@ -330,20 +372,49 @@ __global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
   // 2. faces m+1/2, m = seg0-1 .. seg0+ncell-1 (tile face index fi = m - seg0 + 1)
   constexpr int MAXP = (T::ROWS * T::FACES + THREADS - 1) / THREADS;
   float Fh[MAXP][NV];
+  if constexpr (SCHEME == IBFSA_MLP_TENO5) {
+    unsigned char *img = reinterpret_cast<unsigned char *>(smf + 2 * NV * T::ROWS * T::LEN);
+    unsigned used = 0, seen = 0;
 #pragma unroll
-  for (int ps = 0; ps < MAXP; ps++) {
-    int e = threadIdx.x + ps * THREADS;
-    int row, fi;
-    if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
-    else { row = e % T::ROWS; fi = e / T::ROWS; }
-    if (e < T::ROWS * T::FACES && row < nrow && fi < nface) {
+    for (int ps = 0; ps < MAXP; ps++) {
+      int e = threadIdx.x + ps * THREADS;
+      int row, fi;
+      if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
+      else { row = e % T::ROWS; fi = e / T::ROWS; }
+      bool valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
+      if (!valid) { row = 0; fi = 0; }  // in-bounds reads; results discarded
       int b = fi + 2;
 #pragma unroll
       for (int c = 0; c < NV; c++) {
         const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
         const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
-        Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
-                    recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+        float hp = recon_mlp(p, img, valid, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2],
+                             used, seen);
+        float hm = recon_mlp(p, img, valid, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1],
+                             used, seen);
+        Fh[ps][c] = hp + hm;
+      }
+    }
+    if ((threadIdx.x & 31) == 0 && seen) {
+      atomicAdd(&p.mlp_counts[0], (unsigned long long)used);
+      atomicAdd(&p.mlp_counts[1], (unsigned long long)seen);
+    }
+  } else {
+#pragma unroll
+    for (int ps = 0; ps < MAXP; ps++) {
+      int e = threadIdx.x + ps * THREADS;
+      int row, fi;
+      if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
+      else { row = e % T::ROWS; fi = e / T::ROWS; }
+      if (e < T::ROWS * T::FACES && row < nrow && fi < nface) {
+        int b = fi + 2;
+#pragma unroll
+        for (int c = 0; c < NV; c++) {
+          const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
+          const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
+          Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
+                      recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+        }
       }
     }
   }
@@ -629,7 +700,8 @@ inline unsigned blocks_for(long long n, int threads) {
 template <int DIM, int A, int SCHEME>
 cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
   using T = Tile<A>;
-  constexpr size_t smem = conv_smem<DIM, A>();
+  constexpr size_t smem =
+      conv_smem<DIM, A>() + (SCHEME == IBFSA_MLP_TENO5 ? (size_t)mlp::PACKED_BYTES : 0);
   cudaError_t e = cudaFuncSetAttribute(k_conv32<DIM, A, SCHEME>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -706,13 +778,141 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// training stencils of the learned weights from the current state
+// ------------------------------------------------------------------------------------------
+struct Coef9 {
+  float c[9];  // face value of the 9-point upwind-biased reconstruction from cells i-4 .. i+4
+};
+
+__device__ __forceinline__ unsigned long long splitmix(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+template <int DIM>
+__global__ void k_mlp_sample(Plan p, int n_max, unsigned long long seed, int attempts, Coef9 cf,
+                             float *__restrict__ S, float *__restrict__ T, int *count) {
+  constexpr int NV = DIM + 2;
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  Free fs = free_stream(p);
+  for (int att = 0; att < attempts; att++) {
+    unsigned long long r = splitmix(seed ^ splitmix((unsigned long long)tid * attempts + att));
+    int A = (int)(r % DIM);
+    int c = (int)((r >> 8) % NV);
+    int sign = (int)((r >> 16) & 1);
+    unsigned long long r2 = splitmix(r);
+    int I[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      unsigned span = a == A ? (unsigned)(p.n[a] - 1) : (unsigned)p.n[a];
+      I[a] = a < DIM ? (int)((r2 >> (20 * a)) % (span ? span : 1u)) : 0;
+    }
+    if (p.n[A] < 2) continue;
+    const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
+    float f[10];
+#pragma unroll
+    for (int o = 0; o < 10; o++) {
+      int J[3] = {I[0], I[1], I[2]};
+      J[A] += o - 4;
+      long long sidx = ((long long)(J[2] + p.g[2]) * p.P[1] + (J[1] + p.g[1])) * p.P[0] + (J[0] + p.g[0]);
+      float up = p.Wp32[A * p.NP + sidx];
+      float pp = p.Wp32[DIM * p.NP + sidx];
+      float ua = fs.u[A] + up;
+      float q = p.Qp32[c * p.NP + sidx];
+      float F;
+      if (c == 0) F = p.Qp32[(1 + A) * p.NP + sidx];
+      else if (c == NV - 1) F = (q + pp) * ua + fs.H * up;
+      else {
+        F = q * ua + fs.m[c - 1] * up;
+        if (c - 1 == A) F += pp;
+      }
+      f[o] = 0.5f * (sign == 0 ? F + alpha * q : F - alpha * q);
+    }
+    float v[5];
+    if (sign == 0) { v[0] = f[2]; v[1] = f[3]; v[2] = f[4]; v[3] = f[5]; v[4] = f[6]; }
+    else { v[0] = f[7]; v[1] = f[6]; v[2] = f[5]; v[3] = f[4]; v[4] = f[3]; }
+    Cands k = candidates(v[0], v[1], v[2], v[3], v[4]);
+    float amp = 0.f;
+#pragma unroll
+    for (int j = 0; j < 5; j++) amp = fmaxf(amp, fabsf(v[j] - v[2]));
+    if (teno_mask(k) != 7 || !(amp > p.mlp_floor)) continue;
+    // upwind side of the face: cells i-4 .. i+4 for the right-going flux, the mirror image
+    // (cells i+5 .. i-3) for the left-going one
+    float tgt = 0.f;
+#pragma unroll
+    for (int o = 0; o < 9; o++) tgt += cf.c[o] * (sign == 0 ? f[o] : f[9 - o]);
+    int idx = atomicAdd(count, 1);
+    if (idx >= n_max) return;
+#pragma unroll
+    for (int j = 0; j < 5; j++) S[(size_t)idx * 5 + j] = v[j];
+    T[idx] = tgt;
+  }
+}
+
 }  // namespace fp32_ns
+
+// coefficients c_o (o = -4..4) with sum_o c_o avg_o(h) = h(0) for polynomials h of degree <= 8,
+// avg_o = mean over [o-1, o] (the cell left of the face is o = 0): the flux-reconstruction target
+// of the ninth-order upwind-biased scheme
+static void upwind9(float out[9]) {
+  constexpr int K = 9;
+  double M[K][K + 1];
+  for (int pw = 0; pw < K; pw++) {
+    for (int j = 0; j < K; j++) {
+      double o = j - 4;
+      M[pw][j] = (pow(o, pw + 1) - pow(o - 1.0, pw + 1)) / (pw + 1);
+    }
+    M[pw][K] = pw == 0 ? 1.0 : 0.0;
+  }
+  for (int col = 0; col < K; col++) {
+    int piv = col;
+    for (int r = col + 1; r < K; r++)
+      if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+    for (int k = 0; k <= K; k++) {
+      double tmp = M[col][k];
+      M[col][k] = M[piv][k];
+      M[piv][k] = tmp;
+    }
+    for (int r = 0; r < K; r++) {
+      if (r == col) continue;
+      double fct = M[r][col] / M[col][col];
+      for (int k = col; k <= K; k++) M[r][k] -= fct * M[col][k];
+    }
+  }
+  for (int j = 0; j < K; j++) out[j] = (float)(M[j][K] / M[j][j]);
+}
+
+cudaError_t fp32_mlp_sample(const Plan &p, const double *Q, int n_max, unsigned long long seed,
+                            int attempts, float *stencils, float *targets, int *count,
+                            cudaStream_t st) {
+  using namespace fp32_ns;
+  cudaError_t e = fp32_wavespeed(p, Q, st);  // qn32, padded perturbation and split speeds
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(count, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  Coef9 cf;
+  upwind9(cf.c);
+  int threads = 256, blocks = 152 * 8;
+  if (p.dim == 2)
+    k_mlp_sample<2><<<blocks, threads, 0, st>>>(p, n_max, seed, attempts, cf, stencils, targets,
+                                               count);
+  else
+    k_mlp_sample<3><<<blocks, threads, 0, st>>>(p, n_max, seed, attempts, cf, stencils, targets,
+                                               count);
+  return cudaGetLastError();
+}
 
 cudaError_t fp32_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   using namespace fp32_ns;
-  if (p.dim == 2)
+  if (p.dim == 2) {
+    if (p.scheme == IBFSA_MLP_TENO5) return run_stage<2, IBFSA_MLP_TENO5>(p, s, st);
     return p.scheme == IBFSA_TENO5 ? run_stage<2, IBFSA_TENO5>(p, s, st)
                                    : run_stage<2, IBFSA_WENO5JS>(p, s, st);
+  }
+  if (p.scheme == IBFSA_MLP_TENO5) return run_stage<3, IBFSA_MLP_TENO5>(p, s, st);
   return p.scheme == IBFSA_TENO5 ? run_stage<3, IBFSA_TENO5>(p, s, st)
                                  : run_stage<3, IBFSA_WENO5JS>(p, s, st);
 }

@@ -35,7 +35,7 @@ EXPORTS = (
     "ibfsa_max_wavespeed", "ibfsa_probe", "ibfsa_get_status", "ibfsa_last_error",
     "ibfsa_profile_enable", "ibfsa_profile_read", "ibfsa_rhs_noalloc",
     "ibfsa_mlp_state_bytes", "ibfsa_mlp_init", "ibfsa_mlp_train_step", "ibfsa_mlp_read",
-    "ibfsa_mlp_eval",
+    "ibfsa_mlp_eval", "ibfsa_set_mlp", "ibfsa_mlp_stats", "ibfsa_mlp_sample",
 )
 MLP_NPARAM = 2403
 
@@ -106,6 +106,10 @@ def lib():
         L.ibfsa_mlp_train_step.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.c_int, _P]
         L.ibfsa_mlp_read.argtypes = [_P, _P, _P, _P, _P]
         L.ibfsa_mlp_eval.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+        L.ibfsa_set_mlp.argtypes = [_P, _P]
+        L.ibfsa_mlp_stats.argtypes = [_P, _P]
+        L.ibfsa_mlp_sample.argtypes = [_P, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _P, _P,
+                                       _P]
         L.ibfsa_rhs_noalloc.argtypes = [D, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]
         _lib = L
     return _lib
@@ -256,6 +260,22 @@ def ibfsa_mlp_eval(state: int, n: int, stencils: int, targets: int = 0, face: in
     _check(lib().ibfsa_mlp_eval(_P(state), int(n), _P(stencils), _P(targets or None),
                                 _P(face or None), _P(omega or None), _P(loss or None),
                                 _P(stream)))
+
+
+def ibfsa_set_mlp(g, state: int):
+    _check(lib().ibfsa_set_mlp(g, _P(state)))
+
+
+def ibfsa_mlp_stats(g):
+    c = (ctypes.c_ulonglong * 2)()
+    _check(lib().ibfsa_mlp_stats(g, ctypes.cast(c, _P)))
+    return int(c[0]), int(c[1])
+
+
+def ibfsa_mlp_sample(g, n_max: int, seed: int, attempts: int, stencils: int, targets: int,
+                     count: int):
+    _check(lib().ibfsa_mlp_sample(g, int(n_max), int(seed), int(attempts), _P(stencils),
+                                  _P(targets), _P(count)))
 
 
 class MLP:
