@@ -243,17 +243,30 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
-def make_grid(ib, args, precision, strict=False):
+def make_grid(ib, args, precision, strict=False, scheme=None, state="pulse", mlp=None):
     n = args.n
-    scheme = W.TENO5 if args.scheme == "teno5" else W.WENO5JS
+    if scheme is None:
+        scheme = W.TENO5 if args.scheme == "teno5" else W.WENO5JS
     spec, dt = workload_spec(n, args.markers, scheme)
     spec.precision = precision
     X, U, dS = W.fibonacci_sphere(args.markers, 0.5)
     probes, _, _ = W.fibonacci_sphere(1000, 6.0 * n / 512.0)
     g = ib.Grid(spec, strict=strict, max_probes=probes.shape[1])
-    g.set_state(W.gaussian_pulse_state_torch(spec, (2.0 * n / 512.0, 0.0, 0.0)))
+    if mlp is not None:
+        ib.ibfsa_set_mlp(g.h, mlp.ptr)
+    if state == "pulse":
+        g.set_state(W.gaussian_pulse_state_torch(spec, (2.0 * n / 512.0, 0.0, 0.0)))
+    else:
+        g.set_state(W.stress_state_torch(spec))
     g.set_markers(X, U, dS)
     return g, spec, dt, (X, U, dS), probes
+
+
+def learned_weights(ib):
+    """the committed trained parameters of the learned weights"""
+    path = os.path.join(ROOT, "paper_1905_00182_gb300", "mlp_weights.npz")
+    params = np.load(path)["params"]
+    return ib.MLP(params)
 
 
 def timed_steps(ib, g, dt, steps, barrier, profile):
@@ -352,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
     # the plain FP64 form on the same workload: its throughput, and the pressure-field error
     # of the FP32 form after the same number of steps from the same initial state
     compare = None
+    p64_keep = None
     if fp32 and args.compare:
         g64, _, _, _, _ = make_grid(ib, args, W.FP64)
         k64 = 2
@@ -362,6 +376,7 @@ def run_ours(args, rank, world, local_rank):
         p64 = pressure(spec, g64.get_state())
         pinf = 1.0 / spec.gamma
         err = float(torch.linalg.vector_norm(p_head - p64) / torch.linalg.vector_norm(p64 - pinf))
+        p64_keep = p64
         v64 = spec.cells * 3 * k64 * world / (ms64 * 1e-3)
         compare = {"fp64_value": v64, "fp64_ms_per_step": ms64 / k64,
                    "fp32_speedup_vs_fp64": value / v64,
@@ -369,8 +384,50 @@ def run_ours(args, rank, world, local_rank):
                    "fp64_kernel_ms_per_step": {k: v["ms"] / k64 for k, v in prof64.items()
                                                if v["timed"]}}
         g64.close()
-        del g64, p_head, p64
+        del g64, p_head
         torch.cuda.empty_cache()
+
+    # the learned-weight form (TENO5 fallback) on the same workload, and on the stress state
+    # (perturbations everywhere) next to the FP32 TENO5 form; fallback rate = share of
+    # reconstructions that used TENO5's weights
+    learned = None
+    if fp32 and args.compare and args.scheme == "teno5":
+        net = learned_weights(ib)
+        k_l = 3
+        out_l = {}
+        for state in ("pulse", "stress"):
+            gl, _, _, _, _ = make_grid(ib, args, W.FP32_PERTURB, scheme=W.MLP_TENO5,
+                                       state=state, mlp=net)
+            for _ in range(args.warmup):
+                gl.rk3_step(dt, 1)
+            ib.ibfsa_mlp_stats(gl.h)
+            msl, _ = timed_steps(ib, gl, dt, k_l, barrier, profile=False)
+            used, seen = ib.ibfsa_mlp_stats(gl.h)
+            out_l[state] = {"value": spec.cells * 3 * k_l * world / (max_over_ranks(msl) * 1e-3),
+                            "ms_per_step": msl / k_l,
+                            "fallback_rate": 1.0 - used / max(seen, 1)}
+            if state == "pulse":
+                for _ in range(steps_done - args.warmup - k_l):
+                    gl.rk3_step(dt, 1)
+                p_l = pressure(spec, gl.get_state())
+                out_l[state]["vs_fp64_pressure_rel_l2"] = float(
+                    torch.linalg.vector_norm(p_l - p64_keep) /
+                    torch.linalg.vector_norm(p64_keep - 1.0 / spec.gamma)) if p64_keep is not None else None
+                del p_l
+            gl.close()
+            del gl
+            torch.cuda.empty_cache()
+        gs, _, _, _, _ = make_grid(ib, args, W.FP32_PERTURB, state="stress")
+        for _ in range(args.warmup):
+            gs.rk3_step(dt, 1)
+        mss, _ = timed_steps(ib, gs, dt, k_l, barrier, profile=False)
+        gs.close()
+        del gs
+        torch.cuda.empty_cache()
+        learned = {"pulse": out_l["pulse"], "stress": out_l["stress"],
+                   "fp32_teno5_stress_value": spec.cells * 3 * k_l * world /
+                   (max_over_ranks(mss) * 1e-3),
+                   "weights": "paper_1905_00182_gb300/mlp_weights.npz"}
 
     if rank != 0:
         if dist is not None:
@@ -416,6 +473,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if compare is not None:
         out["forms"] = compare
+        if learned is not None:
+            out["forms"]["learned"] = learned
     if e2e is not None:
         out["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:

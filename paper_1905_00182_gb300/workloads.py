@@ -319,3 +319,41 @@ def mlp_init_params(seed: int = 0) -> np.ndarray:
     parts[6] = parts[6] * 0.1
     parts[7] = np.log(np.array([0.1, 0.6, 0.3]))
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def stress_state_torch(spec: GridSpec, seed: int = 1, amp: float = 1e-3, step: float = 0.1,
+                       device="cuda"):
+    """The rest state plus seeded smooth random modes of amplitude `amp` in every primitive and a
+    planar density step of relative size `step` at mid-x (a contact discontinuity), generated in
+    device memory: every cell carries a perturbation, so the non-linear weights (and the learned
+    form's network) are exercised everywhere instead of only around a pulse."""
+    import torch
+    f64 = torch.float64
+    rnd = splitmix64(seed, 8 * (spec.dim + 2) * 2)
+    xs = [(torch.arange(spec.n[a], dtype=f64, device=device) + 0.5) / spec.n[a]
+          for a in range(spec.dim)]
+    Q = torch.zeros(spec.shape(), dtype=f64, device=device)
+    it = 0
+    prim = []
+    for v in range(spec.dim + 2):
+        kk = [int(rnd[it + a] * 3) + 1 for a in range(spec.dim)]
+        ph = 2.0 * math.pi * rnd[it + spec.dim]
+        it += spec.dim + 1
+        prim.append((kk, ph))
+    for k in range(spec.n[2]):
+        def field(kk, ph):
+            arg = 2.0 * math.pi * (kk[0] * xs[0][None, :] + kk[1] * xs[1][:, None])
+            if spec.dim == 3:
+                arg = arg + 2.0 * math.pi * kk[2] * xs[2][k]
+            return amp * torch.sin(arg + ph)
+        rho = 1.0 + field(*prim[0])
+        rho = rho * torch.where(xs[0][None, :] > 0.5, 1.0 + step, 1.0)
+        vel = [field(*prim[1 + a]) for a in range(spec.dim)]
+        p = 1.0 / spec.gamma + field(*prim[spec.dim + 1])
+        Q[0, k] = rho
+        ke = torch.zeros_like(rho)
+        for a in range(spec.dim):
+            Q[1 + a, k] = rho * vel[a]
+            ke = ke + 0.5 * rho * vel[a] * vel[a]
+        Q[spec.nv - 1, k] = p / (spec.gamma - 1.0) + ke
+    return Q
