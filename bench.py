@@ -114,6 +114,27 @@ def flops_per_cell(scheme, dim=3, viscous=True):
     return per
 
 
+def bytes_per_cell(precision, dim=3, viscous=True):
+    """Algorithmic DRAM bytes per cell and stage of each kernel class (averaged over the three
+    stages; padded arrays counted per interior cell with their ghost overhead at 512^3)."""
+    nv = dim + 2
+    pad_ratio = (520 / 512) ** 3
+    if precision == "fp32":
+        prim = 4 * (nv + dim + 1)                     # padded q' and primitive perturbations
+        inc = 4 * nv * 2 / 3                          # stage increments read in stages 2 and 3
+        return {"pad": 4 * nv + inc + prim * pad_ratio,
+                "conv_x": prim + 4 * nv, "conv_y": prim + 8 * nv, "conv_z": prim + 8 * nv,
+                "visc_flux": (4 * dim + 4 * dim * (dim + 1)) if viscous else 0,
+                "finish": 4 * nv + (4 * dim * (dim + 1) if viscous else 0) + inc +
+                          (4 * nv * 2 + (8 * nv * 2 + 4 * nv)) / 3}
+    prim = 8 * (nv + dim + 1)
+    return {"pad": 8 * nv + prim * pad_ratio, "conv_x": prim + 8 * nv, "conv_y": prim + 16 * nv,
+            "conv_z": prim + 16 * nv,
+            "visc_flux": (8 * dim + 8 * dim * (dim + 1)) if viscous else 0,
+            "visc_div": (8 * dim * (dim + 1) + 16 * (dim + 1)) if viscous else 0,
+            "finish": 8 * nv + (8 * nv * 3 + 8 * nv * 4 + 8 * nv * 4) / 3}
+
+
 def bytes_per_cell_stage(dim=3):
     # fused minimum: stage 1 reads Qn and writes Q1; stages 2, 3 read Qn and Qs, write Qo
     nv = dim + 2
@@ -436,11 +457,8 @@ def run_ours(args, rank, world, local_rank):
 
     peaks, peak_kind = measured_peaks()
     fl = flops_per_cell(args.scheme)
-    classes = {k: v for k, v in prof.items() if v["timed"] > 0}
-    dom = max(classes, key=lambda k: classes[k]["ms"])
-    avg_ms = classes[dom]["ms"] / classes[dom]["timed"]
-    per_launch_flops = fl.get(dom, 0.0)
-    achieved = per_launch_flops * spec.cells / (avg_ms * 1e-3) / 1e12
+    fl["finish"] = fl["finish"] + (fl["visc_div"] if fp32 else 0)  # FP32 finish fuses the divergence
+    by = bytes_per_cell(args.precision)
     sm_mhz = clk["sm_mhz"] or 2070.0
     if fp32:
         peak_tf = FP32_FLOP_PER_CLK_PER_SM * SMS * sm_mhz * 1e6 / 1e12
@@ -448,14 +466,31 @@ def run_ours(args, rank, world, local_rank):
     else:
         peak_tf = FP64_FLOP_PER_CLK_PER_SM * SMS * sm_mhz * 1e6 / 1e12
         note = "FP64 pipe: 4 flop/clk/SM x 152 SMs x median SM clock of the run"
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved / peak_tf,
-                "traffic": ncu_traffic(dom, args.precision), "peak_note": note,
-                "flops_per_cell": per_launch_flops, "avg_launch_ms": avg_ms}
+    hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+
+    def kernel_roofline(k):
+        v = prof[k]
+        avg_ms = v["ms"] / v["timed"]
+        f_tf = fl.get(k, 0.0) * spec.cells / (avg_ms * 1e-3) / 1e12
+        b_gbs = by.get(k, 0.0) * spec.cells / (avg_ms * 1e-3) / 1e9
+        # the binding resource is the one the kernel's algorithmic work fills the most
+        if f_tf / peak_tf >= b_gbs / hbm_peak:
+            return {"bound": "alu", "kernel": k, "achieved": f_tf, "peak": peak_tf,
+                    "unit": "TFLOP/s", "frac": f_tf / peak_tf, "peak_note": note,
+                    "flops_per_cell": fl.get(k, 0.0), "avg_launch_ms": avg_ms}
+        return {"bound": "hbm", "kernel": k, "achieved": b_gbs, "peak": hbm_peak,
+                "unit": "GB/s", "frac": b_gbs / hbm_peak, "peak_note": f"{peak_kind} copy bandwidth",
+                "bytes_per_cell": by.get(k, 0.0), "avg_launch_ms": avg_ms}
+
+    classes = {k: v for k, v in prof.items() if v["timed"] > 0}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    roofline = kernel_roofline(dom)
+    roofline["traffic"] = ncu_traffic(dom, args.precision)
+    kernel_rooflines = {k: {kk: kernel_roofline(k)[kk] for kk in ("bound", "frac", "avg_launch_ms")}
+                        for k in classes if k in fl or k in by}
     stage_ms = ms / world / (3 * args.steps)
     bpc = bytes_per_cell_stage()
     hbm_achieved = bpc * spec.cells / (stage_ms * 1e-3) / 1e9
-    hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
     out = {
         "metric": "stage-RHS cell-updates/s", "value": value, "unit": "cell-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -467,6 +502,7 @@ def run_ours(args, rank, world, local_rank):
                          "frac": hbm_achieved / hbm_peak, "bytes_per_cell_stage": bpc,
                          "peak_kind": peak_kind},
         "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["timed"]},
+        "kernel_rooflines": kernel_rooflines,
         "flops_per_cell_stage": fl["total"],
         "alu_frac_whole_stage": fl["total"] * spec.cells / (stage_ms * 1e-3) / 1e12 / peak_tf,
         "clocks": clk, "gpu_launches": gpu_launches, "device_status": status,

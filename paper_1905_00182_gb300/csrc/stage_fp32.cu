@@ -168,10 +168,39 @@ __device__ __forceinline__ float teno5(const Plan &tw, float a, float b, float c
   return w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
 }
 
+// Smoothness indicators only (the candidates are not needed on the smooth path).
+__device__ __forceinline__ void indicators(float a, float b, float c, float d, float e,
+                                           float &b0, float &b1, float &b2) {
+  const float k13 = 13.f / 12.f;
+  float t, u;
+  t = a - 2.f * b + c; u = a - 4.f * b + 3.f * c; b0 = k13 * t * t + 0.25f * u * u;
+  t = b - 2.f * c + d; u = b - d;                 b1 = k13 * t * t + 0.25f * u * u;
+  t = c - 2.f * d + e; u = 3.f * c - 4.f * d + e; b2 = k13 * t * t + 0.25f * u * u;
+}
+
+// TENO5 keeps every stencil when tau5 <= 4 (min beta + eps): then each gamma_k lies in
+// [1, 5^6] and chi_k >= 1/(3 5^6) = 2.1e-5 > C_T = 1e-5.  The reconstruction is then the
+// optimal linear combination (2a - 13b + 47c + 27d - 3e)/60, without divisions or powers.
+__device__ __forceinline__ bool teno_all_kept(float b0, float b1, float b2) {
+  return fabsf(b0 - b2) <= 4.f * (fminf(b0, fminf(b1, b2)) + 1e-30f);
+}
+
+__device__ __forceinline__ float linear5(float a, float b, float c, float d, float e) {
+  return (2.f * a - 13.f * b + 47.f * c + 27.f * d - 3.f * e) * (1.f / 60.f);
+}
+
+__device__ __forceinline__ float teno5_fast(const Plan &tw, float a, float b, float c, float d,
+                                            float e) {
+  float b0, b1, b2;
+  indicators(a, b, c, d, e, b0, b1, b2);
+  if (teno_all_kept(b0, b1, b2)) return linear5(a, b, c, d, e);
+  return teno5(tw, a, b, c, d, e);
+}
+
 template <int SCHEME>
 __device__ __forceinline__ float recon(const Plan &tw, float a, float b, float c, float d,
                                        float e) {
-  if constexpr (SCHEME == IBFSA_TENO5) return teno5(tw, a, b, c, d, e);
+  if constexpr (SCHEME == IBFSA_TENO5) return teno5_fast(tw, a, b, c, d, e);
   else return weno5js(a, b, c, d, e);
 }
 
@@ -273,7 +302,7 @@ __device__ __forceinline__ float recon_mlp(const Plan &p, const unsigned char *i
                                            float a, float b, float c, float d, float e,
                                            unsigned &used, unsigned &seen) {
   Cands k = candidates(a, b, c, d, e);
-  int mask = teno_mask(k);
+  int mask = teno_all_kept(k.b0, k.b1, k.b2) ? 7 : teno_mask(k);
   float v[5] = {a, b, c, d, e}, x[5];
   float amp = mlp::normalise(v, x);
   bool elig = valid && mask == 7 && amp > p.mlp_floor;
@@ -497,31 +526,6 @@ __global__ void __launch_bounds__(THREADS) k_visc_flux32(Plan p) {
   }
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(THREADS) k_visc_div32(Plan p) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.N) return;
-  int i = (int)(t % p.n[0]);
-  long long r = t / p.n[0];
-  int j = (int)(r % p.n[1]);
-  int k = (int)(r / p.n[1]);
-  long long b = ((long long)(DIM > 2 ? k + 2 : k) * p.B[1] + (DIM > 1 ? j + 2 : j)) * p.B[0] + (i + 2);
-  long long stride[3] = {1, p.B[0], (long long)p.B[0] * p.B[1]};
-  const float inv_Re = p.inv_Re32;
-#pragma unroll
-  for (int fc = 0; fc <= DIM; fc++) {
-    float sum = 0.f;
-#pragma unroll
-    for (int a = 0; a < DIM; a++) {
-      const float *F = p.V32 + (long long)(a * (DIM + 1) + fc) * p.NB + b;
-      long long st = stride[a];
-      sum += d4f(F[-2 * st], F[-st], F[st], F[2 * st], p.inv_h12_32[a]);
-    }
-    long long o = (long long)(fc + 1) * p.N + t;
-    p.L32[o] += sum * inv_Re;
-  }
-}
-
 // ------------------------------------------------------------------------------------------
 // immersed boundary in FP64 from the FP64 stage state
 // ------------------------------------------------------------------------------------------
@@ -599,7 +603,7 @@ __global__ void k_spread32(Plan p, const double *__restrict__ Qn, const float *_
 //   mode 0: L out (FP64 copy);  mode 1: dout = b (din + dt L);
 //   mode 2: Qn += b (din + dt L) in FP64 and qn32 = (float)(Qn - q_inf)
 // ------------------------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, bool VISC>
 __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__restrict__ din,
                                                       float *__restrict__ dout, double *Qn,
                                                       double *__restrict__ Lout, float Bc,
@@ -610,6 +614,26 @@ __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__res
   float Lc[NV];
 #pragma unroll
   for (int c = 0; c < NV; c++) Lc[c] = p.L32[c * p.N + t];
+  if constexpr (VISC) {
+    // viscous divergence (1/Re) sum_a D4_a [0, tau_{.a}, b_a], fused here to save a pass over L
+    int i = (int)(t % p.n[0]);
+    long long r = t / p.n[0];
+    int j = (int)(r % p.n[1]);
+    int k = (int)(r / p.n[1]);
+    long long bb = ((long long)(DIM > 2 ? k + 2 : k) * p.B[1] + (DIM > 1 ? j + 2 : j)) * p.B[0] + (i + 2);
+    long long stride[3] = {1, p.B[0], (long long)p.B[0] * p.B[1]};
+#pragma unroll
+    for (int fc = 0; fc <= DIM; fc++) {
+      float sum = 0.f;
+#pragma unroll
+      for (int a = 0; a < DIM; a++) {
+        const float *F = p.V32 + (long long)(a * (DIM + 1) + fc) * p.NB + bb;
+        long long st = stride[a];
+        sum += d4f(F[-2 * st], F[-st], F[st], F[2 * st], p.inv_h12_32[a]);
+      }
+      Lc[fc + 1] += sum * p.inv_Re32;
+    }
+  }
   if (p.sponge_cells > 0) {
     int I[3];
     I[0] = (int)(t % p.n[0]);
@@ -758,10 +782,6 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
     k_visc_flux32<DIM><<<blocks_for(p.NB, THREADS), THREADS, 0, st>>>(p);
     prof_end(pr, K_VISC_FLUX, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    prof_begin(pr, st);
-    k_visc_div32<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p);
-    prof_end(pr, K_VISC_DIV, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (p.nm > 0) {
     constexpr int S = DIM > 2 ? 64 : 16;
@@ -772,8 +792,12 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   }
   int mode = !advance ? 0 : (s.stage < 2 ? 1 : 2);
   prof_begin(pr, st);
-  k_finish32<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(
-      p, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
+  if (p.Re > 0.0)
+    k_finish32<DIM, true><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(
+        p, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
+  else
+    k_finish32<DIM, false><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(
+        p, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
   prof_end(pr, K_FINISH, st);
   return cudaGetLastError();
 }

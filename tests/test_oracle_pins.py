@@ -323,3 +323,22 @@ def test_penalty_force_law_and_spreading_in_rhs():
     assert np.allclose(L[2].sum() * h2, -(F[1] * dS).sum(), atol=1e-14)
     assert np.all(L[0] == 0.0)
     assert np.all(L[3] == 0.0)  # u = 0 everywhere: the source does no work
+
+
+def test_teno5_keeps_all_stencils_when_tau_is_small_against_the_smoothest():
+    # premise of the kernels' shortcut: tau5 <= 4 (min beta + eps) implies every gamma_k is in
+    # [1, 5^6], chi_k >= 1/(3 5^6) > C_T, so TENO5 returns the optimal linear combination
+    rng = np.random.default_rng(9)
+    hits = 0
+    for _ in range(20000):
+        v = np.cumsum(rng.standard_normal(5) * rng.choice([1e-6, 1e-3, 1.0, 10.0]))
+        v += rng.standard_normal(5) * rng.choice([0.0, 1e-8, 1e-3])
+        a, b, c, d, e = v
+        b0 = 13 / 12 * (a - 2 * b + c) ** 2 + 0.25 * (a - 4 * b + 3 * c) ** 2
+        b1 = 13 / 12 * (b - 2 * c + d) ** 2 + 0.25 * (b - d) ** 2
+        b2 = 13 / 12 * (c - 2 * d + e) ** 2 + 0.25 * (3 * c - 4 * d + e) ** 2
+        if abs(b0 - b2) <= 4.0 * (min(b0, b1, b2) + 1e-40):
+            hits += 1
+            lin = (2 * a - 13 * b + 47 * c + 27 * d - 3 * e) / 60
+            assert abs(O.teno5(v) - lin) <= 1e-13 * (np.max(np.abs(v)) + 1e-300)
+    assert hits > 1000
