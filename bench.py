@@ -320,6 +320,24 @@ def pressure(spec, Q):
     return (spec.gamma - 1.0) * (Q[nv - 1] - 0.5 * ke)
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ms_local, units_per_rank, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the units all ranks processed over the
+    slowest rank's time.  Returns (value per second, max ms)."""
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    ms = max_over_ranks(ms_local, dist, device)
+    return units_per_rank * world / (ms * 1e-3), ms
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1905_00182_gb300 import ibfsa as ib
@@ -334,12 +352,8 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x):
+        return max_over_ranks(x, dist, "cuda")
 
     fp32 = args.precision == "fp32"
     prec = W.FP32_PERTURB if fp32 else W.FP64
@@ -351,9 +365,7 @@ def run_ours(args, rank, world, local_rank):
     ms, prof = timed_steps(ib, g, dt, args.steps, barrier, profile=True)
     clk = clocks.stop()
     status = g.status()
-    ms = max_over_ranks(ms)
-    units = spec.cells * 3 * args.steps * world
-    value = units / (ms * 1e-3)
+    value, ms = job_throughput(ms, spec.cells * 3 * args.steps, dist, "cuda")
     steps_done = args.warmup + args.steps
     p_head = pressure(spec, g.get_state()) if (fp32 and args.compare) else None
 
@@ -373,7 +385,7 @@ def run_ours(args, rank, world, local_rank):
             ib.ibfsa_set_markers(g.h, X.shape[1], Xh.data_ptr(), Uh.data_ptr(), dSh.data_ptr(), 0)
             ib.ibfsa_rk3_step(g.h, dt, 1)
             ib.ibfsa_probe(g.h, probes.shape[1], xph.data_ptr(), outh.data_ptr())  # synchronises
-        el = max_over_ranks(time.perf_counter() - t0)
+        el = max_ranks(time.perf_counter() - t0)
         nm = X.shape[1]
         e2e = {"value": spec.cells * 3 * k_e2e * world / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": 8 * (2 * 3 * nm + nm + 3 * probes.shape[1]),
@@ -393,7 +405,7 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(steps_done - k64):
             g64.rk3_step(dt, 1)
         ms64, prof64 = timed_steps(ib, g64, dt, k64, barrier, profile=True)
-        ms64 = max_over_ranks(ms64)
+        ms64 = max_ranks(ms64)
         p64 = pressure(spec, g64.get_state())
         pinf = 1.0 / spec.gamma
         err = float(torch.linalg.vector_norm(p_head - p64) / torch.linalg.vector_norm(p64 - pinf))
@@ -424,7 +436,7 @@ def run_ours(args, rank, world, local_rank):
             ib.ibfsa_mlp_stats(gl.h)
             msl, _ = timed_steps(ib, gl, dt, k_l, barrier, profile=False)
             used, seen = ib.ibfsa_mlp_stats(gl.h)
-            out_l[state] = {"value": spec.cells * 3 * k_l * world / (max_over_ranks(msl) * 1e-3),
+            out_l[state] = {"value": spec.cells * 3 * k_l * world / (max_ranks(msl) * 1e-3),
                             "ms_per_step": msl / k_l,
                             "fallback_rate": 1.0 - used / max(seen, 1)}
             if state == "pulse":
@@ -447,7 +459,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         learned = {"pulse": out_l["pulse"], "stress": out_l["stress"],
                    "fp32_teno5_stress_value": spec.cells * 3 * k_l * world /
-                   (max_over_ranks(mss) * 1e-3),
+                   (max_ranks(mss) * 1e-3),
                    "weights": "paper_1905_00182_gb300/mlp_weights.npz"}
 
     if rank != 0:
