@@ -122,10 +122,11 @@ def bytes_per_cell(precision, dim=3, viscous=True):
     if precision == "fp32":
         prim = 4 * (nv + dim + 1)                     # padded q' and primitive perturbations
         inc = 4 * nv * 2 / 3                          # stage increments read in stages 2 and 3
+        # 3D with viscosity: the finish pass also forms the viscous fluxes from the padded
+        # velocity perturbations (read once), so no viscous-flux arrays go to DRAM
         return {"pad": 4 * nv + inc + prim * pad_ratio,
                 "conv_x": prim + 4 * nv, "conv_y": prim + 8 * nv, "conv_z": prim + 8 * nv,
-                "visc_flux": (4 * dim + 4 * dim * (dim + 1)) if viscous else 0,
-                "finish": 4 * nv + (4 * dim * (dim + 1) if viscous else 0) + inc +
+                "finish": 4 * nv + (4 * dim if viscous else 0) + inc +
                           (4 * nv * 2 + (8 * nv * 2 + 4 * nv)) / 3}
     prim = 8 * (nv + dim + 1)
     return {"pad": 8 * nv + prim * pad_ratio, "conv_x": prim + 8 * nv, "conv_y": prim + 16 * nv,

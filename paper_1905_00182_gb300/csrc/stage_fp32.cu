@@ -679,6 +679,191 @@ __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__res
   if (bad) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
 }
 
+// 3D viscous term + finish, marching along z.  A 32 x 8 block of threads owns 32 x 8 columns
+// and walks a z-chunk: velocity perturbations of five planes (x, y halo 4) sit in a shared-
+// memory ring; at each plane c the 9 gradients are evaluated at the block's cells and at the
+// x/y halo points the x/y divergence needs, giving F_v,x and F_v,y (shared memory, divergence
+// taken at once) and F_v,z (a five-plane register window per thread); two planes later the
+// z-divergence completes the cell: L += (1/Re) sum_a D4_a F_v,a, sponge, RK update.
+namespace vm {
+constexpr int TX = 32, TY = 8, ZC = 64;        // block columns, z-chunk
+constexpr int SX = TX + 8, SY = TY + 8;        // staged plane (halo 4)
+constexpr int PX = TX + 4, PY = TY + 4;        // flux points (halo 2)
+constexpr size_t SMEM = sizeof(float) * (5 * 3 * SX * SY + 4 * PX * TY + 4 * TX * PY);
+}  // namespace vm
+
+__global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *__restrict__ din,
+                                                          float *__restrict__ dout, double *Qn,
+                                                          double *__restrict__ Lout, float Bc,
+                                                          float dt, int mode) {
+  using namespace vm;
+  extern __shared__ float smm[];
+  float *ring = smm;                              // [5][3][SY][SX]
+  float *fx = smm + 5 * 3 * SX * SY;              // F_v,x at [TY][PX], 4 components
+  float *fy = fx + 4 * PX * TY;                   // F_v,y at [PY][TX], 4 components
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, zs = blockIdx.z * ZC;
+  const int ze = min(zs + ZC, p.n[2]);
+  const int X = x0 + tx, Y = y0 + ty;
+  const bool own = X < p.n[0] && Y < p.n[1];
+  Free fs = free_stream(p);
+  const float ih[3] = {p.inv_h12_32[0], p.inv_h12_32[1], p.inv_h12_32[2]};
+  const int PLANE = 3 * SX * SY;
+
+  auto stage = [&](int z) {  // plane z (ghost range -4 .. n+3) into ring slot z mod 5
+    float *dst = ring + ((z + 8) % 5) * PLANE;
+    for (int e = threadIdx.x; e < SX * SY; e += THREADS) {
+      int sx = e % SX, sy = e / SX;
+      int gx = min(x0 - 4 + sx, p.n[0] + 3), gy = min(y0 - 4 + sy, p.n[1] + 3);
+      long long s = pad_index(p, gx, gy, z);
+#pragma unroll
+      for (int c = 0; c < 3; c++) dst[c * SX * SY + e] = p.Wp32[c * p.NP + s];
+    }
+  };
+  // gradients g[i][j] = du_i/dx_j at staged position (sx, sy) of plane c
+  auto grads = [&](int c, int sx, int sy, float g[3][3], float u[3]) {
+    const float *pl[5];
+#pragma unroll
+    for (int o = 0; o < 5; o++) pl[o] = ring + ((c - 2 + o + 8) % 5) * PLANE;
+    int e = sy * SX + sx;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const float *m = pl[2] + i * SX * SY + e;
+      u[i] = m[0];
+      g[i][0] = d4f(m[-2], m[-1], m[1], m[2], ih[0]);
+      g[i][1] = d4f(m[-2 * SX], m[-SX], m[SX], m[2 * SX], ih[1]);
+      g[i][2] = d4f(pl[0][i * SX * SY + e], pl[1][i * SX * SY + e], pl[3][i * SX * SY + e],
+                    pl[4][i * SX * SY + e], ih[2]);
+    }
+  };
+  // viscous flux of direction a: [tau_0a, tau_1a, tau_2a, b_a]
+  auto vflux = [&](int a, const float g[3][3], const float u[3], float f[4]) {
+    float div = g[0][0] + g[1][1] + g[2][2];
+    float b = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      float tau = g[i][a] + g[a][i];
+      if (i == a) tau -= (2.f / 3.f) * div;
+      f[i] = tau;
+      b += (fs.u[i] + u[i]) * tau;
+    }
+    f[3] = b;
+  };
+
+  float fz[5][4];   // F_v,z of this column at planes c-4 .. c
+  float pxy[3][4];  // x/y divergence of planes c-2 .. c
+#pragma unroll
+  for (int o = 0; o < 5; o++)
+#pragma unroll
+    for (int k = 0; k < 4; k++) fz[o][k] = 0.f;
+#pragma unroll
+  for (int o = 0; o < 3; o++)
+#pragma unroll
+    for (int k = 0; k < 4; k++) pxy[o][k] = 0.f;
+
+  for (int z = zs - 4; z < zs; z++) stage(z);
+  for (int c = zs - 2; c < ze + 2; c++) {
+    stage(c + 2);
+    __syncthreads();
+    // own cell: all three fluxes; halo points: F_v,x (x offsets -2,-1,32,33) or F_v,y
+    {
+      float g[3][3], u[3], f[4];
+      grads(c, tx + 4, ty + 4, g, u);
+      vflux(0, g, u, f);
+#pragma unroll
+      for (int k = 0; k < 4; k++) fx[(k * TY + ty) * PX + tx + 2] = f[k];
+      vflux(1, g, u, f);
+#pragma unroll
+      for (int k = 0; k < 4; k++) fy[(k * PY + ty + 2) * TX + tx] = f[k];
+      vflux(2, g, u, f);
+#pragma unroll
+      for (int o = 0; o < 4; o++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) fz[o][k] = fz[o + 1][k];
+#pragma unroll
+      for (int k = 0; k < 4; k++) fz[4][k] = f[k];
+    }
+    for (int e = threadIdx.x; e < 4 * TY + 4 * TX; e += THREADS) {
+      float g[3][3], u[3], f[4];
+      if (e < 4 * TY) {  // x-halo point
+        int r = e / 4, h = e % 4, px = h < 2 ? h : TX + h;  // 0,1,TX+2,TX+3
+        grads(c, px + 2, r + 4, g, u);
+        vflux(0, g, u, f);
+#pragma unroll
+        for (int k = 0; k < 4; k++) fx[(k * TY + r) * PX + px] = f[k];
+      } else {           // y-halo point
+        int e2 = e - 4 * TY, col = e2 % TX, h = e2 / TX, py = h < 2 ? h : TY + h;
+        grads(c, col + 4, py + 2, g, u);
+        vflux(1, g, u, f);
+#pragma unroll
+        for (int k = 0; k < 4; k++) fy[(k * PY + py) * TX + col] = f[k];
+      }
+    }
+    __syncthreads();
+    // x/y divergence at this column's cell of plane c
+#pragma unroll
+    for (int o = 0; o < 2; o++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) pxy[o][k] = pxy[o + 1][k];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const float *Fx = fx + (k * TY + ty) * PX + tx + 2;
+      const float *Fy = fy + (k * PY + ty + 2) * TX + tx;
+      pxy[2][k] = d4f(Fx[-2], Fx[-1], Fx[1], Fx[2], ih[0]) +
+                  d4f(Fy[-2 * TX], Fy[-TX], Fy[TX], Fy[2 * TX], ih[1]);
+    }
+    // plane d = c - 2 is complete: z-divergence, sponge, RK update
+    int d = c - 2;
+    if (own && d >= zs && d < ze) {
+      long long t = int_index(p, X, Y, d);
+      float Lc[5];
+#pragma unroll
+      for (int cc = 0; cc < 5; cc++) Lc[cc] = p.L32[cc * p.N + t];
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        Lc[k + 1] += (pxy[0][k] + d4f(fz[0][k], fz[1][k], fz[3][k], fz[4][k], ih[2])) * p.inv_Re32;
+      if (p.sponge_cells > 0) {
+        int I[3] = {X, Y, d};
+        int S = p.sponge_cells, nmin = 1 << 30;
+#pragma unroll
+        for (int a = 0; a < 3; a++) nmin = min(nmin, min(I[a], p.n[a] - 1 - I[a]));
+        if (nmin < S) {
+          float rr = (float)(S - nmin) / (float)S;
+          float sig = (float)p.sponge_sigma * rr * rr * rr;
+#pragma unroll
+          for (int cc = 0; cc < 5; cc++)
+            Lc[cc] -= sig * (p.qn32[cc * p.N + t] + (din ? din[cc * p.N + t] : 0.f));
+        }
+      }
+      if (mode == 0) {
+#pragma unroll
+        for (int cc = 0; cc < 5; cc++) Lout[cc * p.N + t] = (double)Lc[cc];
+      } else {
+        bool bad = false;
+        float inc[5];
+#pragma unroll
+        for (int cc = 0; cc < 5; cc++) {
+          inc[cc] = Bc * ((din ? din[cc * p.N + t] : 0.f) + dt * Lc[cc]);
+          bad |= !isfinite(inc[cc]);
+        }
+        if (mode == 1) {
+#pragma unroll
+          for (int cc = 0; cc < 5; cc++) dout[cc * p.N + t] = inc[cc];
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < 5; cc++) {
+            double qv = Qn[cc * p.N + t] + (double)inc[cc];
+            Qn[cc * p.N + t] = qv;
+            p.qn32[cc * p.N + t] = (float)(qv - p.qinf[cc]);
+          }
+        }
+        if (bad) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
+      }
+    }
+    __syncthreads();  // the ring slot of plane c - 2 is restaged next iteration
+  }
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(THREADS) k_refresh32(Plan p, const double *__restrict__ Q) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -777,7 +962,7 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
     prof_end(pr, K_CONV_Z, st);
     if (e != cudaSuccess) return e;
   }
-  if (p.Re > 0.0) {
+  if (p.Re > 0.0 && DIM == 2) {
     prof_begin(pr, st);
     k_visc_flux32<DIM><<<blocks_for(p.NB, THREADS), THREADS, 0, st>>>(p);
     prof_end(pr, K_VISC_FLUX, st);
@@ -792,7 +977,15 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   }
   int mode = !advance ? 0 : (s.stage < 2 ? 1 : 2);
   prof_begin(pr, st);
-  if (p.Re > 0.0)
+  if (p.Re > 0.0 && DIM == 3) {
+    using namespace vm;
+    e = cudaFuncSetAttribute(k_visc_march32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.n[0] + TX - 1) / TX, (p.n[1] + TY - 1) / TY, (p.n[2] + ZC - 1) / ZC);
+    k_visc_march32<<<grid, THREADS, SMEM, st>>>(p, din, dout, const_cast<double *>(Qn), s.Lout,
+                                               (float)s.b, (float)s.dt, mode);
+  } else if (p.Re > 0.0)
     k_finish32<DIM, true><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(
         p, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
   else
