@@ -146,6 +146,13 @@ int ibfsa_max_wavespeed(ibfsa_grid *g, double *host_alpha);
  * (device or host) into out [np] (device or host; synchronises when out is host memory). */
 int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out);
 
+/* Force on the body and power delivered to it, from the penalty forces of the last evaluated
+ * stage (Eq. 7): host_force[d] = sum_k F_k,d dS_k (d < dim), *host_power = sum_k (F_k . U_k) dS_k
+ * (may be NULL).  The force the body exerts on the fluid is the opposite (Eq. 9); the drag,
+ * lift and power coefficients of Sec. 4 are these divided by 0.5 rho U^2 L (and U).  FP64,
+ * summed in a fixed order; synchronises the stream. */
+int ibfsa_body_force(ibfsa_grid *g, double *host_force, double *host_power);
+
 /* Device status bits (IBFSA_STATUS_*) accumulated since the last call; clears them.
  * Synchronises the grid's stream. */
 int ibfsa_get_status(ibfsa_grid *g, int *host_flags);

@@ -179,6 +179,7 @@ Layout layout_for(const ibfsa_grid_desc &d) {
   L.probe_out = take(sizeof(double) * Pn);
   L.mlp_img = take(d.scheme == IBFSA_MLP_TENO5 ? mlp_image_bytes() : 0);
   L.mlp_counts = take(sizeof(unsigned long long) * 4);
+  L.reduce = take(sizeof(double) * 4);
   L.total = off;
   return L;
 }
@@ -296,6 +297,7 @@ int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t wor
   G.max_probes = desc->max_probes;
   G.p.mlp_img = (const unsigned char *)(w + L.mlp_img);
   G.p.mlp_counts = (unsigned long long *)(w + L.mlp_counts);
+  G.p.probe_scratch = (double *)(w + L.reduce);
   G.p.mlp_floor = 1e-9f;
   G.mlp_set = false;
   G.p.nm = 0;
@@ -555,6 +557,20 @@ int ibfsa_mlp_sample(ibfsa_grid *g, int n_max, unsigned long long seed, int atte
                                   d_count, G.stream);
   G.qn32_valid = true;
   return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_mlp_sample");
+}
+
+int ibfsa_body_force(ibfsa_grid *g, double *host_force, double *host_power) {
+  if (!g || !host_force) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  double out[4] = {0.0, 0.0, 0.0, 0.0};
+  cudaError_t e = body_force(G.p, G.U, G.p.probe_scratch, G.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, G.p.probe_scratch, sizeof(out), cudaMemcpyDeviceToHost, G.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ibfsa_body_force");
+  for (int a = 0; a < G.p.dim; a++) host_force[a] = out[a];
+  if (host_power) *host_power = out[3];
+  return IBFSA_OK;
 }
 
 int ibfsa_get_status(ibfsa_grid *g, int *host_flags) {

@@ -57,6 +57,7 @@ struct Plan {
   const unsigned char *mlp_img;
   unsigned long long *mlp_counts;
   float mlp_floor;
+  double *probe_scratch;   // small reduction results (body force, power)
   unsigned long long *alpha_bits;  // [3] ordered bits of the split speeds
   int *status;
   // markers
@@ -108,7 +109,7 @@ struct Grid {
 // Workspace layout: byte offsets of every buffer for a descriptor.
 struct Layout {
   size_t Q, Q1, Q2, Qp, Wp, L, V, f, X, U, dS, F, xi, xi1, xi2, alpha, status, probe_xp,
-      probe_out, mlp_img, mlp_counts, total;
+      probe_out, mlp_img, mlp_counts, reduce, total;
 };
 Layout layout_for(const ibfsa_grid_desc &d);
 void record_error(const char *msg);  // sets the thread-local message of ibfsa_last_error
@@ -139,6 +140,7 @@ cudaError_t fp32_refresh(const Plan &p, const double *Q, cudaStream_t st);
 cudaError_t fp32_mlp_sample(const Plan &p, const double *Q, int n_max, unsigned long long seed,
                             int attempts, float *stencils, float *targets, int *count,
                             cudaStream_t st);
+cudaError_t body_force(const Plan &p, const double *U, double *out, cudaStream_t st);
 size_t mlp_image_offset();   // byte offset of the packed image inside a training state
 size_t mlp_image_bytes();
 cudaError_t fp32_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,

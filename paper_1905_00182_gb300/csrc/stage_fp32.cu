@@ -1122,6 +1122,37 @@ cudaError_t fp32_mlp_sample(const Plan &p, const double *Q, int n_max, unsigned 
   return cudaGetLastError();
 }
 
+// Force the fluid exerts on the body and the power it delivers, from the Lagrangian penalty
+// forces of the last evaluated stage (Eq. 7): sum_k F_k dS_k and sum_k (F_k . U_k) dS_k, in
+// FP64, summed by one block in a fixed order (reproducible).
+__global__ void k_body_force(Plan p, const double *__restrict__ U, double *__restrict__ out) {
+  __shared__ double red[4][256];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int M = p.max_markers;
+  for (int k = threadIdx.x; k < p.nm; k += blockDim.x) {
+    double pw = 0.0;
+    for (int a = 0; a < p.dim; a++) {
+      double fa = p.F[a * M + k] * p.dS[k];
+      acc[a] += fa;
+      pw += fa * U[a * M + k];
+    }
+    acc[3] += pw;
+  }
+  for (int c = 0; c < 4; c++) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int c = 0; c < 4; c++) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+cudaError_t body_force(const Plan &p, const double *U, double *out, cudaStream_t st) {
+  k_body_force<<<1, 256, 0, st>>>(p, U, out);
+  return cudaGetLastError();
+}
+
 cudaError_t fp32_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   using namespace fp32_ns;
   if (p.dim == 2) {

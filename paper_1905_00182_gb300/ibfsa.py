@@ -36,6 +36,7 @@ EXPORTS = (
     "ibfsa_profile_enable", "ibfsa_profile_read", "ibfsa_rhs_noalloc",
     "ibfsa_mlp_state_bytes", "ibfsa_mlp_init", "ibfsa_mlp_train_step", "ibfsa_mlp_read",
     "ibfsa_mlp_eval", "ibfsa_set_mlp", "ibfsa_mlp_stats", "ibfsa_mlp_sample",
+    "ibfsa_body_force",
 )
 MLP_NPARAM = 2403
 
@@ -106,6 +107,7 @@ def lib():
         L.ibfsa_mlp_train_step.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.c_int, _P]
         L.ibfsa_mlp_read.argtypes = [_P, _P, _P, _P, _P]
         L.ibfsa_mlp_eval.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]
+        L.ibfsa_body_force.argtypes = [_P, _P, _P]
         L.ibfsa_set_mlp.argtypes = [_P, _P]
         L.ibfsa_mlp_stats.argtypes = [_P, _P]
         L.ibfsa_mlp_sample.argtypes = [_P, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _P, _P,
@@ -260,6 +262,13 @@ def ibfsa_mlp_eval(state: int, n: int, stencils: int, targets: int = 0, face: in
     _check(lib().ibfsa_mlp_eval(_P(state), int(n), _P(stencils), _P(targets or None),
                                 _P(face or None), _P(omega or None), _P(loss or None),
                                 _P(stream)))
+
+
+def ibfsa_body_force(g):
+    f = (ctypes.c_double * 3)()
+    pw = ctypes.c_double(0.0)
+    _check(lib().ibfsa_body_force(g, ctypes.cast(f, _P), ctypes.cast(ctypes.byref(pw), _P)))
+    return list(f), pw.value
 
 
 def ibfsa_set_mlp(g, state: int):
