@@ -285,7 +285,9 @@ __global__ void __launch_bounds__(THREADS) k_pad32(Plan p, const float *__restri
 // ------------------------------------------------------------------------------------------
 template <int A>
 struct Tile {
-  static constexpr int ROWS = A == 0 ? 4 : 32;
+  // A == 0: 8 lines (y) of 63 cells; otherwise 32 lines (consecutive x) of 15 cells -- two
+  // faces per thread either way
+  static constexpr int ROWS = A == 0 ? 8 : 32;
   static constexpr int SEG = A == 0 ? 63 : 15;
   static constexpr int LEN = SEG + 6;
   static constexpr int FACES = SEG + 1;
