@@ -683,10 +683,14 @@ __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__res
 
 // 3D viscous term + finish, marching along z.  A 32 x 8 block of threads owns 32 x 8 columns
 // and walks a z-chunk: velocity perturbations of five planes (x, y halo 4) sit in a shared-
-// memory ring; at each plane c the 9 gradients are evaluated at the block's cells and at the
-// x/y halo points the x/y divergence needs, giving F_v,x and F_v,y (shared memory, divergence
-// taken at once) and F_v,z (a five-plane register window per thread); two planes later the
-// z-divergence completes the cell: L += (1/Re) sum_a D4_a F_v,a, sponge, RK update.
+// memory ring, refilled from registers loaded one plane ahead; at each plane c the 9 gradients
+// are evaluated at the block's cells and at the x/y halo points the x/y divergence needs,
+// giving F_v,x and F_v,y (shared memory, divergence taken at once) and F_v,z, whose
+// z-differences are accumulated per thread into the cells c-2 .. c+2 of its column; cell c-2
+// is then complete: L += (1/Re) sum_a D4_a F_v,a, sponge, RK update.
+#ifndef VM_MIN_BLOCKS
+#define VM_MIN_BLOCKS 4
+#endif
 namespace vm {
 constexpr int TX = 32, TY = 8, ZC = 64;        // block columns, z-chunk
 constexpr int SX = TX + 8, SY = TY + 8;        // staged plane (halo 4)
@@ -694,7 +698,7 @@ constexpr int PX = TX + 4, PY = TY + 4;        // flux points (halo 2)
 constexpr size_t SMEM = sizeof(float) * (5 * 3 * SX * SY + 4 * PX * TY + 4 * TX * PY);
 }  // namespace vm
 
-__global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *__restrict__ din,
+__global__ void __launch_bounds__(THREADS, VM_MIN_BLOCKS) k_visc_march32(Plan p, const float *__restrict__ din,
                                                           float *__restrict__ dout, double *Qn,
                                                           double *__restrict__ Lout, float Bc,
                                                           float dt, int mode) {
@@ -712,14 +716,32 @@ __global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *_
   const float ih[3] = {p.inv_h12_32[0], p.inv_h12_32[1], p.inv_h12_32[2]};
   const int PLANE = 3 * SX * SY;
 
-  auto stage = [&](int z) {  // plane z (ghost range -4 .. n+3) into ring slot z mod 5
-    float *dst = ring + ((z + 8) % 5) * PLANE;
-    for (int e = threadIdx.x; e < SX * SY; e += THREADS) {
-      int sx = e % SX, sy = e / SX;
-      int gx = min(x0 - 4 + sx, p.n[0] + 3), gy = min(y0 - 4 + sy, p.n[1] + 3);
-      long long s = pad_index(p, gx, gy, z);
+  // plane z (ghost range -4 .. n+3) is read into registers one iteration before it enters
+  // ring slot z mod 5, so its global-memory latency hides behind the gradients of a plane
+  constexpr int PER = (SX * SY + THREADS - 1) / THREADS;
+  float R[PER][3];
+  auto fetch = [&](int z) {
 #pragma unroll
-      for (int c = 0; c < 3; c++) dst[c * SX * SY + e] = p.Wp32[c * p.NP + s];
+    for (int j = 0; j < PER; j++) {
+      int e = threadIdx.x + j * THREADS;
+      if (e < SX * SY) {
+        int sx = e % SX, sy = e / SX;
+        int gx = min(x0 - 4 + sx, p.n[0] + 3), gy = min(y0 - 4 + sy, p.n[1] + 3);
+        long long s = pad_index(p, gx, gy, z);
+#pragma unroll
+        for (int c = 0; c < 3; c++) R[j][c] = p.Wp32[c * p.NP + s];
+      }
+    }
+  };
+  auto put = [&](int z) {
+    float *dst = ring + ((z + 8) % 5) * PLANE;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+      int e = threadIdx.x + j * THREADS;
+      if (e < SX * SY) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) dst[c * SX * SY + e] = R[j][c];
+      }
     }
   };
   // gradients g[i][j] = du_i/dx_j at staged position (sx, sy) of plane c
@@ -752,21 +774,35 @@ __global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *_
     f[3] = b;
   };
 
-  float fz[5][4];   // F_v,z of this column at planes c-4 .. c
-  float pxy[3][4];  // x/y divergence of planes c-2 .. c
+  // divergence of the viscous flux of this column's cells c-2 .. c+2, accumulated as the
+  // fluxes arrive: F_v,z of plane c enters the z-differences of cells c-2, c-1, c+1, c+2
+  // (weights -1, 8, -8, 1 over 12 h), the x/y divergence of plane c enters cell c
+  float acc[5][4];
 #pragma unroll
   for (int o = 0; o < 5; o++)
 #pragma unroll
-    for (int k = 0; k < 4; k++) fz[o][k] = 0.f;
+    for (int k = 0; k < 4; k++) acc[o][k] = 0.f;
+  const float ihz8 = 8.f * ih[2];
+  // inputs of the cell finished next (L, stage increment), loaded one plane ahead
+  float Lnext[5], Dnext[5];
+  auto fetch_cell = [&](int d) {
+    if (own && d >= zs && d < ze) {
+      long long t = int_index(p, X, Y, d);
 #pragma unroll
-  for (int o = 0; o < 3; o++)
-#pragma unroll
-    for (int k = 0; k < 4; k++) pxy[o][k] = 0.f;
+      for (int cc = 0; cc < 5; cc++) {
+        Lnext[cc] = p.L32[cc * p.N + t];
+        Dnext[cc] = din ? din[cc * p.N + t] : 0.f;
+      }
+    }
+  };
 
-  for (int z = zs - 4; z < zs; z++) stage(z);
+  for (int z = zs - 4; z <= zs; z++) {
+    fetch(z);
+    put(z);
+  }
+  fetch(zs + 1);
+  __syncthreads();
   for (int c = zs - 2; c < ze + 2; c++) {
-    stage(c + 2);
-    __syncthreads();
     // own cell: all three fluxes; halo points: F_v,x (x offsets -2,-1,32,33) or F_v,y
     {
       float g[3][3], u[3], f[4];
@@ -779,11 +815,12 @@ __global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *_
       for (int k = 0; k < 4; k++) fy[(k * PY + ty + 2) * TX + tx] = f[k];
       vflux(2, g, u, f);
 #pragma unroll
-      for (int o = 0; o < 4; o++)
-#pragma unroll
-        for (int k = 0; k < 4; k++) fz[o][k] = fz[o + 1][k];
-#pragma unroll
-      for (int k = 0; k < 4; k++) fz[4][k] = f[k];
+      for (int k = 0; k < 4; k++) {
+        acc[0][k] -= ih[2] * f[k];
+        acc[1][k] += ihz8 * f[k];
+        acc[3][k] -= ihz8 * f[k];
+        acc[4][k] += ih[2] * f[k];
+      }
     }
     for (int e = threadIdx.x; e < 4 * TY + 4 * TX; e += THREADS) {
       float g[3][3], u[3], f[4];
@@ -804,26 +841,21 @@ __global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *_
     __syncthreads();
     // x/y divergence at this column's cell of plane c
 #pragma unroll
-    for (int o = 0; o < 2; o++)
-#pragma unroll
-      for (int k = 0; k < 4; k++) pxy[o][k] = pxy[o + 1][k];
-#pragma unroll
     for (int k = 0; k < 4; k++) {
       const float *Fx = fx + (k * TY + ty) * PX + tx + 2;
       const float *Fy = fy + (k * PY + ty + 2) * TX + tx;
-      pxy[2][k] = d4f(Fx[-2], Fx[-1], Fx[1], Fx[2], ih[0]) +
-                  d4f(Fy[-2 * TX], Fy[-TX], Fy[TX], Fy[2 * TX], ih[1]);
+      acc[2][k] += d4f(Fx[-2], Fx[-1], Fx[1], Fx[2], ih[0]) +
+                   d4f(Fy[-2 * TX], Fy[-TX], Fy[TX], Fy[2 * TX], ih[1]);
     }
-    // plane d = c - 2 is complete: z-divergence, sponge, RK update
+    // plane d = c - 2 is complete: viscous term, sponge, RK update
     int d = c - 2;
     if (own && d >= zs && d < ze) {
       long long t = int_index(p, X, Y, d);
       float Lc[5];
 #pragma unroll
-      for (int cc = 0; cc < 5; cc++) Lc[cc] = p.L32[cc * p.N + t];
+      for (int cc = 0; cc < 5; cc++) Lc[cc] = Lnext[cc];
 #pragma unroll
-      for (int k = 0; k < 4; k++)
-        Lc[k + 1] += (pxy[0][k] + d4f(fz[0][k], fz[1][k], fz[3][k], fz[4][k], ih[2])) * p.inv_Re32;
+      for (int k = 0; k < 4; k++) Lc[k + 1] += acc[0][k] * p.inv_Re32;
       if (p.sponge_cells > 0) {
         int I[3] = {X, Y, d};
         int S = p.sponge_cells, nmin = 1 << 30;
@@ -833,8 +865,7 @@ __global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *_
           float rr = (float)(S - nmin) / (float)S;
           float sig = (float)p.sponge_sigma * rr * rr * rr;
 #pragma unroll
-          for (int cc = 0; cc < 5; cc++)
-            Lc[cc] -= sig * (p.qn32[cc * p.N + t] + (din ? din[cc * p.N + t] : 0.f));
+          for (int cc = 0; cc < 5; cc++) Lc[cc] -= sig * (p.qn32[cc * p.N + t] + Dnext[cc]);
         }
       }
       if (mode == 0) {
@@ -845,7 +876,7 @@ __global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *_
         float inc[5];
 #pragma unroll
         for (int cc = 0; cc < 5; cc++) {
-          inc[cc] = Bc * ((din ? din[cc * p.N + t] : 0.f) + dt * Lc[cc]);
+          inc[cc] = Bc * (Dnext[cc] + dt * Lc[cc]);
           bad |= !isfinite(inc[cc]);
         }
         if (mode == 1) {
@@ -862,7 +893,20 @@ __global__ void __launch_bounds__(THREADS) k_visc_march32(Plan p, const float *_
         if (bad) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
       }
     }
-    __syncthreads();  // the ring slot of plane c - 2 is restaged next iteration
+    // plane c + 3 (needed from the next iteration on) replaces plane c - 2, whose gradients
+    // were all taken before the barrier above; plane c + 4 starts loading
+#pragma unroll
+    for (int o = 0; o < 4; o++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) acc[o][k] = acc[o + 1][k];
+#pragma unroll
+    for (int k = 0; k < 4; k++) acc[4][k] = 0.f;
+    if (c + 1 < ze + 2) {
+      put(c + 3);
+      if (c + 2 < ze + 2) fetch(c + 4);
+      fetch_cell(c - 1);
+    }
+    __syncthreads();
   }
 }
 
