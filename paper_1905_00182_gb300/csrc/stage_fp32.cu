@@ -197,6 +197,38 @@ __device__ __forceinline__ float teno5_fast(const Plan &tw, float a, float b, fl
   return teno5(tw, a, b, c, d, e);
 }
 
+// TENO5 at one face for both split fluxes at once on packed FP32x2 arithmetic (.x: the f+
+// stencil, .y: the f- stencil, each ordered upwind to downwind): smoothness indicators and the
+// linear combination for both sides in one instruction each; a side that fails the all-kept
+// test takes the full scalar TENO5.  Returns h+ + h-.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float teno5_pm(const Plan &tw, float2 a, float2 b, float2 c,
+                                          float2 d, float2 e) {
+  float2 t0 = __fadd2_rn(__ffma2_rn(f2(-2.f), b, a), c);
+  float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.f), c, b), d);
+  float2 t2 = __fadd2_rn(__ffma2_rn(f2(-2.f), d, c), e);
+  float2 u0 = __ffma2_rn(f2(3.f), c, __ffma2_rn(f2(-4.f), b, a));
+  float2 u1 = __ffma2_rn(f2(-1.f), d, b);
+  float2 u2 = __ffma2_rn(f2(3.f), c, __ffma2_rn(f2(-4.f), d, e));
+  const float2 k13 = f2(13.f / 12.f), q = f2(0.25f);
+  float2 b0 = __ffma2_rn(__fmul2_rn(k13, t0), t0, __fmul2_rn(__fmul2_rn(q, u0), u0));
+  float2 b1 = __ffma2_rn(__fmul2_rn(k13, t1), t1, __fmul2_rn(__fmul2_rn(q, u1), u1));
+  float2 b2 = __ffma2_rn(__fmul2_rn(k13, t2), t2, __fmul2_rn(__fmul2_rn(q, u2), u2));
+  float2 tau = __ffma2_rn(f2(-1.f), b2, b0);
+  bool kx = fabsf(tau.x) <= 4.f * (fminf(b0.x, fminf(b1.x, b2.x)) + 1e-30f);
+  bool ky = fabsf(tau.y) <= 4.f * (fminf(b0.y, fminf(b1.y, b2.y)) + 1e-30f);
+  float2 lin = __fmul2_rn(f2(2.f / 60.f), a);
+  lin = __ffma2_rn(f2(-13.f / 60.f), b, lin);
+  lin = __ffma2_rn(f2(47.f / 60.f), c, lin);
+  lin = __ffma2_rn(f2(27.f / 60.f), d, lin);
+  lin = __ffma2_rn(f2(-3.f / 60.f), e, lin);
+  if (kx && ky) return lin.x + lin.y;
+  float hx = kx ? lin.x : teno5(tw, a.x, b.x, c.x, d.x, e.x);
+  float hy = ky ? lin.y : teno5(tw, a.y, b.y, c.y, d.y, e.y);
+  return hx + hy;
+}
+
 template <int SCHEME>
 __device__ __forceinline__ float recon(const Plan &tw, float a, float b, float c, float d,
                                        float e) {
@@ -319,8 +351,11 @@ __device__ __forceinline__ float recon_mlp(const Plan &p, const unsigned char *i
               : w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
 }
 
+// eight blocks per SM (32 registers) for the fixed schemes, four (64 registers) for the
+// learned form's warp-wide network tiles
 template <int DIM, int A, int SCHEME>
-__global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
+__global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
+    k_conv32(Plan p, int first) {
   constexpr int NV = DIM + 2;
   using T = Tile<A>;
   // face fluxes are stored with an odd row stride when a warp walks the rows (A != 0), so the
@@ -443,8 +478,13 @@ __global__ void __launch_bounds__(THREADS) k_conv32(Plan p, int first) {
         for (int c = 0; c < NV; c++) {
           const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
           const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
-          Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
-                      recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+          if constexpr (SCHEME == IBFSA_TENO5)
+            Fh[ps][c] = teno5_pm(p, make_float2(fp[b - 2], fm[b + 3]),
+                                 make_float2(fp[b - 1], fm[b + 2]), make_float2(fp[b], fm[b + 1]),
+                                 make_float2(fp[b + 1], fm[b]), make_float2(fp[b + 2], fm[b - 1]));
+          else
+            Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
+                        recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
         }
       }
     }
