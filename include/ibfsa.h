@@ -64,8 +64,10 @@ enum { IBFSA_FP64 = 0, IBFSA_FP32_PERTURB = 1 };
 /* boundary rules per face of the box: ghost cells copy the nearest interior cell, hold the
  * free stream, or wrap around */
 enum { IBFSA_BC_ZERO_GRAD = 0, IBFSA_BC_FREESTREAM = 1, IBFSA_BC_PERIODIC = 2 };
-/* status bits of ibfsa_get_status */
-enum { IBFSA_STATUS_BOUNDS = 1, IBFSA_STATUS_NONFINITE = 2 };
+/* status bits of ibfsa_get_status: a marker or probe support left the grid; a non-finite
+ * value entered the state; a kernel gave up waiting for its tensor copies (iteration limit), so
+ * the results of that call are invalid */
+enum { IBFSA_STATUS_BOUNDS = 1, IBFSA_STATUS_NONFINITE = 2, IBFSA_STATUS_TIMEOUT = 4 };
 
 typedef struct ibfsa_grid ibfsa_grid; /* opaque; created and destroyed by the library */
 

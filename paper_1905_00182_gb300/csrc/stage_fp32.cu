@@ -27,6 +27,7 @@
 
 #include "ibfsa_internal.h"
 #include "mlp_tile.cuh"
+#include "tma.cuh"
 
 namespace ibfsa {
 namespace fp32_ns {
@@ -325,9 +326,19 @@ struct Tile {
   static constexpr int FACES = SEG + 1;
 };
 
+// floats of the tensor-copied tile (y/z passes): conservative perturbations [NV][LEN][ROWS],
+// u'_A and p' [2][LEN][ROWS], the right-hand side [NV][SEG][ROWS]
 template <int DIM, int A>
+__host__ __device__ constexpr int tma_tile_floats() {
+  using T = Tile<A>;
+  return (DIM + 4) * T::LEN * T::ROWS + (DIM + 2) * T::SEG * T::ROWS;
+}
+
+template <int DIM, int A, bool TMA = false>
 constexpr size_t conv_smem() {
-  return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN;  // >= face-flux area
+  // split fluxes (>= face-flux area), plus the copied tile and its barrier
+  return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN +
+         (TMA ? sizeof(float) * tma_tile_floats<DIM, A>() + 16 : 0);
 }
 
 // learned weights: reconstruction of one stencil with the TENO5 guard; every lane of the warp
@@ -353,17 +364,27 @@ __device__ __forceinline__ float recon_mlp(const Plan &p, const unsigned char *i
 
 // eight blocks per SM (32 registers) for the fixed schemes, four (64 registers) for the
 // learned form's warp-wide network tiles
-template <int DIM, int A, int SCHEME>
-__global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
-    k_conv32(Plan p, int first) {
+//
+// TMA (y and z passes, x extent a multiple of 4): one thread copies the tile -- q' of the
+// staged cells, u'_A and p', and the block's part of L' -- into shared memory with three tensor
+// copies completing on one barrier; L' is updated there and written back by a tensor store.
+template <int DIM, int A, int SCHEME, bool TMA>
+__global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (TMA ? 4 : 8))
+    k_conv32(Plan p, int first, const __grid_constant__ CUtensorMap tq,
+             const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap tl) {
   constexpr int NV = DIM + 2;
   using T = Tile<A>;
+  static_assert(!TMA || (A != 0 && SCHEME != IBFSA_MLP_TENO5), "tensor copies: y/z passes");
   // face fluxes are stored with an odd row stride when a warp walks the rows (A != 0), so the
   // 32 lanes hit 32 different banks
   constexpr int FST = A == 0 ? T::FACES : T::FACES + 1;
-  extern __shared__ float smf[];
-  float *sfp = smf;
-  float *sfm = smf + NV * T::ROWS * T::LEN;
+  extern __shared__ __align__(128) float smf[];
+  constexpr int RAW = TMA ? tma_tile_floats<DIM, A>() : 0;
+  float *rawQ = smf;                                  // [NV][LEN][ROWS]
+  float *rawW = smf + NV * T::LEN * T::ROWS;          // [2][LEN][ROWS]: u'_A, p'
+  float *Ls = rawW + 2 * T::LEN * T::ROWS;            // [NV][SEG][ROWS]
+  float *sfp = smf + RAW;
+  float *sfm = sfp + NV * T::ROWS * T::LEN;
   const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
   Free fs = free_stream(p);
 
@@ -402,6 +423,31 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
   for (int c = 0; c < NV; c++) Qc[c] = p.Qp32 + (size_t)c * p.NP;
   const float *Wa = p.Wp32 + (size_t)A * p.NP;
   const float *Wpr = p.Wp32 + (size_t)DIM * p.NP;
+  int tyi = 0, tzi = 0;  // interior y, z of the tile's first cell (TMA)
+  if constexpr (TMA) {
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sfm + NV * T::ROWS * T::LEN);
+    tyi = A == 1 ? seg0 : other;
+    tzi = A == 1 ? other : seg0;
+    if (threadIdx.x == 0) tma::mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma::mbar_expect_tx(bar, (uint32_t)(sizeof(float) * RAW));
+      const int px = line0 + p.g[0];
+      const int py = (A == 1 ? tyi - 3 : tyi) + p.g[1], pz = (A == 2 ? tzi - 3 : tzi) + p.g[2];
+      tma::load_4d(rawQ, &tq, px, py, pz, 0, bar);
+      tma::load_4d(rawW, &tw, px, py, pz, A, bar);
+      tma::load_4d(rawW + T::LEN * T::ROWS, &tw, px, py, pz, DIM, bar);
+      tma::load_4d(Ls, &tl, line0, tyi, tzi, 0, bar);
+    }
+    const bool ok = tma::mbar_wait(bar, 0);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(p.status, IBFSA_STATUS_TIMEOUT);
+        tma::mbar_wait(bar, 0);  // give copies still in flight a second bounded wait
+      }
+      return;
+    }
+  }
 
   if constexpr (SCHEME == IBFSA_MLP_TENO5) {
     uint4 *dst = reinterpret_cast<uint4 *>(smf + 2 * NV * T::ROWS * T::LEN);
@@ -415,14 +461,15 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
     else { row = e % T::ROWS; l = e / T::ROWS; }
     if (row >= nrow || l >= ncell + 6) continue;
     int s = pbase + row * prs + (l - 3) * pas;
-    float up = Wa[s];
-    float pp = Wpr[s];
+    const int r = l * T::ROWS + row;  // position in the copied tile
+    float up = TMA ? rawW[r] : Wa[s];
+    float pp = TMA ? rawW[T::LEN * T::ROWS + r] : Wpr[s];
     float ua = fs.u[A] + up;
 #pragma unroll
     for (int c = 0; c < NV; c++) {
-      float q = Qc[c][s];
+      float q = TMA ? rawQ[c * T::LEN * T::ROWS + r] : Qc[c][s];
       float F;
-      if (c == 0) F = Qc[1 + A][s];
+      if (c == 0) F = TMA ? rawQ[(1 + A) * T::LEN * T::ROWS + r] : Qc[1 + A][s];
       else if (c == NV - 1) F = (q + pp) * ua + fs.H * up;
       else {
         F = q * ua + fs.m[c - 1] * up;
@@ -490,7 +537,7 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
     }
   }
   __syncthreads();
-  float *sh = smf;
+  float *sh = sfp;
 #pragma unroll
   for (int ps = 0; ps < MAXP; ps++) {
     int e = threadIdx.x + ps * THREADS;
@@ -516,9 +563,19 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
     for (int c = 0; c < NV; c++) {
       const float *hh = sh + (c * T::ROWS + row) * FST;
       float d = (hh[l + 1] - hh[l]) * inv_h;
-      float *Lc = p.L32 + (size_t)c * p.N;
-      Lc[o] = (first ? 0.f : Lc[o]) - d;
+      if constexpr (TMA) {
+        float &Lv = Ls[(c * T::SEG + l) * T::ROWS + row];
+        Lv = (first ? 0.f : Lv) - d;
+      } else {
+        float *Lc = p.L32 + (size_t)c * p.N;
+        Lc[o] = (first ? 0.f : Lc[o]) - d;
+      }
     }
+  }
+  if constexpr (TMA) {
+    tma::fence_async_shared();
+    __syncthreads();
+    if (threadIdx.x == 0) tma::store_4d(&tl, line0, tyi, tzi, 0, Ls);
   }
 }
 
@@ -992,14 +1049,39 @@ inline unsigned blocks_for(long long n, int threads) {
   return (unsigned)((n + threads - 1) / threads);
 }
 
-template <int DIM, int A, int SCHEME>
-cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
+// Tensor maps of the y/z tile copies: q' and the primitives over the padded box, L' over the
+// interior, each as a rank-4 tensor (x, y, z, component) with boxes of 32 x-lines by the staged
+// (or owned) cells along A.
+template <int DIM, int A>
+cudaError_t conv_tensor_maps(const Plan &p, CUtensorMap *tq, CUtensorMap *tw, CUtensorMap *tl) {
+  using T = Tile<A>;
+  const uint64_t P0 = p.P[0], P1 = p.P[1], P2 = p.P[2], n0 = p.n[0], n1 = p.n[1], n2 = p.n[2];
+  const uint64_t ps[3] = {4 * P0, 4 * P0 * P1, 4 * (uint64_t)p.NP};
+  const uint64_t is[3] = {4 * n0, 4 * n0 * n1, 4 * (uint64_t)p.N};
+  const uint64_t dq[4] = {P0, P1, P2, (uint64_t)DIM + 2}, dw[4] = {P0, P1, P2, (uint64_t)DIM + 1};
+  const uint64_t dl[4] = {n0, n1, n2, (uint64_t)DIM + 2};
+  const uint32_t ly = A == 1 ? T::LEN : 1, lz = A == 2 ? T::LEN : 1;
+  const uint32_t sy = A == 1 ? T::SEG : 1, sz = A == 2 ? T::SEG : 1;
+  const uint32_t bq[4] = {T::ROWS, ly, lz, DIM + 2}, bw[4] = {T::ROWS, ly, lz, 1};
+  const uint32_t bl[4] = {T::ROWS, sy, sz, DIM + 2};
+  cudaError_t e;
+  if ((e = tma::encode_f32_4d(tq, p.Qp32, dq, ps, bq)) != cudaSuccess) return e;
+  if ((e = tma::encode_f32_4d(tw, p.Wp32, dw, ps, bw)) != cudaSuccess) return e;
+  return tma::encode_f32_4d(tl, p.L32, dl, is, bl);
+}
+
+template <int DIM, int A, int SCHEME, bool TMA>
+cudaError_t launch_conv_as(const Plan &p, int first, cudaStream_t st) {
   using T = Tile<A>;
   constexpr size_t smem =
-      conv_smem<DIM, A>() + (SCHEME == IBFSA_MLP_TENO5 ? (size_t)mlp::PACKED_BYTES : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_conv32<DIM, A, SCHEME>,
+      conv_smem<DIM, A, TMA>() + (SCHEME == IBFSA_MLP_TENO5 ? (size_t)mlp::PACKED_BYTES : 0);
+  cudaError_t e = cudaFuncSetAttribute(k_conv32<DIM, A, SCHEME, TMA>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  CUtensorMap tq{}, tw{}, tl{};
+  if constexpr (TMA) {
+    if ((e = conv_tensor_maps<DIM, A>(p, &tq, &tw, &tl)) != cudaSuccess) return e;
+  }
   dim3 grid;
   if (A == 0) {
     grid = dim3((p.n[0] + T::SEG - 1) / T::SEG, (p.n[1] + T::ROWS - 1) / T::ROWS, p.n[2]);
@@ -1008,8 +1090,18 @@ cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
     int nx = (p.n[0] + T::ROWS - 1) / T::ROWS;
     grid = dim3(nseg * nx, A == 1 ? p.n[2] : p.n[1]);
   }
-  k_conv32<DIM, A, SCHEME><<<grid, THREADS, smem, st>>>(p, first);
+  k_conv32<DIM, A, SCHEME, TMA><<<grid, THREADS, smem, st>>>(p, first, tq, tw, tl);
   return cudaGetLastError();
+}
+
+// y and z passes of the fixed schemes use the tensor copies when every stride of the copied
+// tensors is a multiple of 16 bytes (x extent a multiple of 4)
+template <int DIM, int A, int SCHEME>
+cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
+  if constexpr (A != 0 && SCHEME != IBFSA_MLP_TENO5) {
+    if (p.n[0] % 4 == 0) return launch_conv_as<DIM, A, SCHEME, true>(p, first, st);
+  }
+  return launch_conv_as<DIM, A, SCHEME, false>(p, first, st);
 }
 
 template <int DIM, int SCHEME>

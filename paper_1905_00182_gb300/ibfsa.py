@@ -26,6 +26,7 @@ IBFSA_ERR_UNSUPPORTED = -5
 IBFSA_ERR_WORKSPACE = -6
 IBFSA_STATUS_BOUNDS = 1
 IBFSA_STATUS_NONFINITE = 2
+IBFSA_STATUS_TIMEOUT = 4
 
 # every symbol include/ibfsa.h declares
 EXPORTS = (
