@@ -326,19 +326,9 @@ struct Tile {
   static constexpr int FACES = SEG + 1;
 };
 
-// floats of the tensor-copied tile (y/z passes): conservative perturbations [NV][LEN][ROWS],
-// u'_A and p' [2][LEN][ROWS], the right-hand side [NV][SEG][ROWS]
 template <int DIM, int A>
-__host__ __device__ constexpr int tma_tile_floats() {
-  using T = Tile<A>;
-  return (DIM + 4) * T::LEN * T::ROWS + (DIM + 2) * T::SEG * T::ROWS;
-}
-
-template <int DIM, int A, bool TMA = false>
 constexpr size_t conv_smem() {
-  // split fluxes (>= face-flux area), plus the copied tile and its barrier
-  return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN +
-         (TMA ? sizeof(float) * tma_tile_floats<DIM, A>() + 16 : 0);
+  return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN;  // >= face-flux area
 }
 
 // learned weights: reconstruction of one stencil with the TENO5 guard; every lane of the warp
@@ -362,31 +352,46 @@ __device__ __forceinline__ float recon_mlp(const Plan &p, const unsigned char *i
               : w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
 }
 
+// split fluxes f+-' = (F' +- alpha q') / 2 along A of one staged cell, from q', u'_A and p';
+// F' is the perturbation-expanded flux (no O(1) free-stream terms cancel)
+template <int DIM, int A>
+__device__ __forceinline__ void split_cell(const Free &fs, float alpha, const float q[DIM + 2],
+                                           float up, float pp, float fpv[DIM + 2],
+                                           float fmv[DIM + 2]) {
+  constexpr int NV = DIM + 2;
+  const float ua = fs.u[A] + up;
+#pragma unroll
+  for (int c = 0; c < NV; c++) {
+    float F;
+    if (c == 0) F = q[1 + A];
+    else if (c == NV - 1) F = (q[c] + pp) * ua + fs.H * up;
+    else {
+      F = q[c] * ua + fs.m[c - 1] * up;
+      if (c - 1 == A) F += pp;
+    }
+    const float aq = alpha * q[c];
+    fpv[c] = 0.5f * (F + aq);
+    fmv[c] = 0.5f * (F - aq);
+  }
+}
+
 // eight blocks per SM (32 registers) for the fixed schemes, four (64 registers) for the
-// learned form's warp-wide network tiles
-//
-// TMA (y and z passes, x extent a multiple of 4): one thread copies the tile -- q' of the
-// staged cells, u'_A and p', and the block's part of L' -- into shared memory with three tensor
-// copies completing on one barrier; L' is updated there and written back by a tensor store.
-template <int DIM, int A, int SCHEME, bool TMA>
-__global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (TMA ? 4 : 8))
-    k_conv32(Plan p, int first, const __grid_constant__ CUtensorMap tq,
-             const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap tl) {
+// learned form's warp-wide network tiles.  The x pass gives each warp one row of the tile.
+template <int DIM, int A, int SCHEME>
+__global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
+    k_conv32(Plan p, int first) {
   constexpr int NV = DIM + 2;
   using T = Tile<A>;
-  static_assert(!TMA || (A != 0 && SCHEME != IBFSA_MLP_TENO5), "tensor copies: y/z passes");
+  static_assert(A != 0 || T::ROWS * 32 == THREADS, "x pass: one warp per row");
   // face fluxes are stored with an odd row stride when a warp walks the rows (A != 0), so the
   // 32 lanes hit 32 different banks
   constexpr int FST = A == 0 ? T::FACES : T::FACES + 1;
-  extern __shared__ __align__(128) float smf[];
-  constexpr int RAW = TMA ? tma_tile_floats<DIM, A>() : 0;
-  float *rawQ = smf;                                  // [NV][LEN][ROWS]
-  float *rawW = smf + NV * T::LEN * T::ROWS;          // [2][LEN][ROWS]: u'_A, p'
-  float *Ls = rawW + 2 * T::LEN * T::ROWS;            // [NV][SEG][ROWS]
-  float *sfp = smf + RAW;
-  float *sfm = sfp + NV * T::ROWS * T::LEN;
+  extern __shared__ float smf[];
+  float *sfp = smf;
+  float *sfm = smf + NV * T::ROWS * T::LEN;
   const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
   Free fs = free_stream(p);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   int seg0, line0, other;
   if constexpr (A == 0) {
@@ -418,36 +423,8 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (TMA 
     ibase = z * NXY + y * NX + line0;
     irs = 1; ias = A == 1 ? NX : NXY;
   }
-  const float *Qc[NV];
-#pragma unroll
-  for (int c = 0; c < NV; c++) Qc[c] = p.Qp32 + (size_t)c * p.NP;
   const float *Wa = p.Wp32 + (size_t)A * p.NP;
   const float *Wpr = p.Wp32 + (size_t)DIM * p.NP;
-  int tyi = 0, tzi = 0;  // interior y, z of the tile's first cell (TMA)
-  if constexpr (TMA) {
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sfm + NV * T::ROWS * T::LEN);
-    tyi = A == 1 ? seg0 : other;
-    tzi = A == 1 ? other : seg0;
-    if (threadIdx.x == 0) tma::mbar_init(bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tma::mbar_expect_tx(bar, (uint32_t)(sizeof(float) * RAW));
-      const int px = line0 + p.g[0];
-      const int py = (A == 1 ? tyi - 3 : tyi) + p.g[1], pz = (A == 2 ? tzi - 3 : tzi) + p.g[2];
-      tma::load_4d(rawQ, &tq, px, py, pz, 0, bar);
-      tma::load_4d(rawW, &tw, px, py, pz, A, bar);
-      tma::load_4d(rawW + T::LEN * T::ROWS, &tw, px, py, pz, DIM, bar);
-      tma::load_4d(Ls, &tl, line0, tyi, tzi, 0, bar);
-    }
-    const bool ok = tma::mbar_wait(bar, 0);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        atomicOr(p.status, IBFSA_STATUS_TIMEOUT);
-        tma::mbar_wait(bar, 0);  // give copies still in flight a second bounded wait
-      }
-      return;
-    }
-  }
 
   if constexpr (SCHEME == IBFSA_MLP_TENO5) {
     uint4 *dst = reinterpret_cast<uint4 *>(smf + 2 * NV * T::ROWS * T::LEN);
@@ -455,29 +432,30 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (TMA 
     for (int i = threadIdx.x; i < mlp::PACKED_BYTES / 16; i += THREADS) dst[i] = src[i];
   }
   // 1. f+-' of the staged cells (seg0-3 .. seg0+ncell+2)
-  for (int e = threadIdx.x; e < T::ROWS * T::LEN; e += THREADS) {
+  constexpr int S1 = A == 0 ? (T::LEN + 31) / 32 : (T::ROWS * T::LEN + THREADS - 1) / THREADS;
+#pragma unroll
+  for (int k = 0; k < S1; k++) {
     int row, l;
-    if constexpr (A == 0) { row = e / T::LEN; l = e - row * T::LEN; }
-    else { row = e % T::ROWS; l = e / T::ROWS; }
+    if constexpr (A == 0) {
+      row = warp;
+      l = lane + 32 * k;
+      if (l >= T::LEN) break;
+    } else {
+      const int e = threadIdx.x + k * THREADS;
+      if (e >= T::ROWS * T::LEN) break;
+      row = e % T::ROWS;
+      l = e / T::ROWS;
+    }
     if (row >= nrow || l >= ncell + 6) continue;
-    int s = pbase + row * prs + (l - 3) * pas;
-    const int r = l * T::ROWS + row;  // position in the copied tile
-    float up = TMA ? rawW[r] : Wa[s];
-    float pp = TMA ? rawW[T::LEN * T::ROWS + r] : Wpr[s];
-    float ua = fs.u[A] + up;
+    const int s = pbase + row * prs + (l - 3) * pas;
+    float q[NV], fpv[NV], fmv[NV];
+#pragma unroll
+    for (int c = 0; c < NV; c++) q[c] = p.Qp32[(size_t)c * p.NP + s];
+    split_cell<DIM, A>(fs, alpha, q, Wa[s], Wpr[s], fpv, fmv);
 #pragma unroll
     for (int c = 0; c < NV; c++) {
-      float q = TMA ? rawQ[c * T::LEN * T::ROWS + r] : Qc[c][s];
-      float F;
-      if (c == 0) F = TMA ? rawQ[(1 + A) * T::LEN * T::ROWS + r] : Qc[1 + A][s];
-      else if (c == NV - 1) F = (q + pp) * ua + fs.H * up;
-      else {
-        F = q * ua + fs.m[c - 1] * up;
-        if (c - 1 == A) F += pp;
-      }
-      float aq = alpha * q;
-      sfp[(c * T::ROWS + row) * T::LEN + l] = 0.5f * (F + aq);
-      sfm[(c * T::ROWS + row) * T::LEN + l] = 0.5f * (F - aq);
+      sfp[(c * T::ROWS + row) * T::LEN + l] = fpv[c];
+      sfm[(c * T::ROWS + row) * T::LEN + l] = fmv[c];
     }
   }
   __syncthreads();
@@ -537,7 +515,7 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (TMA 
     }
   }
   __syncthreads();
-  float *sh = sfp;
+  float *sh = smf;
 #pragma unroll
   for (int ps = 0; ps < MAXP; ps++) {
     int e = threadIdx.x + ps * THREADS;
@@ -553,30 +531,179 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (TMA 
 
   // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / h
   const float inv_h = p.inv_h32[A];
-  for (int e = threadIdx.x; e < T::ROWS * T::SEG; e += THREADS) {
+  constexpr int S3 = A == 0 ? (T::SEG + 31) / 32 : (T::ROWS * T::SEG + THREADS - 1) / THREADS;
+#pragma unroll
+  for (int k = 0; k < S3; k++) {
     int row, l;
-    if constexpr (A == 0) { row = e / T::SEG; l = e - row * T::SEG; }
-    else { row = e % T::ROWS; l = e / T::ROWS; }
+    if constexpr (A == 0) {
+      row = warp;
+      l = lane + 32 * k;
+      if (l >= T::SEG) break;
+    } else {
+      const int e = threadIdx.x + k * THREADS;
+      if (e >= T::ROWS * T::SEG) break;
+      row = e % T::ROWS;
+      l = e / T::ROWS;
+    }
     if (row >= nrow || l >= ncell) continue;
     int o = ibase + row * irs + l * ias;
 #pragma unroll
     for (int c = 0; c < NV; c++) {
       const float *hh = sh + (c * T::ROWS + row) * FST;
       float d = (hh[l + 1] - hh[l]) * inv_h;
-      if constexpr (TMA) {
-        float &Lv = Ls[(c * T::SEG + l) * T::ROWS + row];
-        Lv = (first ? 0.f : Lv) - d;
-      } else {
-        float *Lc = p.L32 + (size_t)c * p.N;
-        Lc[o] = (first ? 0.f : Lc[o]) - d;
+      float *Lc = p.L32 + (size_t)c * p.N;
+      Lc[o] = (first ? 0.f : Lc[o]) - d;
+    }
+  }
+}
+
+// y and z passes of the fixed schemes with tensor copies (x extent a multiple of 4, so every
+// stride of the copied tensors is a multiple of 16 bytes).  A tile is 32 consecutive x-lines by
+// the staged cells along A; a warp covers the 32 lines of one position along A, so there is no
+// index division and every shared-memory access of a warp falls in 32 banks.
+//   shared memory: [ q' (NV) | u'_A | p' ] staged cells, [NV][LEN][32], reused for the block's
+//   L' [NV][SEG][32] once the split fluxes are built; f+ at staged cells 0..LEN-2 and f- at
+//   1..LEN-1 (the only ones the faces read), [NV][LEN-1][32] each, reused for the face fluxes;
+//   one barrier.  44 KB in 3D: five blocks per SM.
+// One thread issues the copies: the staged inputs (three copies) at entry, the block's L' after
+// the split fluxes (its latency hides behind the reconstruction); L' is updated in shared
+// memory and written back with a tensor store.  Waits are bounded: on expiry the block reports
+// IBFSA_STATUS_TIMEOUT and ends.
+template <int DIM, int A>
+struct TmaTile {
+  using T = Tile<A>;
+  static constexpr int NV = DIM + 2, R = T::ROWS, LEN = T::LEN, SEG = T::SEG;
+  static constexpr int IN = (NV + 2) * LEN * R;     // floats of the staged inputs
+  static constexpr int LT = NV * SEG * R;           // floats of the L' tile
+  static constexpr int SF = NV * (LEN - 1) * R;     // floats of f+ (and of f-)
+  static constexpr size_t BYTES = sizeof(float) * (IN + 2 * SF) + 16;
+  static_assert(LT <= IN, "the L' tile reuses the staged inputs");
+  static_assert(R == 32, "one warp spans the x-lines of a tile");
+};
+
+template <int DIM, int A, int SCHEME>
+__global__ void __launch_bounds__(THREADS, 5)
+    k_conv32_tma(Plan p, const __grid_constant__ CUtensorMap tq,
+                 const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap tl) {
+  using TT = TmaTile<DIM, A>;
+  using T = Tile<A>;
+  constexpr int NV = TT::NV, R = TT::R, LEN = TT::LEN, SEG = TT::SEG;
+  constexpr int FST = T::FACES + 1;
+  static_assert(SCHEME != IBFSA_MLP_TENO5, "fixed schemes only");
+  extern __shared__ __align__(128) float smf[];
+  float *in = smf;                         // [NV + 2][LEN][R], then L' [NV][SEG][R]
+  float *sfp = smf + TT::IN;               // [NV][LEN - 1][R]: f+ at staged cells 0..LEN-2
+  float *sfm = sfp + TT::SF;               // [NV][LEN - 1][R]: f- at staged cells 1..LEN-1
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sfm + TT::SF);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = THREADS / 32;
+
+  const int nseg = (p.n[A] + SEG - 1) / SEG;
+  const int seg0 = (blockIdx.x % nseg) * SEG;
+  const int line0 = (blockIdx.x / nseg) * R;
+  const int other = blockIdx.y;
+  const int ncell = min(SEG, p.n[A] - seg0);
+  const int nface = ncell + 1;
+  const bool row_ok = lane < min(R, p.n[0] - line0);
+  const int yi = A == 1 ? seg0 : other, zi = A == 1 ? other : seg0;  // first owned cell
+
+  if (threadIdx.x == 0) tma::mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma::mbar_expect_tx(bar, (uint32_t)(sizeof(float) * TT::IN));
+    const int px = line0 + p.g[0];
+    const int py = (A == 1 ? yi - 3 : yi) + p.g[1], pz = (A == 2 ? zi - 3 : zi) + p.g[2];
+    tma::load_4d(in, &tq, px, py, pz, 0, bar);
+    tma::load_4d(in + NV * LEN * R, &tw, px, py, pz, A, bar);
+    tma::load_4d(in + (NV + 1) * LEN * R, &tw, px, py, pz, DIM, bar);
+  }
+  if (__syncthreads_or(!tma::mbar_wait(bar, 0))) {
+    if (threadIdx.x == 0) {
+      atomicOr(p.status, IBFSA_STATUS_TIMEOUT);
+      tma::mbar_wait(bar, 0);  // a second bounded wait for copies still in flight
+    }
+    return;
+  }
+
+  // 1. f+-' of the staged cells l = 0 .. ncell+5 (cells seg0-3 .. seg0+ncell+2)
+  const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
+  {
+    Free fs = free_stream(p);
+    for (int l = warp; l < ncell + 6; l += NW) {
+      float q[NV], fpv[NV], fmv[NV];
+#pragma unroll
+      for (int c = 0; c < NV; c++) q[c] = in[(c * LEN + l) * R + lane];
+      split_cell<DIM, A>(fs, alpha, q, in[(NV * LEN + l) * R + lane],
+                         in[((NV + 1) * LEN + l) * R + lane], fpv, fmv);
+#pragma unroll
+      for (int c = 0; c < NV; c++) {
+        if (l < LEN - 1) sfp[(c * (LEN - 1) + l) * R + lane] = fpv[c];
+        if (l > 0) sfm[(c * (LEN - 1) + l - 1) * R + lane] = fmv[c];
       }
     }
   }
-  if constexpr (TMA) {
-    tma::fence_async_shared();
-    __syncthreads();
-    if (threadIdx.x == 0) tma::store_4d(&tl, line0, tyi, tzi, 0, Ls);
+  __syncthreads();
+  // the staged inputs are consumed: the block's L' comes into their place
+  if (threadIdx.x == 0) {
+    tma::mbar_expect_tx(bar, (uint32_t)(sizeof(float) * TT::LT));
+    tma::load_4d(in, &tl, line0, yi, zi, 0, bar);
   }
+
+  // 2. faces fi = warp, warp + NW (face m+1/2 with m = seg0-1+fi): f+ at staged cells
+  //    fi .. fi+4, f- at fi+1 .. fi+5
+  constexpr int MAXP = (T::FACES + NW - 1) / NW;
+  float Fh[MAXP][NV];
+#pragma unroll
+  for (int ps = 0; ps < MAXP; ps++) {
+    const int fi = warp + ps * NW;
+    if (fi < nface) {
+#pragma unroll
+      for (int c = 0; c < NV; c++) {
+        const float *fp = sfp + (c * (LEN - 1) + fi) * R + lane;
+        const float *fm = sfm + (c * (LEN - 1) + fi) * R + lane;   // f- of staged cell fi+1
+        if constexpr (SCHEME == IBFSA_TENO5)
+          Fh[ps][c] = teno5_pm(p, make_float2(fp[0], fm[4 * R]), make_float2(fp[R], fm[3 * R]),
+                               make_float2(fp[2 * R], fm[2 * R]), make_float2(fp[3 * R], fm[R]),
+                               make_float2(fp[4 * R], fm[0]));
+        else
+          Fh[ps][c] = recon<SCHEME>(p, fp[0], fp[R], fp[2 * R], fp[3 * R], fp[4 * R]) +
+                      recon<SCHEME>(p, fm[4 * R], fm[3 * R], fm[2 * R], fm[R], fm[0]);
+      }
+    }
+  }
+  __syncthreads();
+  float *sh = sfp;  // face fluxes [NV][R][FST]
+#pragma unroll
+  for (int ps = 0; ps < MAXP; ps++) {
+    const int fi = warp + ps * NW;
+    if (fi < nface) {
+#pragma unroll
+      for (int c = 0; c < NV; c++) sh[(c * R + lane) * FST + fi] = Fh[ps][c];
+    }
+  }
+  __syncthreads();
+  if (__syncthreads_or(!tma::mbar_wait(bar, 1))) {
+    if (threadIdx.x == 0) {
+      atomicOr(p.status, IBFSA_STATUS_TIMEOUT);
+      tma::mbar_wait(bar, 1);
+    }
+    return;
+  }
+
+  // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / h on the copied tile, then stored back
+  const float inv_h = p.inv_h32[A];
+  if (row_ok) {
+    for (int l = warp; l < ncell; l += NW) {
+#pragma unroll
+      for (int c = 0; c < NV; c++) {
+        const float *hh = sh + (c * R + lane) * FST;
+        in[(c * SEG + l) * R + lane] -= (hh[l + 1] - hh[l]) * inv_h;
+      }
+    }
+  }
+  tma::fence_async_shared();
+  __syncthreads();
+  if (threadIdx.x == 0) tma::store_4d(&tl, line0, yi, zi, 0, in);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1070,18 +1197,30 @@ cudaError_t conv_tensor_maps(const Plan &p, CUtensorMap *tq, CUtensorMap *tw, CU
   return tma::encode_f32_4d(tl, p.L32, dl, is, bl);
 }
 
-template <int DIM, int A, int SCHEME, bool TMA>
-cudaError_t launch_conv_as(const Plan &p, int first, cudaStream_t st) {
+template <int DIM, int A, int SCHEME>
+cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
   using T = Tile<A>;
-  constexpr size_t smem =
-      conv_smem<DIM, A, TMA>() + (SCHEME == IBFSA_MLP_TENO5 ? (size_t)mlp::PACKED_BYTES : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_conv32<DIM, A, SCHEME, TMA>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  CUtensorMap tq{}, tw{}, tl{};
-  if constexpr (TMA) {
-    if ((e = conv_tensor_maps<DIM, A>(p, &tq, &tw, &tl)) != cudaSuccess) return e;
+  cudaError_t e;
+  if constexpr (A != 0 && SCHEME != IBFSA_MLP_TENO5) {
+    if (p.n[0] % 4 == 0 && !first) {
+      using TT = TmaTile<DIM, A>;
+      e = cudaFuncSetAttribute(k_conv32_tma<DIM, A, SCHEME>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::BYTES);
+      if (e != cudaSuccess) return e;
+      CUtensorMap tq, tw, tl;
+      if ((e = conv_tensor_maps<DIM, A>(p, &tq, &tw, &tl)) != cudaSuccess) return e;
+      int nseg = (p.n[A] + T::SEG - 1) / T::SEG;
+      int nx = (p.n[0] + T::ROWS - 1) / T::ROWS;
+      dim3 grid(nseg * nx, A == 1 ? p.n[2] : p.n[1]);
+      k_conv32_tma<DIM, A, SCHEME><<<grid, THREADS, TT::BYTES, st>>>(p, tq, tw, tl);
+      return cudaGetLastError();
+    }
   }
+  constexpr size_t smem =
+      conv_smem<DIM, A>() + (SCHEME == IBFSA_MLP_TENO5 ? (size_t)mlp::PACKED_BYTES : 0);
+  e = cudaFuncSetAttribute(k_conv32<DIM, A, SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
   dim3 grid;
   if (A == 0) {
     grid = dim3((p.n[0] + T::SEG - 1) / T::SEG, (p.n[1] + T::ROWS - 1) / T::ROWS, p.n[2]);
@@ -1090,18 +1229,8 @@ cudaError_t launch_conv_as(const Plan &p, int first, cudaStream_t st) {
     int nx = (p.n[0] + T::ROWS - 1) / T::ROWS;
     grid = dim3(nseg * nx, A == 1 ? p.n[2] : p.n[1]);
   }
-  k_conv32<DIM, A, SCHEME, TMA><<<grid, THREADS, smem, st>>>(p, first, tq, tw, tl);
+  k_conv32<DIM, A, SCHEME><<<grid, THREADS, smem, st>>>(p, first);
   return cudaGetLastError();
-}
-
-// y and z passes of the fixed schemes use the tensor copies when every stride of the copied
-// tensors is a multiple of 16 bytes (x extent a multiple of 4)
-template <int DIM, int A, int SCHEME>
-cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
-  if constexpr (A != 0 && SCHEME != IBFSA_MLP_TENO5) {
-    if (p.n[0] % 4 == 0) return launch_conv_as<DIM, A, SCHEME, true>(p, first, st);
-  }
-  return launch_conv_as<DIM, A, SCHEME, false>(p, first, st);
 }
 
 template <int DIM, int SCHEME>

@@ -61,9 +61,17 @@ def case_3d_weno_periodic(n=(16, 12, 20)):
     return dict(spec=spec, Q=Q, X=None, U=None, dS=None, xi=None, dt=0.1 * spec.h[0])
 
 
+def case_3d_teno_x36():
+    """3D TENO5 with an x extent that is a multiple of 4 (the FP32 y/z passes then stage their
+    tiles with tensor copies): one full and one 4-line tile in x, ragged 15-cell segments in y
+    and z."""
+    return case_3d_teno(n=(36, 19, 17))
+
+
 ALL = {
     "2d_weno": case_2d_weno,
     "2d_teno_stream": case_2d_teno_stream,
     "3d_teno": case_3d_teno,
+    "3d_teno_x36": case_3d_teno_x36,
     "3d_weno_periodic": case_3d_weno_periodic,
 }
