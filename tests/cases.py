@@ -68,6 +68,28 @@ def case_3d_teno_x36():
     return case_3d_teno(n=(36, 19, 17))
 
 
+def cylinder_scattering(ppd, t_end=8.0, sample=0.1, precision=W.FP64):
+    """Sec. 3.1's pulse scattered by a rigid cylinder (D = 1 at the origin, pulse at (4, 0)) on
+    the window [-6, 8] x [-6, 6], from which no boundary reflection reaches the probes (2, 0)
+    and (2, 2) before t = 8; D/h = ppd, WENO5-JS, Re 1e4, markers at most h/2 apart (at least
+    the 160 of the 256^2 set-up), dt = sample / m with CFL <= 0.5."""
+    h = 1.0 / ppd
+    nx, ny = int(round(14.0 * ppd)), int(round(12.0 * ppd))
+    lo = (-6.0, -0.5 * ny * h, 0.0)
+    spec = W.GridSpec(dim=2, n=(nx, ny, 1), lo=lo, hi=(lo[0] + nx * h, 0.5 * ny * h, 1.0),
+                      gamma=1.4, Re=1e4, qinf=W.freestream(2, 1.4), scheme=W.WENO5JS,
+                      precision=precision)
+    m = int(math.ceil(4.0 * sample * ppd))
+    dt = sample / m
+    markers = max(160, int(math.ceil(2.0 * math.pi * 0.5 / (0.5 * h))))
+    spec.max_markers = markers
+    spec.alpha_pen, spec.beta_pen = W.penalty_defaults(h, dt)
+    X, U, dS = W.circle_markers(markers, 0.5, seed=0)
+    return dict(spec=spec, Q=W.gaussian_pulse_state(spec, (4.0, 0.0)), X=X, U=U, dS=dS, dt=dt,
+                every=m, samples=int(round(t_end / sample)), sample=sample,
+                probes=np.array([[2.0, 2.0], [0.0, 2.0]]))
+
+
 ALL = {
     "2d_weno": case_2d_weno,
     "2d_teno_stream": case_2d_teno_stream,
