@@ -41,20 +41,7 @@
 
 #define NG 4 /* ghost layers: viscous D4 of D4 reaches +-4 */
 
-typedef struct {
-  int dim;              /* 2 or 3 */
-  int n[3];             /* interior cells per direction (n[2] = 1 in 2D) */
-  double lo[3], hi[3];  /* domain box; h_d = (hi_d - lo_d)/n_d, nodes at lo + (i+1/2) h */
-  double gamma, Re;     /* Re <= 0: inviscid */
-  double qinf[5];       /* free-stream conservative state [rho, m_x, m_y, (m_z), E] */
-  int scheme;           /* 0 = WENO5-JS, 1 = TENO5 */
-  int bc[3][2];         /* 0 = zero gradient, 1 = free stream, 2 = periodic */
-  int sponge_cells;     /* 0: no sponge */
-  double sponge_sigma;  /* sigma_max */
-  double alpha_pen, beta_pen; /* Eq. 7 constants */
-} orc_desc;
-
-enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_BOUNDS = -4, ORC_ERR_NOMEM = -7 };
+#include "ibfsa_oracle.h"
 
 /* ----------------------------------------------------------------------------------------- */
 /* Peskin 4-point kernel, Eq. 11                                                              */

@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ibfsa_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "plate_oracle.c"), os.path.join(_HERE, "ibfsa_oracle.h")]
 _LIB = os.path.join(_HERE, "libibfsa_oracle.so")
 
 ORC_OK = 0
@@ -23,10 +24,12 @@ ORC_ERR_BOUNDS = -4
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with plain gcc: -O2, no fused multiply-add contraction."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle (fluid stage and plate) with plain gcc: -O2, no fused multiply-add
+    contraction."""
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared",
-               "-o", _LIB, _SRC, "-lm"]
+               "-o", _LIB, *[f for f in _SRCS if f.endswith(".c")], "-lm"]
         subprocess.check_call(cmd)
     return _LIB
 
@@ -218,3 +221,160 @@ def spread_scalar(spec, X, Fk, dS):
     if rc != ORC_OK:
         raise RuntimeError(f"oracle spread failed: {rc}")
     return f
+
+
+# --------------------------------------------------------------------------------------------
+# Flexible plate (Eq. 1, ANCF) and the coupled plate-fluid step (oracle/plate_oracle.c)
+# --------------------------------------------------------------------------------------------
+
+class OrcPlate(ctypes.Structure):
+    _fields_ = [
+        ("n_el", ctypes.c_int),
+        ("n_markers", ctypes.c_int),
+        ("length", ctypes.c_double),
+        ("rho_s", ctypes.c_double),
+        ("K_S", ctypes.c_double),
+        ("K_B", ctypes.c_double),
+        ("clamped", ctypes.c_int),
+        ("x0", ctypes.c_double * 2),
+        ("theta0", ctypes.c_double),
+        ("A0", ctypes.c_double),
+        ("freq", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("alpha_m", ctypes.c_double),
+        ("phi", ctypes.c_double),
+        ("newton_max", ctypes.c_int),
+        ("newton_tol", ctypes.c_double),
+    ]
+
+
+ORC_PLATE_NOCONV = -8
+_I = ctypes.POINTER(ctypes.c_int)
+_plate_ready = False
+
+
+def _plate_lib():
+    global _plate_ready
+    L = lib()
+    if not _plate_ready:
+        P = ctypes.POINTER(OrcPlate)
+        L.orc_plate_motion.restype = None
+        L.orc_plate_motion.argtypes = [P, ctypes.c_double, _D, _D]
+        L.orc_plate_markers.argtypes = [P, _D, _D, _D, _D, _D]
+        L.orc_plate_load.argtypes = [P, _D, _D]
+        L.orc_plate_internal.argtypes = [P, _D, _D, _D, _D]
+        L.orc_plate_step.argtypes = [P, _D, _D, ctypes.c_double, ctypes.c_double, _D, _I]
+        L.orc_plate_static.argtypes = [P, _D, _D, _I]
+        L.orc_fsi_step.argtypes = [ctypes.POINTER(OrcDesc), P, _D, _D, _D, _D, _D,
+                                   ctypes.c_double, ctypes.c_int, _I]
+        _plate_ready = True
+    return L
+
+
+def plate_desc(ps) -> OrcPlate:
+    d = OrcPlate()
+    d.n_el = int(ps.n_el)
+    d.n_markers = int(ps.n_markers)
+    d.length = float(ps.length)
+    d.rho_s = float(ps.rho_s)
+    d.K_S = float(ps.K_S)
+    d.K_B = float(ps.K_B)
+    d.clamped = int(ps.clamped)
+    d.x0[0], d.x0[1] = float(ps.x0[0]), float(ps.x0[1])
+    d.theta0 = float(ps.theta0)
+    d.A0 = float(ps.A0)
+    d.freq = float(ps.freq)
+    d.beta = float(ps.beta)
+    d.alpha_m = float(ps.alpha_m)
+    d.phi = float(ps.phi)
+    d.newton_max = int(ps.newton_max)
+    d.newton_tol = float(ps.newton_tol)
+    return d
+
+
+def plate_motion(ps, t):
+    """Prescribed clamp coordinates and rates of node 0 at time t (Eq. 17)."""
+    e4, v4 = np.zeros(4), np.zeros(4)
+    d = plate_desc(ps)
+    _plate_lib().orc_plate_motion(ctypes.byref(d), float(t), _p(e4), _p(v4))
+    return e4, v4
+
+
+def plate_markers(ps, e, v):
+    e, v = _f64(e), _f64(v)
+    nm = ps.n_markers
+    X, U, dS = np.zeros((2, nm)), np.zeros((2, nm)), np.zeros(nm)
+    d = plate_desc(ps)
+    rc = _plate_lib().orc_plate_markers(ctypes.byref(d), _p(e), _p(v), _p(X), _p(U), _p(dS))
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle plate markers failed: {rc}")
+    return X, U, dS
+
+
+def plate_load(ps, F):
+    F = _f64(F)
+    Qf = np.zeros(4 * (ps.n_el + 1))
+    d = plate_desc(ps)
+    rc = _plate_lib().orc_plate_load(ctypes.byref(d), _p(F), _p(Qf))
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle plate load failed: {rc}")
+    return Qf
+
+
+def plate_internal(ps, e, tangent=False, mass=False):
+    """Internal force Q_int(e); optionally the dense tangent dQ_int/de and mass matrix."""
+    e = _f64(e)
+    nd = 4 * (ps.n_el + 1)
+    Q = np.zeros(nd)
+    K = np.zeros((nd, nd)) if tangent else None
+    M = np.zeros((nd, nd)) if mass else None
+    d = plate_desc(ps)
+    rc = _plate_lib().orc_plate_internal(ctypes.byref(d), _p(e), _p(Q), _p(K), _p(M))
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle plate internal failed: {rc}")
+    return Q, K, M
+
+
+def plate_step(ps, e, v, t_new, dt, Qf=None, nsteps=1, t_step=None):
+    """nsteps implicit-midpoint steps under the generalised load Qf (constant); the clamp is
+    taken to t_new, t_new + dt, ... Returns (e, v, iterations of the last step)."""
+    e, v = _f64(e).copy(), _f64(v).copy()
+    Qf = None if Qf is None else _f64(Qf)
+    it = ctypes.c_int(0)
+    d = plate_desc(ps)
+    t = float(t_new)
+    for _ in range(nsteps):
+        rc = _plate_lib().orc_plate_step(ctypes.byref(d), _p(e), _p(v), t, float(dt), _p(Qf),
+                                         ctypes.byref(it))
+        if rc != ORC_OK:
+            raise RuntimeError(f"oracle plate step failed: {rc}")
+        t = t + float(dt)
+    return e, v, it.value
+
+
+def plate_static(ps, e0, Qf):
+    e = _f64(e0).copy()
+    Qf = _f64(Qf)
+    it = ctypes.c_int(0)
+    d = plate_desc(ps)
+    rc = _plate_lib().orc_plate_static(ctypes.byref(d), _p(e), _p(Qf), ctypes.byref(it))
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle plate static failed: {rc}")
+    return e, it.value
+
+
+def fsi_step(spec, ps, Q, xi, e, v, t, dt, nsteps=1):
+    """nsteps coupled plate-fluid steps; returns (Q, xi, e, v, t, Newton iterations per step)."""
+    Q = _f64(Q).copy()
+    xi = _f64(xi).copy()
+    e, v = _f64(e).copy(), _f64(v).copy()
+    tt = ctypes.c_double(float(t))
+    iters = (ctypes.c_int * max(1, nsteps))()
+    d = desc(spec)
+    pd = plate_desc(ps)
+    rc = _plate_lib().orc_fsi_step(ctypes.byref(d), ctypes.byref(pd), _p(Q), _p(xi), _p(e), _p(v),
+                                   ctypes.cast(ctypes.pointer(tt), _D), float(dt), int(nsteps),
+                                   ctypes.cast(iters, _I))
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle fsi step failed: {rc}")
+    return Q, xi, e, v, tt.value, list(iters)[:nsteps]

@@ -70,6 +70,63 @@ class GridSpec:
         return (self.nv, nz, ny, nx)
 
 
+@dataclasses.dataclass
+class PlateSpec:
+    """A flexible plate (Eq. 1) in absolute nodal coordinates: n_el equal elements, node j
+    carrying [x, y, x_s, y_s]; markers at s_k = (k + 1/2) L / n_markers.  clamped = 1: node 0
+    follows the clamp motion of Eq. 17, x0 + (A0/2) cos(2 pi f t) [cos beta, sin beta] with the
+    chord direction theta0 + (alpha_m/2) sin(2 pi f t + phi); clamped = 0: a free plate."""
+    n_el: int = 40
+    n_markers: int = 800
+    length: float = 1.0
+    rho_s: float = 1.0
+    K_S: float = 1.0
+    K_B: float = 1.0
+    clamped: int = 1
+    x0: tuple = (0.0, 0.0)
+    theta0: float = 0.0
+    A0: float = 0.0
+    freq: float = 0.0
+    beta: float = 0.0
+    alpha_m: float = 0.0
+    phi: float = 0.0
+    newton_max: int = 30
+    newton_tol: float = 1e-12
+
+    @property
+    def ndof(self) -> int:
+        return 4 * (self.n_el + 1)
+
+
+def plate_straight(ps: PlateSpec, origin=None, theta=None, omega: Optional[float] = None,
+                   vel=(0.0, 0.0)):
+    """Straight plate from `origin` (default: the clamp position at t = 0) along angle `theta`
+    (default: the clamp's chord direction at t = 0), moving rigidly with translation `vel` and
+    rotation rate `omega` about the origin (default for a clamped plate: the clamp's own rate
+    at t = 0, so the plate starts in step with its clamp).  Returns e, v [4 (n_el + 1)]."""
+    w = 2.0 * math.pi * ps.freq
+    if origin is None:
+        half = 0.5 * ps.A0
+        origin = (ps.x0[0] + half * math.cos(ps.beta), ps.x0[1] + half * math.sin(ps.beta))
+    if theta is None:
+        theta = ps.theta0 + 0.5 * ps.alpha_m * math.sin(ps.phi)
+    if omega is None:
+        omega = 0.5 * ps.alpha_m * w * math.cos(ps.phi) if ps.clamped else 0.0
+    s = np.arange(ps.n_el + 1) * (ps.length / ps.n_el)
+    c, sn = math.cos(theta), math.sin(theta)
+    e = np.zeros((ps.n_el + 1, 4))
+    e[:, 0] = origin[0] + s * c
+    e[:, 1] = origin[1] + s * sn
+    e[:, 2] = c
+    e[:, 3] = sn
+    v = np.zeros((ps.n_el + 1, 4))
+    v[:, 0] = vel[0] - omega * s * sn
+    v[:, 1] = vel[1] + omega * s * c
+    v[:, 2] = -omega * sn
+    v[:, 3] = omega * c
+    return e.ravel(), v.ravel()
+
+
 def splitmix64(seed: int, count: int) -> np.ndarray:
     """Uniform doubles in [0, 1) from the splitmix64 generator (Steele, Lea & Flood 2014)."""
     out = np.empty(count, dtype=np.float64)
@@ -274,6 +331,42 @@ def sphere_pulse_3d(n: int = 512, markers: int = 20000, Re: float = 1e4, scheme:
     X, U, dS = fibonacci_sphere(markers, 0.5)
     pr, _, _ = fibonacci_sphere(probes, 6.0 * L / 8.0)
     return dict(spec=spec, Q=Q, X=X, U=U, dS=dS, dt=dt, steps=2000, probes=pr)
+
+
+def flapping_plate_2d(n=(4096, 2048), n_el: int = 40, markers: int = 800,
+                      scheme: int = TENO5, precision: int = FP32_PERTURB):
+    """Flexible plate flapping in a uniform stream (Sec. 4.1 set-up, Eq. 17-18): chord L = 1,
+    40 elements, thickness ratio 0.01, mass ratio m* = rho_s/(rho_f L) = 1, bending stiffness
+    K_B/(rho_f U^2 L^3) = 0.5, clamped leading edge heaving with amplitude A0/2 = 0.5 across the
+    stream (beta = 90 deg) and pitching with amplitude alpha_m/2 = 30 deg, Mach number
+    M = pi U/(2c) = 0.1 with U = 2 f A0, free stream U0 = 0.4 U (U_r of Sec. 4.1),
+    Re = rho_f U L / mu = 200; uniform grid on [-20,20]x[-10,10] with free-stream ghosts and a
+    20-cell sponge; 800 markers; 360 probes on a ring r = 8 around the mean clamp position.
+    Units: rho_f = 1, c = 1, L = 1 (the solver's Re is then rho_f c L / mu)."""
+    g = 1.4
+    M = 0.1
+    U = 2.0 * M / math.pi            # M = pi U / (2 c)
+    A0 = 1.0
+    f = U / (2.0 * A0)               # U = 2 f A0
+    U0 = 0.4 * U
+    Re_flow = 200.0
+    K_B = 0.5 * U * U                # K_B / (rho_f U^2 L^3) = 0.5
+    K_S = 12.0 * K_B / (0.01 ** 2)   # plate of thickness ratio 0.01: E A / E I = 12 / t^2
+    spec = GridSpec(dim=2, n=(n[0], n[1], 1), lo=(-20.0, -10.0, 0.0), hi=(20.0, 10.0, 1.0),
+                    gamma=g, Re=Re_flow / U, qinf=freestream(2, g, vel=(U0, 0.0, 0.0)),
+                    scheme=scheme, precision=precision, bc=((1, 1), (1, 1), (0, 0)),
+                    sponge_cells=20, max_markers=markers)
+    h = min(spec.h[0], spec.h[1])
+    dt = 0.5 / ((1.0 + U0) / spec.h[0] + 1.0 / spec.h[1])
+    spec.alpha_pen, spec.beta_pen = penalty_defaults(h, dt)
+    spec.sponge_sigma = 0.5 * (1.0 + U0) / h
+    ps = PlateSpec(n_el=n_el, n_markers=markers, length=1.0, rho_s=1.0, K_S=K_S, K_B=K_B,
+                   clamped=1, x0=(-0.5, 0.0), theta0=0.0, A0=A0, freq=f,
+                   beta=0.5 * math.pi, alpha_m=math.radians(60.0), phi=0.0)
+    e, v = plate_straight(ps)
+    Q = random_smooth_state(spec, seed=3, amp=0.0, modes=1, vel0=(U0, 0.0, 0.0))
+    probes = ring_probes(360, 8.0, center=(-0.5, 0.0))
+    return dict(spec=spec, plate=ps, Q=Q, e=e, v=v, dt=dt, probes=probes, U_ref=U)
 
 
 def gaussian_pulse_state_torch(spec: GridSpec, center, amp: float = 1e-3, halfwidth: float = 0.2,
