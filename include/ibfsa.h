@@ -163,7 +163,8 @@ int ibfsa_get_status(ibfsa_grid *g, int *host_flags);
  * with profiling enabled every launch is bracketed by CUDA events on the grid's stream.
  * Classes, in order: 0 pad (ghosts, primitives, split speeds), 1 IB interpolation and penalty
  * force, 2-4 convective x/y/z, 5 viscous fluxes, 6 viscous divergence, 7 IB spreading,
- * 8 finish (sponge, source, RK combination), 9 probes.  ibfsa_profile_read synchronises the
+ * 8 finish (sponge, source, RK combination), 9 probes, 10 plate (markers from the plate, stage
+ * force averaging, structure step; ibfsa_fsi_step).  ibfsa_profile_read synchronises the
  * stream, copies up to nclass entries (milliseconds summed over timed launches, launches,
  * timed launches; any pointer may be NULL) and resets the counters. */
 int ibfsa_profile_enable(ibfsa_grid *g, int enable);
@@ -218,6 +219,73 @@ int ibfsa_mlp_stats(ibfsa_grid *g, unsigned long long *host_counts);
  * first min(count, n_max) were written).  attempts: candidate faces drawn per thread. */
 int ibfsa_mlp_sample(ibfsa_grid *g, int n_max, unsigned long long seed, int attempts,
                      float *d_stencils, float *d_targets, int *d_count);
+
+/* ---- Flexible plate and two-way coupling (Sec. 2, Eq. 1; Sec. 4.1, Eq. 17) ----------------
+ * A plate immersed in a 2D fluid, governed by Eq. 1 and discretised in the absolute nodal
+ * coordinate formulation named by the paper: n_el equal elements of length l = L / n_el; node j
+ * carries e_j = [x, y, x_s, y_s] (position and slope); inside an element r(s) is the cubic
+ * Hermite interpolation of the two nodes.  Eq. 1 is taken as the Euler-Lagrange equation of the
+ * kinetic energy 1/2 int rho_s |r_t|^2 ds and the elastic energy
+ * 1/2 int [K_S (|r_s| - 1)^2 + K_B |r_ss|^2] ds: consistent mass matrix, constant bending matrix,
+ * stretching force by five-point Gauss-Legendre quadrature.  Time: the implicit midpoint rule
+ *   e_{n+1} = e_n + dt (v_n + v_{n+1}) / 2,  M (v_{n+1} - v_n) = dt [Q_f - Q_int((e_n + e_{n+1})/2)],
+ * solved by Newton's method (banded LDL^T, half-bandwidth 7) in one thread block, in FP64 with
+ * every operation rounded separately (reproducible bit for bit by a sequential evaluation).
+ * Load: the penalty force F_k of Eq. 7 (force of the fluid on the structure, per unit length) at
+ * markers s_k = (k + 1/2) L / n_markers, dS_k = L / n_markers: Q_f = sum_k S(s_k)^T F_k dS_k in
+ * marker order.  Clamp (IBFSA_PLATE_CLAMPED): node 0 at x0 + (A0/2) cos(2 pi f t)[cos b, sin b]
+ * with its slope along [cos(theta0 + a), sin(theta0 + a)], a = (alpha_m/2) sin(2 pi f t + phi)
+ * (Eq. 17); the slope's length stays free.  Layouts: e, v [4 (n_el + 1)] node-major; marker
+ * arrays [2][n_markers].  Memory: one caller-owned workspace of ibfsa_plate_workspace_bytes(),
+ * 256-byte aligned; the library allocates nothing.  Work goes to the stream given at creation;
+ * Newton failures (iteration limit, zero or non-finite pivot, non-finite increment) set
+ * IBFSA_STATUS_NOCONV, read with ibfsa_plate_get_status. */
+enum { IBFSA_PLATE_FREE = 0, IBFSA_PLATE_CLAMPED = 1 };
+enum { IBFSA_STATUS_NOCONV = 8 };
+#define IBFSA_PLATE_MAX_EL 128
+typedef struct ibfsa_plate ibfsa_plate; /* opaque; created and destroyed by the library */
+typedef struct {
+  int n_el;              /* elements, 1..IBFSA_PLATE_MAX_EL */
+  int n_markers;         /* Lagrangian markers along the plate, >= 1 */
+  double length;         /* L */
+  double rho_s;          /* mass per unit length (Eq. 1) */
+  double K_S, K_B;       /* stretching and bending rigidity (Eq. 1) */
+  int clamp;             /* IBFSA_PLATE_FREE | IBFSA_PLATE_CLAMPED */
+  double x0[2];          /* clamp mean position */
+  double theta0;         /* chord direction of the clamp at a = 0 */
+  double A0, freq, beta, alpha_m, phi;  /* clamp motion, Eq. 17 */
+  int newton_max;        /* Newton iteration limit (>= 1) */
+  double newton_tol;     /* converged when max |Newton increment| <= newton_tol * L */
+} ibfsa_plate_desc;
+
+int ibfsa_plate_workspace_bytes(const ibfsa_plate_desc *desc, size_t *bytes);
+/* Create a plate on the current device; the state is undefined until ibfsa_plate_set_state. */
+int ibfsa_plate_create(const ibfsa_plate_desc *desc, void *d_workspace, size_t workspace_bytes,
+                       void *cuda_stream, ibfsa_plate **out);
+int ibfsa_plate_destroy(ibfsa_plate *p);
+/* Nodal coordinates e and rates v (device or host) and the time t of the clamp motion. */
+int ibfsa_plate_set_state(ibfsa_plate *p, const double *e, const double *v, double t);
+/* Copy e, v out (device or host; either may be NULL) and the time to *host_t (may be NULL);
+ * synchronises when an output is host memory. */
+int ibfsa_plate_get_state(ibfsa_plate *p, double *e, double *v, double *host_t);
+/* One step of size dt > 0 under marker forces F [2][n_markers] (device or host; NULL = none),
+ * held over the step; the clamp is taken to t + dt. */
+int ibfsa_plate_step(ibfsa_plate *p, double dt, const double *F);
+/* Marker positions X, velocities U [2][n_markers] and weights dS [n_markers] of the current
+ * state (device or host; synchronises when an output is host memory). */
+int ibfsa_plate_markers(ibfsa_plate *p, double *X, double *U, double *dS);
+/* Status bits (IBFSA_STATUS_NOCONV) and the largest Newton iteration count since the last
+ * call (either pointer may be NULL); clears both; synchronises. */
+int ibfsa_plate_get_status(ibfsa_plate *p, int *host_flags, int *host_max_iters);
+
+/* nsteps coupled steps of plate and fluid (2D grid with max_markers >= n_markers; the grid's
+ * stream must be the plate's): the grid's markers take the plate's positions, velocities and
+ * weights at the step start and keep them for the three SSP-RK3 stages (ibfsa_rk3_step); the
+ * plate then steps under Fbar = F1/6 + F2/6 + 2 F3/3 of the stages' penalty forces -- the
+ * weights the Runge-Kutta update gives the stages -- so the impulse the fluid receives through
+ * Eq. 9 is exactly the opposite of the plate's.  The penalty integral xi carries over between
+ * calls (zero it when the coupling starts, e.g. ibfsa_set_markers(..., 1)).  Asynchronous. */
+int ibfsa_fsi_step(ibfsa_grid *g, ibfsa_plate *p, double dt, int nsteps);
 
 /* Allocation-free right-hand side.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- plug-ins whose host application owns the whole

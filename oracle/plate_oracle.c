@@ -278,25 +278,38 @@ int orc_plate_internal(const orc_plate *p, const double *e, double *Qint, double
   return ORC_OK;
 }
 
-/* Banded LDL^T solve of the symmetric system A x = b in place: A[i][k] = A(i, i + k),
- * k = 0..BW, n rows; b is overwritten by x.  Returns 0, or -1 on a zero or non-finite pivot. */
-static int band_ldlt_solve(double (*A)[BW + 1], double *b, int n) {
+/* Banded LDL^T factorisation of the symmetric matrix A (A[i][k] = A(i, i + k), k = 0..BW, n
+ * rows) in place: afterwards A[i][k], k >= 1, holds L(i + k, i), and rinv[i] = 1 / D(i).
+ * Returns 0, or -1 on a zero or non-finite pivot. */
+static int band_ldlt_factor(double (*A)[BW + 1], double *rinv, int n) {
   for (int i = 0; i < n; i++) {
     double d = A[i][0];
     if (!(d != 0.0) || !isfinite(d)) return -1;
+    double r = 1.0 / d;
+    rinv[i] = r;
     double lk[BW + 1];
-    for (int k = 1; k <= BW && i + k < n; k++) lk[k] = A[i][k] / d;
+    for (int k = 1; k <= BW && i + k < n; k++) lk[k] = A[i][k] * r;
     for (int k = 1; k <= BW && i + k < n; k++)
       for (int m = k; m <= BW && i + m < n; m++)
         A[i + k][m - k] = A[i + k][m - k] - lk[k] * A[i][m];
     for (int k = 1; k <= BW && i + k < n; k++) A[i][k] = lk[k];
   }
+  return 0;
+}
+
+/* Solve L D L^T x = b with the factors; b is overwritten by x.  In the back substitution the
+ * seven products of a row are summed pairwise, ((p1 + p2) + (p3 + p4)) + ((p5 + p6) + p7), a
+ * missing product (past the last row) counting as zero. */
+static void band_ldlt_solve(double (*A)[BW + 1], const double *rinv, double *b, int n) {
   for (int i = 0; i < n; i++)
     for (int k = 1; k <= BW && i + k < n; k++) b[i + k] = b[i + k] - A[i][k] * b[i];
-  for (int i = 0; i < n; i++) b[i] = b[i] / A[i][0];
-  for (int i = n - 1; i >= 0; i--)
-    for (int k = 1; k <= BW && i + k < n; k++) b[i] = b[i] - A[i][k] * b[i + k];
-  return 0;
+  for (int i = 0; i < n; i++) b[i] = b[i] * rinv[i];
+  for (int i = n - 1; i >= 0; i--) {
+    double pr[BW + 2];
+    for (int k = 1; k <= BW + 1; k++) pr[k] = (k <= BW && i + k < n) ? A[i][k] * b[i + k] : 0.0;
+    double s = ((pr[1] + pr[2]) + (pr[3] + pr[4])) + ((pr[5] + pr[6]) + (pr[7] + pr[8]));
+    b[i] = b[i] - s;
+  }
 }
 
 /* Newton solve shared by the dynamic step (dt > 0) and the static solve (dt = 0).
@@ -319,7 +332,7 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
   element_mass(p, Ms);
   double *d = calloc(nd, sizeof(double)), *em = calloc(nd, sizeof(double));
   double *g = calloc(nd, sizeof(double)), *R = calloc(nd, sizeof(double));
-  double *x = calloc(nf, sizeof(double));
+  double *x = calloc(nf, sizeof(double)), *rinv = calloc(nf, sizeof(double));
   double (*Ag)[BW + 1] = calloc((size_t)nd, sizeof(*Ag));
   double (*A)[BW + 1] = calloc((size_t)nf, sizeof(*A));
   double (*Rel)[8] = calloc((size_t)ne, sizeof(*Rel));
@@ -390,26 +403,29 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
     /* the free system: right-hand side -R and the band */
     if (clamped) {
       x[0] = -(tc * R[2] + ts * R[3]);
+      for (int i = 1; i < nf; i++) x[i] = -R[i + 3];
+    } else {
+      for (int i = 0; i < nf; i++) x[i] = -R[i];
+    }
+    if (clamped) {
       A[0][0] = tc * (tc * Ag[2][0] + ts * Ag[2][1]) + ts * (tc * Ag[2][1] + ts * Ag[3][0]);
       for (int k = 1; k <= BW; k++) {
         int J = k + 3;
         double a2 = J - 2 <= BW ? Ag[2][J - 2] : 0.0;
         A[0][k] = tc * a2 + ts * Ag[3][J - 3];
       }
-      for (int i = 1; i < nf; i++) {
-        x[i] = -R[i + 3];
+      for (int i = 1; i < nf; i++)
         for (int k = 0; k <= BW; k++) A[i][k] = Ag[i + 3][k];
-      }
     } else {
-      for (int i = 0; i < nf; i++) {
-        x[i] = -R[i];
+      for (int i = 0; i < nf; i++)
         for (int k = 0; k <= BW; k++) A[i][k] = Ag[i][k];
-      }
     }
-    if (band_ldlt_solve(A, x, nf) != 0) { rc = ORC_PLATE_NOCONV; break; }
+    if (band_ldlt_factor(A, rinv, nf) != 0) { rc = ORC_PLATE_NOCONV; break; }
+    band_ldlt_solve(A, rinv, x, nf);
     /* update: sigma moves the clamped slope along t */
     double *u = dynamic ? d : e;
     double inc = 0.0;
+    int bad = 0;
     for (int i = 0; i < nf; i++) {
       if (clamped && i == 0) {
         u[2] = u[2] + tc * x[0];
@@ -419,8 +435,10 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
         u[I] = u[I] + x[i];
       }
       double a = fabs(x[i]);
-      if (!(a <= inc)) inc = a; /* a NaN increment never converges */
+      if (isnan(a)) bad = 1;
+      else if (a > inc) inc = a;
     }
+    if (bad) { rc = ORC_PLATE_NOCONV; break; } /* a non-finite increment never converges */
     if (inc <= p->newton_tol * p->length) { rc = ORC_OK; break; }
   }
   if (iters) *iters = it > p->newton_max ? p->newton_max : it;
@@ -436,7 +454,8 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
       }
     }
   }
-  free(d); free(em); free(g); free(R); free(x); free(Ag); free(A); free(Rel); free(Jel);
+  free(d); free(em); free(g); free(R); free(x); free(rinv); free(Ag); free(A); free(Rel);
+  free(Jel);
   return rc;
 }
 

@@ -1,7 +1,8 @@
 """Build libibfsa.so in-tree with nvcc for sm_103a (GB300).
 
-Each translation unit is compiled in parallel; the strict-arithmetic unit gets --fmad=false so
-that no multiply and add are fused there.
+Each translation unit is compiled in parallel; the strict-arithmetic units (the FP64 stage and the
+plate) get --fmad=false so that no multiply and add are fused there, and the plate's host code
+(the clamp motion) -ffp-contract=off for the same reason.
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ UNITS = {
     "stage_fp32.cu": ["--fmad=true"],
     "mlp.cu": ["--fmad=true"],
     "noalloc.cu": [],
+    "plate.cu": ["--fmad=false", "-Xcompiler", "-ffp-contract=off"],
 }
 
 

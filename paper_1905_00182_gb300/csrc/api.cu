@@ -224,13 +224,13 @@ static cudaError_t run_stage(Grid *G, const StageArgs &s) {
   return G->d.strict_fp ? strict_stage(G->p, s, G->stream) : fast_stage(G->p, s, G->stream);
 }
 
+cudaError_t grid_stage(Grid *G, const StageArgs &s) { return run_stage(G, s); }
+
+int api_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+
 }  // namespace ibfsa
 
 using namespace ibfsa;
-
-struct ibfsa_grid {
-  Grid g;
-};
 
 extern "C" {
 

@@ -70,7 +70,7 @@ struct Plan {
 // Kernel classes for launch counting and CUDA-event timing (instrumentation only).
 enum KClass {
   K_PAD = 0, K_INTERP, K_CONV_X, K_CONV_Y, K_CONV_Z, K_VISC_FLUX, K_VISC_DIV, K_SPREAD, K_FINISH,
-  K_PROBE, K_NCLASS
+  K_PROBE, K_PLATE, K_NCLASS
 };
 
 // Launch counters (always on) and, when enabled, event pairs around every launch on the grid's
@@ -150,4 +150,12 @@ cudaError_t strict_probe(const Plan &p, const double *Q, int np, const double *x
 cudaError_t fast_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
                        cudaStream_t st, Prof *pr);
 
+// One stage (or right-hand side) of a grid in its arithmetic form (api.cu).
+cudaError_t grid_stage(Grid *G, const StageArgs &s);
+int api_fail(int code, const char *msg);  // records the message, returns code
+
 }  // namespace ibfsa
+
+struct ibfsa_grid {
+  ibfsa::Grid g;
+};

@@ -27,6 +27,10 @@ IBFSA_ERR_WORKSPACE = -6
 IBFSA_STATUS_BOUNDS = 1
 IBFSA_STATUS_NONFINITE = 2
 IBFSA_STATUS_TIMEOUT = 4
+IBFSA_STATUS_NOCONV = 8
+IBFSA_PLATE_FREE = 0
+IBFSA_PLATE_CLAMPED = 1
+IBFSA_PLATE_MAX_EL = 128
 
 # every symbol include/ibfsa.h declares
 EXPORTS = (
@@ -37,12 +41,14 @@ EXPORTS = (
     "ibfsa_profile_enable", "ibfsa_profile_read", "ibfsa_rhs_noalloc",
     "ibfsa_mlp_state_bytes", "ibfsa_mlp_init", "ibfsa_mlp_train_step", "ibfsa_mlp_read",
     "ibfsa_mlp_eval", "ibfsa_set_mlp", "ibfsa_mlp_stats", "ibfsa_mlp_sample",
-    "ibfsa_body_force",
+    "ibfsa_body_force", "ibfsa_plate_workspace_bytes", "ibfsa_plate_create",
+    "ibfsa_plate_destroy", "ibfsa_plate_set_state", "ibfsa_plate_get_state", "ibfsa_plate_step",
+    "ibfsa_plate_markers", "ibfsa_plate_get_status", "ibfsa_fsi_step",
 )
 MLP_NPARAM = 2403
 
 KERNEL_CLASSES = ("pad", "ib_interp", "conv_x", "conv_y", "conv_z", "visc_flux", "visc_div",
-                  "ib_spread", "finish", "probe")
+                  "ib_spread", "finish", "probe", "plate")
 
 
 class IbfsaError(RuntimeError):
@@ -70,6 +76,27 @@ class GridDesc(ctypes.Structure):
         ("beta_pen", ctypes.c_double),
         ("max_markers", ctypes.c_int),
         ("max_probes", ctypes.c_int),
+    ]
+
+
+class PlateDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_el", ctypes.c_int),
+        ("n_markers", ctypes.c_int),
+        ("length", ctypes.c_double),
+        ("rho_s", ctypes.c_double),
+        ("K_S", ctypes.c_double),
+        ("K_B", ctypes.c_double),
+        ("clamp", ctypes.c_int),
+        ("x0", ctypes.c_double * 2),
+        ("theta0", ctypes.c_double),
+        ("A0", ctypes.c_double),
+        ("freq", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("alpha_m", ctypes.c_double),
+        ("phi", ctypes.c_double),
+        ("newton_max", ctypes.c_int),
+        ("newton_tol", ctypes.c_double),
     ]
 
 
@@ -114,6 +141,17 @@ def lib():
         L.ibfsa_mlp_sample.argtypes = [_P, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, _P, _P,
                                        _P]
         L.ibfsa_rhs_noalloc.argtypes = [D, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P]
+        PD = ctypes.POINTER(PlateDesc)
+        L.ibfsa_plate_workspace_bytes.argtypes = [PD, ctypes.POINTER(ctypes.c_size_t)]
+        L.ibfsa_plate_create.argtypes = [PD, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]
+        L.ibfsa_plate_destroy.argtypes = [_P]
+        L.ibfsa_plate_set_state.argtypes = [_P, _P, _P, ctypes.c_double]
+        L.ibfsa_plate_get_state.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]
+        L.ibfsa_plate_step.argtypes = [_P, ctypes.c_double, _P]
+        L.ibfsa_plate_markers.argtypes = [_P, _P, _P, _P]
+        L.ibfsa_plate_get_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]
+        L.ibfsa_fsi_step.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -339,6 +377,73 @@ class MLP:
         return face, omega, (float(loss.item()) if targets is not None else None)
 
 
+def plate_desc_from_spec(ps: W.PlateSpec) -> PlateDesc:
+    d = PlateDesc()
+    d.n_el = int(ps.n_el)
+    d.n_markers = int(ps.n_markers)
+    d.length = float(ps.length)
+    d.rho_s = float(ps.rho_s)
+    d.K_S = float(ps.K_S)
+    d.K_B = float(ps.K_B)
+    d.clamp = IBFSA_PLATE_CLAMPED if ps.clamped else IBFSA_PLATE_FREE
+    d.x0[0], d.x0[1] = float(ps.x0[0]), float(ps.x0[1])
+    d.theta0 = float(ps.theta0)
+    d.A0 = float(ps.A0)
+    d.freq = float(ps.freq)
+    d.beta = float(ps.beta)
+    d.alpha_m = float(ps.alpha_m)
+    d.phi = float(ps.phi)
+    d.newton_max = int(ps.newton_max)
+    d.newton_tol = float(ps.newton_tol)
+    return d
+
+
+def ibfsa_plate_workspace_bytes(desc: PlateDesc) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().ibfsa_plate_workspace_bytes(ctypes.byref(desc), ctypes.byref(n)))
+    return n.value
+
+
+def ibfsa_plate_create(desc: PlateDesc, workspace_ptr: int, workspace_bytes: int,
+                       stream_ptr: int):
+    h = _P()
+    _check(lib().ibfsa_plate_create(ctypes.byref(desc), workspace_ptr, workspace_bytes,
+                                    stream_ptr, ctypes.byref(h)))
+    return h
+
+
+def ibfsa_plate_destroy(p):
+    _check(lib().ibfsa_plate_destroy(p))
+
+
+def ibfsa_plate_set_state(p, e: int, v: int, t: float):
+    _check(lib().ibfsa_plate_set_state(p, e, v, float(t)))
+
+
+def ibfsa_plate_get_state(p, e: int, v: int) -> float:
+    t = ctypes.c_double(0.0)
+    _check(lib().ibfsa_plate_get_state(p, e, v, ctypes.byref(t)))
+    return t.value
+
+
+def ibfsa_plate_step(p, dt: float, F: int = 0):
+    _check(lib().ibfsa_plate_step(p, float(dt), F))
+
+
+def ibfsa_plate_markers(p, X: int, U: int, dS: int):
+    _check(lib().ibfsa_plate_markers(p, X, U, dS))
+
+
+def ibfsa_plate_get_status(p):
+    f, it = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().ibfsa_plate_get_status(p, ctypes.byref(f), ctypes.byref(it)))
+    return f.value, it.value
+
+
+def ibfsa_fsi_step(g, p, dt: float, nsteps: int = 1):
+    _check(lib().ibfsa_fsi_step(g, p, float(dt), int(nsteps)))
+
+
 # ---- convenience wrapper over torch tensors -------------------------------------------------
 
 def _dev_f64(x, device):
@@ -435,3 +540,74 @@ class Grid:
 
     def status(self) -> int:
         return ibfsa_get_status(self.h)
+
+
+class Plate:
+    """A flexible plate with its torch-allocated workspace on the current device and stream."""
+
+    def __init__(self, ps: W.PlateSpec, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libibfsa needs a CUDA device")
+        self.ps = ps
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.desc = plate_desc_from_spec(ps)
+        self.ws_bytes = ibfsa_plate_workspace_bytes(self.desc)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = (self.ws.data_ptr() + 255) & ~255
+        self.h = ibfsa_plate_create(self.desc, self.ws_ptr, self.ws_bytes,
+                                    self.stream.cuda_stream)
+        self._src = None
+
+    def close(self):
+        if self.h is not None:
+            ibfsa_plate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, e, v, t=0.0):
+        e = _dev_f64(e, self.device)
+        v = _dev_f64(v, self.device)
+        ibfsa_plate_set_state(self.h, e.data_ptr(), v.data_ptr(), t)
+        self._src = (e, v)
+
+    def get_state(self):
+        import torch
+        nd = self.ps.ndof
+        e = torch.empty(nd, dtype=torch.float64, device=self.device)
+        v = torch.empty(nd, dtype=torch.float64, device=self.device)
+        t = ibfsa_plate_get_state(self.h, e.data_ptr(), v.data_ptr())
+        return e, v, t
+
+    def step(self, dt, F=None):
+        if F is None:
+            ibfsa_plate_step(self.h, dt, 0)
+        else:
+            F = _dev_f64(F, self.device)
+            ibfsa_plate_step(self.h, dt, F.data_ptr())
+            self._src = self._src + (F,) if self._src else (F,)
+
+    def markers(self):
+        import torch
+        nm = self.ps.n_markers
+        X = torch.empty((2, nm), dtype=torch.float64, device=self.device)
+        U = torch.empty((2, nm), dtype=torch.float64, device=self.device)
+        dS = torch.empty(nm, dtype=torch.float64, device=self.device)
+        ibfsa_plate_markers(self.h, X.data_ptr(), U.data_ptr(), dS.data_ptr())
+        return X, U, dS
+
+    def status(self):
+        """(status bits, largest Newton iteration count) since the last call."""
+        return ibfsa_plate_get_status(self.h)
+
+
+def fsi_step(grid: Grid, plate: Plate, dt: float, nsteps: int = 1):
+    """nsteps coupled plate-fluid steps (ibfsa_fsi_step)."""
+    ibfsa_fsi_step(grid.h, plate.h, dt, nsteps)
+    grid.nm = plate.ps.n_markers

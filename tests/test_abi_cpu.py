@@ -70,3 +70,27 @@ def test_descriptor_validation(ib, field, value, code):
         ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec))
     assert e.value.code == code
     assert ib.lib().ibfsa_last_error()
+
+
+def test_plate_workspace_counts_buffers(ib):
+    ps = W.PlateSpec(n_el=40, n_markers=800)
+    nbytes = ib.ibfsa_plate_workspace_bytes(ib.plate_desc_from_spec(ps))
+    # e, v, Fbar, X, U, dS, marker shape values; marker elements and first marker per element
+    expect = 8 * (2 * 164 + 3 * 2 * 800 + 800 + 4 * 800) + 4 * (800 + 41)
+    assert expect <= nbytes <= expect + 11 * 256
+
+
+@pytest.mark.parametrize("field,value", [
+    ("n_el", 0), ("n_el", 129), ("n_markers", 0), ("length", 0.0), ("rho_s", -1.0),
+    ("K_S", -1.0), ("clamped", 3), ("newton_max", 0), ("newton_tol", 0.0),
+])
+def test_plate_descriptor_validation(ib, field, value):
+    ps = W.PlateSpec()
+    setattr(ps, field, value)
+    d = ib.plate_desc_from_spec(ps)
+    if field == "clamped":
+        d.clamp = value
+    with pytest.raises(ib.IbfsaError) as e:
+        ib.ibfsa_plate_workspace_bytes(d)
+    assert e.value.code == -1
+    assert ib.ibfsa_plate_workspace_bytes(ib.plate_desc_from_spec(W.PlateSpec())) > 0
