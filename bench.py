@@ -56,6 +56,9 @@ def parse():
                     help="skip the FP64 comparison run of the fp32 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "fsi"],
+                    help="sphere: the 512^3 headline; fsi: only the coupled flapping-plate step "
+                         "(4096x2048), e.g. for profiling")
     return ap.parse_args()
 
 
@@ -339,6 +342,54 @@ def job_throughput(ms_local, units_per_rank, dist=None, device="cpu"):
     return units_per_rank * world / (ms * 1e-3), ms
 
 
+def fsi_form(ib, barrier, max_ranks, world, warmup=3, steps=10, steps64=2):
+    """The coupled plate-fluid step on the flexible flapping plate workload (4096x2048, TENO5,
+    40-element FP64 plate, 800 markers): FP32 perturbation form and FP64 form, device-timed
+    with the per-class split (the plate class is the structure solve plus marker and force
+    bookkeeping)."""
+    import torch
+    w = W.flapping_plate_2d()
+    out = {"workload": "flexible plate flapping in a stream, 4096x2048 on [-20,20]x[-10,10], "
+                       "TENO5, Re 200, Ma 0.1, 40-element FP64 ANCF plate, 800 markers, "
+                       "one coupled step = one SSP-RK3 fluid step + one plate step"}
+    for prec, k in ((W.FP32_PERTURB, steps), (W.FP64, steps64)):
+        spec = W.GridSpec(**{**w["spec"].__dict__, "precision": prec})
+        g = ib.Grid(spec)
+        g.set_state(w["Q"])
+        pl = ib.Plate(w["plate"])
+        pl.set_state(w["e"], w["v"], 0.0)
+        X, U, dS = pl.markers()
+        g.set_markers(X, U, dS)
+        ib.fsi_step(g, pl, w["dt"], warmup)
+        torch.cuda.synchronize()
+        ib.ibfsa_profile_enable(g.h, True)
+        ib.ibfsa_profile_read(g.h)
+        pl.status()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        ib.fsi_step(g, pl, w["dt"], k)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = max_ranks(e0.elapsed_time(e1)) / k
+        prof = ib.ibfsa_profile_read(g.h)
+        flags, iters = pl.status()
+        key = "fp32" if prec == W.FP32_PERTURB else "fp64"
+        out[key] = {"value": spec.cells * 3 * world / (ms * 1e-3), "unit": "cell-updates/s",
+                    "ms_per_step": ms,
+                    "plate_ms_per_step": prof["plate"]["ms"] / k,
+                    "kernel_ms_per_step": {c: v["ms"] / k for c, v in prof.items() if v["timed"]},
+                    "newton_max_iterations": iters, "plate_status": flags,
+                    "grid_status": g.status()}
+        g.close()
+        pl.close()
+        del g, pl
+        torch.cuda.empty_cache()
+    out["fp32_speedup_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1905_00182_gb300 import ibfsa as ib
@@ -463,6 +514,8 @@ def run_ours(args, rank, world, local_rank):
                    (max_ranks(mss) * 1e-3),
                    "weights": "paper_1905_00182_gb300/mlp_weights.npz"}
 
+    fsi = fsi_form(ib, barrier, max_ranks, world) if (fp32 and args.compare) else None
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -524,11 +577,36 @@ def run_ours(args, rank, world, local_rank):
         out["forms"] = compare
         if learned is not None:
             out["forms"]["learned"] = learned
+        if fsi is not None:
+            out["forms"]["fsi"] = fsi
     if e2e is not None:
         out["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_fsi_only(args, rank, world, local_rank):
+    """The coupled flapping-plate step alone (one JSON line from rank 0)."""
+    import torch
+    from paper_1905_00182_gb300 import ibfsa as ib
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    barrier = (lambda: dist.barrier()) if dist is not None else (lambda: None)
+    r = fsi_form(ib, barrier, lambda x: max_over_ranks(x, dist, "cuda"), world,
+                 warmup=args.warmup, steps=args.steps, steps64=min(2, args.steps))
+    if rank == 0:
+        print(json.dumps({"metric": "coupled plate-fluid step cell-updates/s",
+                          "value": r["fp32"]["value"], "unit": "cell-updates/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "dtype": "f32",
+                          "data": "synthetic", "config": {"workload": r["workload"]},
+                          "fsi": r}), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -540,6 +618,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "fsi":
+        run_fsi_only(args, rank, world, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 

@@ -5,7 +5,8 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call this file:
  * only the test suite, the smoke check and the bench's CPU-baseline leg use it.  It shares no
- * source, header, table or helper with the CUDA path.  Compile with -O2 -ffp-contract=off.
+ * source, header, table or helper with the CUDA path.  Compile with -O2 -ffp-contract=off
+ * (the only fused multiply-adds are the explicit fma calls).
  *
  * The paper names the formulation (Shabana's ANCF) but prints neither the element nor the time
  * integrator; the readings taken here:
@@ -29,7 +30,9 @@
  *      e_{n+1} = e_n + dt (v_n + v_{n+1}) / 2,
  *      M (v_{n+1} - v_n) = dt [Q_f - Q_int((e_n + e_{n+1}) / 2)],
  *    solved by Newton's method for d = e_{n+1} - e_n; each Newton system is factorised by a
- *    banded LDL^T decomposition (half-bandwidth 7).  The rule conserves the linear and angular
+ *    banded LDL^T decomposition (half-bandwidth 7).  The multiply-adds of the element dot
+ *    products, of the elimination and of the forward substitution are single fused
+ *    operations (C99 fma, one rounding); everything else is rounded operation by operation.  The rule conserves the linear and angular
  *    momentum of an unloaded free plate and hands the plate exactly the impulse dt Q_f of the
  *    step's load, so what the fluid loses the plate gains.
  *  - Clamp (Sec. 4.1, Eq. 17): r(0, t) = x0 + (A0/2) cos(2 pi f t) [cos b, sin b], and the
@@ -147,7 +150,7 @@ static void element_internal(const orc_plate *p, const double *ee, double Qi[8],
     dshape(xi, l, D[g]);
     for (int a = 0; a < 2; a++) {
       double r = 0.0;
-      for (int j = 0; j < 4; j++) r = r + D[g][j] * ee[loc(j, a)];
+      for (int j = 0; j < 4; j++) r = fma(D[g][j], ee[loc(j, a)], r);
       rs[g][a] = r;
     }
     double n = sqrt(rs[g][0] * rs[g][0] + rs[g][1] * rs[g][1]);
@@ -157,9 +160,9 @@ static void element_internal(const orc_plate *p, const double *ee, double Qi[8],
   for (int i = 0; i < 4; i++)
     for (int a = 0; a < 2; a++) {
       double bend = 0.0;
-      for (int j = 0; j < 4; j++) bend = bend + Kb[i][j] * ee[loc(j, a)];
+      for (int j = 0; j < 4; j++) bend = fma(Kb[i][j], ee[loc(j, a)], bend);
       double axial = 0.0;
-      for (int g = 0; g < 5; g++) axial = axial + wl[g] * c1[g] * rs[g][a] * D[g][i];
+      for (int g = 0; g < 5; g++) axial = fma(wl[g] * c1[g] * rs[g][a], D[g][i], axial);
       Qi[loc(i, a)] = bend + axial;
     }
   if (!Kt) return;
@@ -171,7 +174,7 @@ static void element_internal(const orc_plate *p, const double *ee, double Qi[8],
           for (int g = 0; g < 5; g++) {
             double s = c2[g] * rs[g][a] * rs[g][b];
             if (a == b) s = c1[g] + s;
-            k = k + wl[g] * D[g][i] * D[g][j] * s;
+            k = fma(wl[g] * D[g][i] * D[g][j], s, k);
           }
           Kt[loc(i, a)][loc(j, b)] = a == b ? Kb[i][j] + k : k;
         }
@@ -291,7 +294,7 @@ static int band_ldlt_factor(double (*A)[BW + 1], double *rinv, int n) {
     for (int k = 1; k <= BW && i + k < n; k++) lk[k] = A[i][k] * r;
     for (int k = 1; k <= BW && i + k < n; k++)
       for (int m = k; m <= BW && i + m < n; m++)
-        A[i + k][m - k] = A[i + k][m - k] - lk[k] * A[i][m];
+        A[i + k][m - k] = fma(-lk[k], A[i][m], A[i + k][m - k]);
     for (int k = 1; k <= BW && i + k < n; k++) A[i][k] = lk[k];
   }
   return 0;
@@ -302,7 +305,7 @@ static int band_ldlt_factor(double (*A)[BW + 1], double *rinv, int n) {
  * missing product (past the last row) counting as zero. */
 static void band_ldlt_solve(double (*A)[BW + 1], const double *rinv, double *b, int n) {
   for (int i = 0; i < n; i++)
-    for (int k = 1; k <= BW && i + k < n; k++) b[i + k] = b[i + k] - A[i][k] * b[i];
+    for (int k = 1; k <= BW && i + k < n; k++) b[i + k] = fma(-A[i][k], b[i], b[i + k]);
   for (int i = 0; i < n; i++) b[i] = b[i] * rinv[i];
   for (int i = n - 1; i >= 0; i--) {
     double pr[BW + 2];
@@ -371,7 +374,7 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
           int r = loc(i, a);
           if (dynamic) {
             double inert = 0.0;
-            for (int j = 0; j < 4; j++) inert = inert + Ms[i][j] * g[4 * el + loc(j, a)];
+            for (int j = 0; j < 4; j++) inert = fma(Ms[i][j], g[4 * el + loc(j, a)], inert);
             Rel[el][r] = inert + c_load * Qi[r];
           } else {
             Rel[el][r] = Qi[r];

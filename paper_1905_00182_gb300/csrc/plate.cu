@@ -3,8 +3,12 @@
 // fluid grid through the penalty forces (Eq. 7-9).
 //
 // Compiled with --fmad=false and host -ffp-contract=off: every FP64 operation is rounded on its
-// own, in the order written, so a sequential evaluation of the same formulas reproduces the
-// results bit for bit.  The structure solve is tiny (4 (n_el + 1) unknowns, half-bandwidth 7) and
+// own, in the order written, except the explicit fused multiply-adds (__fma_rn) of the dot
+// products, the elimination and the forward substitution -- so a sequential evaluation of the
+// same formulas with the same fused operations reproduces the results bit for bit.  On GB300
+// a warp's FP64 instruction occupies its SM quarter's FP64 pipe for tens of cycles however
+// few lanes are active, so the serial parts are written to issue as few FP64 instructions as
+// possible (fused operations, one reciprocal per pivot, products of a row in parallel lanes).  The structure solve is tiny (4 (n_el + 1) unknowns, half-bandwidth 7) and
 // sequential by nature (Newton, banded factorisation), so it runs in ONE thread block: element
 // residuals and Jacobians one thread per (element, row), assembly one thread per coordinate, the
 // LDL^T factorisation one warp (the 28 updates of a pivot in parallel), all state in shared
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(512) k_step(Params P, StepArgs A) {
       double rs[2];
       for (int b = 0; b < 2; b++) {
         double t = 0.0;
-        for (int j = 0; j < 4; j++) t = t + D[j] * ee[lc(j, b)];
+        for (int j = 0; j < 4; j++) t = __fma_rn(D[j], ee[lc(j, b)], t);
         rs[b] = t;
       }
       double n = sqrt(rs[0] * rs[0] + rs[1] * rs[1]);
@@ -324,17 +328,17 @@ __global__ void __launch_bounds__(512) k_step(Params P, StepArgs A) {
       int i = 2 * (r / 4) + (r % 4) / 2, a = r % 2;
       const double *ee = S.em + 4 * el;
       double bend = 0.0;
-      for (int j = 0; j < 4; j++) bend = bend + S.Kb[i * 4 + j] * ee[lc(j, a)];
+      for (int j = 0; j < 4; j++) bend = __fma_rn(S.Kb[i * 4 + j], ee[lc(j, a)], bend);
       double axial = 0.0;
-      for (int gp = 0; gp < 5; gp++) axial = axial + S.gt[el][gp][a] * S.D[gp * 4 + i];
+      for (int gp = 0; gp < 5; gp++) axial = __fma_rn(S.gt[el][gp][a], S.D[gp * 4 + i], axial);
       double Qi = bend + axial;
       double inert = 0.0;
-      for (int j = 0; j < 4; j++) inert = inert + S.Ms[i * 4 + j] * S.g[4 * el + lc(j, a)];
+      for (int j = 0; j < 4; j++) inert = __fma_rn(S.Ms[i * 4 + j], S.g[4 * el + lc(j, a)], inert);
       S.Rel[el][r] = inert + c_load * Qi;
       for (int c = r; c < 8; c++) {
         int j = 2 * (c / 4) + (c % 4) / 2, b = c % 2;
         double k = 0.0;
-        for (int gp = 0; gp < 5; gp++) k = k + S.PD[(gp * 4 + i) * 4 + j] * S.gs[el][gp][a * 2 + b];
+        for (int gp = 0; gp < 5; gp++) k = __fma_rn(S.PD[(gp * 4 + i) * 4 + j], S.gs[el][gp][a * 2 + b], k);
         double J;
         if (a == b)
           J = S.Ms[i * 4 + j] + c_stiff * (S.Kb[i * 4 + j] + k);
@@ -403,12 +407,13 @@ __global__ void __launch_bounds__(512) k_step(Params P, StepArgs A) {
         bad = !(dpiv != 0.0) || !isfinite(dpiv);
         if (bad) break;  // uniform: every lane read the same pivot
         double r = 1.0 / dpiv;
+        double lk = 0.0;
         if (lane < 28 && i + pm < nf) {
-          double lk = S.A[i][pk] * r;
-          S.A[i + pk][pm - pk] = S.A[i + pk][pm - pk] - lk * S.A[i][pm];
+          lk = S.A[i][pk] * r;
+          S.A[i + pk][pm - pk] = __fma_rn(-lk, S.A[i][pm], S.A[i + pk][pm - pk]);
         }
         __syncwarp();
-        if (lane >= 1 && lane <= BW && i + lane < nf) S.A[i][lane] = S.A[i][lane] * r;
+        if (lane < 28 && pm == pk && i + pk < nf) S.A[i][pk] = lk;  // L(i + k, i)
         if (lane == 0) S.rinv[i] = r;
         __syncwarp();
       }
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(512) k_step(Params P, StepArgs A) {
         double w = lane <= BW && lane < nf ? S.x[lane] : 0.0;
         for (int i = 0; i < nf; i++) {
           double bi = __shfl_sync(FULL, w, 0);
-          if (lane >= 1 && lane <= BW && i + lane < nf) w = w - S.A[i][lane] * bi;
+          if (lane >= 1 && lane <= BW && i + lane < nf) w = __fma_rn(-S.A[i][lane], bi, w);
           if (lane == 0) S.x[i] = bi;
           double nx = __shfl_down_sync(FULL, w, 1);
           w = lane < BW ? nx : (i + 1 + BW < nf ? S.x[i + 1 + BW] : 0.0);

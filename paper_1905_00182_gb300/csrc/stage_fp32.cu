@@ -800,28 +800,65 @@ __global__ void k_ib_interp64(Plan p, const double *__restrict__ Qn, const float
   }
 }
 
+// Spreading (Eq. 9) into the FP32 right-hand side: one group of S = 4^DIM threads per marker,
+// one thread per support cell.  The marker's 4 DIM kernel weights (FP64, Eq. 11) are evaluated
+// once, by the first 4 DIM threads of its group, and shared; the per-cell force, the fluid
+// velocity of the power term f.u and the atomic additions are FP32, the precision of the
+// right-hand side they enter.
 template <int DIM>
-__global__ void k_spread32(Plan p, const double *__restrict__ Qn, const float *__restrict__ din) {
-  constexpr int S = DIM > 2 ? 64 : 16;
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)p.nm * S) return;
-  int k = (int)(t / S), r = (int)(t % S);
+__global__ void __launch_bounds__(128) k_spread32(Plan p, const double *__restrict__ Qn,
+                                                  const float *__restrict__ din) {
+  constexpr int S = DIM > 2 ? 64 : 16, MPB = 128 / S;
+  __shared__ double sw[MPB][3][4];
+  __shared__ int sj[MPB][3];
+  __shared__ float sf[MPB][3];
+  __shared__ int sok[MPB];
+  const int lm = threadIdx.x / S, r = threadIdx.x % S;
+  const int k = blockIdx.x * MPB + lm;
+  const int M = p.max_markers;
+  const bool live = k < p.nm;
+  if (live && r < 4 * DIM) {
+    int a = r / 4, q = r % 4;
+    double s = (p.X[a * M + k] - p.lo[a]) * p.inv_h[a] - 0.5;
+    int j0 = (int)floor(s) - 1;
+    sw[lm][a][q] = peskin(s - (double)(j0 + q));
+    if (q == 0) sj[lm][a] = j0;
+  }
+  if (live && r == 0) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      double s = (p.X[a * M + k] - p.lo[a]) * p.inv_h[a] - 0.5;
+      int j0 = (int)floor(s) - 1;
+      if (j0 < 0 || j0 + 3 > p.n[a] - 1) ok = false;
+    }
+    sok[lm] = ok;
+    double sc = p.dS[k] / p.hprod;
+#pragma unroll
+    for (int a = 0; a < 3; a++) sf[lm][a] = a < DIM ? (float)(-p.F[a * M + k] * sc) : 0.f;
+    if (DIM < 3) {
+      sw[lm][2][0] = 1.0;
+      sw[lm][2][1] = sw[lm][2][2] = sw[lm][2][3] = 0.0;
+      sj[lm][2] = 0;
+    }
+  }
+  __syncthreads();
+  if (!live || !sok[lm]) return;  // the interpolation kernel reports markers off the grid
   int r0 = r & 3, r1 = (r >> 2) & 3, r2 = DIM > 2 ? (r >> 4) : 0;
-  int M = p.max_markers;
-  int j0[3];
-  double w[3][4];
-  if (!point_support<DIM>(p, p.X, M, k, j0, w)) return;
-  double scale = w[0][r0] * w[1][r1] * w[2][r2] * p.dS[k] / p.hprod;
-  long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
-  double inv_rho = 1.0 / stage_q(p, Qn, din, 0, o);
-  double pw = 0.0;
+  float wt = (float)(sw[lm][0][r0] * sw[lm][1][r1] * sw[lm][2][r2]);
+  long long o = int_index(p, sj[lm][0] + r0, sj[lm][1] + r1, sj[lm][2] + r2);
+  Free fs = free_stream(p);
+  float d0 = p.qn32[o] + (din ? din[o] : 0.f);
+  float inv_rho = 1.f / (fs.rho + d0);
+  float pw = 0.f;
 #pragma unroll
   for (int a = 0; a < DIM; a++) {
-    double fa = -p.F[a * M + k] * scale;
-    atomicAdd(&p.L32[(1 + a) * p.N + o], (float)fa);
-    pw += fa * stage_q(p, Qn, din, 1 + a, o) * inv_rho;
+    float da = p.qn32[(1 + a) * p.N + o] + (din ? din[(1 + a) * p.N + o] : 0.f);
+    float fa = sf[lm][a] * wt;
+    atomicAdd(&p.L32[(1 + a) * p.N + o], fa);
+    pw += fa * ((fs.m[a] + da) * inv_rho);
   }
-  atomicAdd(&p.L32[(DIM + 1) * p.N + o], (float)pw);
+  atomicAdd(&p.L32[(DIM + 1) * p.N + o], pw);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -917,12 +954,13 @@ __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__res
 #endif
 namespace vm {
 constexpr int TX = 32, TY = 8, ZC = 64;        // block columns, z-chunk
+constexpr int VT = TX * TY;                    // threads (one column each)
 constexpr int SX = TX + 8, SY = TY + 8;        // staged plane (halo 4)
 constexpr int PX = TX + 4, PY = TY + 4;        // flux points (halo 2)
 constexpr size_t SMEM = sizeof(float) * (5 * 3 * SX * SY + 4 * PX * TY + 4 * TX * PY);
 }  // namespace vm
 
-__global__ void __launch_bounds__(THREADS, VM_MIN_BLOCKS) k_visc_march32(Plan p, const float *__restrict__ din,
+__global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, const float *__restrict__ din,
                                                           float *__restrict__ dout, double *Qn,
                                                           double *__restrict__ Lout, float Bc,
                                                           float dt, int mode) {
@@ -942,12 +980,12 @@ __global__ void __launch_bounds__(THREADS, VM_MIN_BLOCKS) k_visc_march32(Plan p,
 
   // plane z (ghost range -4 .. n+3) is read into registers one iteration before it enters
   // ring slot z mod 5, so its global-memory latency hides behind the gradients of a plane
-  constexpr int PER = (SX * SY + THREADS - 1) / THREADS;
+  constexpr int PER = (SX * SY + VT - 1) / VT;
   float R[PER][3];
   auto fetch = [&](int z) {
 #pragma unroll
     for (int j = 0; j < PER; j++) {
-      int e = threadIdx.x + j * THREADS;
+      int e = threadIdx.x + j * VT;
       if (e < SX * SY) {
         int sx = e % SX, sy = e / SX;
         int gx = min(x0 - 4 + sx, p.n[0] + 3), gy = min(y0 - 4 + sy, p.n[1] + 3);
@@ -961,7 +999,7 @@ __global__ void __launch_bounds__(THREADS, VM_MIN_BLOCKS) k_visc_march32(Plan p,
     float *dst = ring + ((z + 8) % 5) * PLANE;
 #pragma unroll
     for (int j = 0; j < PER; j++) {
-      int e = threadIdx.x + j * THREADS;
+      int e = threadIdx.x + j * VT;
       if (e < SX * SY) {
 #pragma unroll
         for (int c = 0; c < 3; c++) dst[c * SX * SY + e] = R[j][c];
@@ -1046,7 +1084,7 @@ __global__ void __launch_bounds__(THREADS, VM_MIN_BLOCKS) k_visc_march32(Plan p,
         acc[4][k] += ih[2] * f[k];
       }
     }
-    for (int e = threadIdx.x; e < 4 * TY + 4 * TX; e += THREADS) {
+    for (int e = threadIdx.x; e < 4 * TY + 4 * TX; e += VT) {
       float g[3][3], u[3], f[4];
       if (e < 4 * TY) {  // x-halo point
         int r = e / 4, h = e % 4, px = h < 2 ? h : TX + h;  // 0,1,TX+2,TX+3
@@ -1276,9 +1314,9 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (p.nm > 0) {
-    constexpr int S = DIM > 2 ? 64 : 16;
+    constexpr int MPB = DIM > 2 ? 2 : 8;  // markers per 128-thread block
     prof_begin(pr, st);
-    k_spread32<DIM><<<blocks_for((long long)p.nm * S, THREADS), THREADS, 0, st>>>(p, Qn, din);
+    k_spread32<DIM><<<blocks_for(p.nm, MPB), 128, 0, st>>>(p, Qn, din);
     prof_end(pr, K_SPREAD, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -1290,7 +1328,7 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
                              (int)SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((p.n[0] + TX - 1) / TX, (p.n[1] + TY - 1) / TY, (p.n[2] + ZC - 1) / ZC);
-    k_visc_march32<<<grid, THREADS, SMEM, st>>>(p, din, dout, const_cast<double *>(Qn), s.Lout,
+    k_visc_march32<<<grid, VT, SMEM, st>>>(p, din, dout, const_cast<double *>(Qn), s.Lout,
                                                (float)s.b, (float)s.dt, mode);
   } else if (p.Re > 0.0)
     k_finish32<DIM, true><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(

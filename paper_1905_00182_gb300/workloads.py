@@ -91,7 +91,7 @@ class PlateSpec:
     alpha_m: float = 0.0
     phi: float = 0.0
     newton_max: int = 30
-    newton_tol: float = 1e-12
+    newton_tol: float = 1e-10   # on the last increment; Newton's error after it is ~ its square
 
     @property
     def ndof(self) -> int:
@@ -296,12 +296,13 @@ def cylinder_pulse_2d(n: int = 256, markers: int = 160, Re: float = 1e4, scheme:
 
 def rotating_cylinder_2d(n: int = 2048, markers: int = 1024, scheme: int = WENO5JS,
                          precision: int = FP64):
-    """Rotating cylinder in a uniform stream (Sec. 3.3): Mach 0.2, Re 150, [-40,40]^2, 20-cell
-    sponge, surface speed 0.5 U, 360 probes on a ring r = 30."""
+    """Rotating cylinder in a uniform stream (Sec. 3.3): Mach 0.2, Re = rho U D / mu = 150,
+    [-40,40]^2, 20-cell sponge, surface speed 0.5 U, 360 probes on a ring r = 30.  Units:
+    rho = 1, c = 1, D = 1, so the solver's Reynolds number (rho c D / mu) is 150 / 0.2."""
     g = 1.4
     U0 = 0.2
     spec = GridSpec(dim=2, n=(n, n, 1), lo=(-40.0, -40.0, 0.0), hi=(40.0, 40.0, 1.0), gamma=g,
-                    Re=150.0, qinf=freestream(2, g, vel=(U0, 0.0, 0.0)), scheme=scheme,
+                    Re=150.0 / U0, qinf=freestream(2, g, vel=(U0, 0.0, 0.0)), scheme=scheme,
                     precision=precision, bc=((1, 1), (1, 1), (0, 0)), sponge_cells=20,
                     max_markers=markers)
     h = spec.h[0]
