@@ -375,13 +375,17 @@ def fsi_form(ib, barrier, max_ranks, world, warmup=3, steps=10, steps64=2):
         ms = max_ranks(e0.elapsed_time(e1)) / k
         prof = ib.ibfsa_profile_read(g.h)
         flags, iters = pl.status()
+        force, power = pl.force()
+        Ur = w["U_ref"]  # Eq. 19: 2 F / (rho U^2 L), -2 P / (rho U^3 L), rho = L = 1
+        coeff = {"C_T": -2.0 * force[0] / Ur ** 2, "C_L": 2.0 * force[1] / Ur ** 2,
+                 "C_p": -2.0 * power / Ur ** 3, "t": pl.get_state()[2]}
         key = "fp32" if prec == W.FP32_PERTURB else "fp64"
         out[key] = {"value": spec.cells * 3 * world / (ms * 1e-3), "unit": "cell-updates/s",
                     "ms_per_step": ms,
                     "plate_ms_per_step": prof["plate"]["ms"] / k,
                     "kernel_ms_per_step": {c: v["ms"] / k for c, v in prof.items() if v["timed"]},
                     "newton_max_iterations": iters, "plate_status": flags,
-                    "grid_status": g.status()}
+                    "grid_status": g.status(), "coefficients_last_step": coeff}
         g.close()
         pl.close()
         del g, pl

@@ -278,6 +278,14 @@ int ibfsa_plate_markers(ibfsa_plate *p, double *X, double *U, double *dS);
  * call (either pointer may be NULL); clears both; synchronises. */
 int ibfsa_plate_get_status(ibfsa_plate *p, int *host_flags, int *host_max_iters);
 
+/* Force of the fluid on the plate and the power it delivers, over the last step (ibfsa_plate_step
+ * or ibfsa_fsi_step): host_force[a] = sum_k F_k,a dS_k and *host_power = sum_k (F_k . U_k) dS_k
+ * (may be NULL), with F the step's load and U the marker velocities held during the step, FP64
+ * summed in marker order; synchronises.  The thrust, lift and power coefficients of Sec. 4.1
+ * (Eq. 19) are -host_force[0], host_force[1] and -*host_power times 2 / (rho U^2 L) (power:
+ * 2 / (rho U^3 L)) for a stream along +x. */
+int ibfsa_plate_force(ibfsa_plate *p, double *host_force, double *host_power);
+
 /* nsteps coupled steps of plate and fluid (2D grid with max_markers >= n_markers; the grid's
  * stream must be the plate's): the grid's markers take the plate's positions, velocities and
  * weights at the step start and keep them for the three SSP-RK3 stages (ibfsa_rk3_step); the

@@ -267,6 +267,8 @@ def _plate_lib():
         L.orc_plate_static.argtypes = [P, _D, _D, _I]
         L.orc_fsi_step.argtypes = [ctypes.POINTER(OrcDesc), P, _D, _D, _D, _D, _D,
                                    ctypes.c_double, ctypes.c_int, _I]
+        L.orc_plate_force.argtypes = [P, _D, _D, _D, _D]
+        L.orc_fsi_last_load.argtypes = [_D, ctypes.c_int]
         _plate_ready = True
     return L
 
@@ -379,3 +381,25 @@ def fsi_step(spec, ps, Q, xi, e, v, t, dt, nsteps=1):
     if rc != ORC_OK:
         raise RuntimeError(f"oracle fsi step failed: {rc}")
     return Q, xi, e, v, tt.value, list(iters)[:nsteps]
+
+
+def plate_force(ps, F, U):
+    """(force [2], power) of the load F on markers moving with U (Eq. 19 numerators)."""
+    F, U = _f64(F), _f64(U)
+    force = np.zeros(2)
+    pw = ctypes.c_double(0.0)
+    d = plate_desc(ps)
+    rc = _plate_lib().orc_plate_force(ctypes.byref(d), _p(F), _p(U), _p(force),
+                                      ctypes.cast(ctypes.pointer(pw), _D))
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle plate force failed: {rc}")
+    return force, pw.value
+
+
+def fsi_last_load(ps):
+    """The stage-weighted load of the last coupled step, [2][n_markers]."""
+    F = np.zeros((2, ps.n_markers))
+    rc = _plate_lib().orc_fsi_last_load(_p(F), 2 * ps.n_markers)
+    if rc != ORC_OK:
+        raise RuntimeError("no coupled step ran")
+    return F

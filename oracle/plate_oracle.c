@@ -490,6 +490,39 @@ int orc_plate_static(const orc_plate *p, double *e, const double *Qf, int *iters
   return newton(p, e, NULL, Qf, 0.0, ep, vp, iters);
 }
 
+/* Force of the fluid on the plate and the power it delivers over a step (Sec. 4.1, Eq. 19):
+ * force[a] = sum_k F_k,a dS_k and *power = sum_k (F_k . U_k) dS_k, in marker order, from the
+ * step's load F [2][n_markers] and the marker velocities U [2][n_markers] held during the step.
+ * The thrust, lift and power coefficients of Eq. 19 are -force[0], force[1] and -power scaled
+ * by 2 / (rho U^2 L) (power: 2 / (rho U^3 L)). */
+int orc_plate_force(const orc_plate *p, const double *F, const double *U, double force[2],
+                    double *power) {
+  int rc = check_plate(p);
+  if (rc) return rc;
+  int nm = p->n_markers;
+  double dS = p->length / (double)nm;
+  double fx = 0.0, fy = 0.0, pw = 0.0;
+  for (int k = 0; k < nm; k++) {
+    fx = fx + F[k] * dS;
+    fy = fy + F[nm + k] * dS;
+    pw = pw + (F[k] * U[k] + F[nm + k] * U[nm + k]) * dS;
+  }
+  force[0] = fx;
+  force[1] = fy;
+  *power = pw;
+  return ORC_OK;
+}
+
+/* The load Fbar the coupled step hands the plate (last step), for the force pin. */
+static double *g_last_fbar = NULL;
+static int g_last_fbar_n = 0;
+
+int orc_fsi_last_load(double *F, int n) {
+  if (!g_last_fbar || n != g_last_fbar_n) return ORC_ERR_ARG;
+  memcpy(F, g_last_fbar, sizeof(double) * n);
+  return ORC_OK;
+}
+
 /* nsteps coupled steps of plate and fluid (2D):
  *   markers <- plate (positions, velocities, weights) at the step start;
  *   three SSP-RK3 stages of the fluid and of xi with those markers (as orc_rk3), collecting
@@ -533,6 +566,10 @@ int orc_fsi_step(const orc_desc *d, const orc_plate *p, double *Q, double *xi, d
     memcpy(Q, Qs, sizeof(double) * M);
     memcpy(xi, xs, sizeof(double) * 2 * nm);
     orc_plate_load(p, Fbar, Qf);
+    free(g_last_fbar);
+    g_last_fbar = malloc(sizeof(double) * 2 * nm);
+    g_last_fbar_n = 2 * nm;
+    if (g_last_fbar) memcpy(g_last_fbar, Fbar, sizeof(double) * 2 * nm);
     double t_new = *t + dt;
     int it = 0;
     rc = orc_plate_step(p, e, v, t_new, dt, Qf, &it);

@@ -141,7 +141,7 @@ __global__ void k_tables(Params P, int *mk_el, double *mk_S, int *el_first) {
 // ---- markers from the plate: X, U [2][stride], dS ------------------------------------------
 __global__ void k_markers(Params P, const double *__restrict__ e, const double *__restrict__ v,
                           const int *__restrict__ mk_el, const double *__restrict__ mk_S,
-                          double *X, double *U, double *dS, int stride) {
+                          double *X, double *U, double *dS, int stride, double *U2) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P.nm) return;
   int el = mk_el[k];
@@ -155,8 +155,26 @@ __global__ void k_markers(Params P, const double *__restrict__ e, const double *
     }
     X[a * stride + k] = x;
     U[a * stride + k] = u;
+    if (U2) U2[a * P.nm + k] = u;  // the plate's own copy of the step's marker velocities
   }
   dS[k] = P.L / (double)P.nm;
+}
+
+// ---- force and power of the step's load (Eq. 19 numerators), summed in marker order ------
+__global__ void k_force(Params P, const double *__restrict__ F, const double *__restrict__ U,
+                        double *res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int nm = P.nm;
+  double dS = P.L / (double)nm;
+  double fx = 0.0, fy = 0.0, pw = 0.0;
+  for (int k = 0; k < nm; k++) {
+    fx = fx + F[k] * dS;
+    fy = fy + F[nm + k] * dS;
+    pw = pw + (F[k] * U[k] + F[nm + k] * U[nm + k]) * dS;
+  }
+  res[0] = fx;
+  res[1] = fy;
+  res[2] = pw;
 }
 
 // ---- stage force average: Fbar = w F (first stage) or Fbar + w F ---------------------------
@@ -506,6 +524,8 @@ struct Plate {
   double t;
   double *e, *v, *Fbar, *X, *U, *dS;  // workspace
   double *mk_S;                       // marker shape values [nm][4]
+  double *res;                        // force [2] and power of the last step
+  double *Ustep;                      // marker velocities held during the last step [2][nm]
   int *mk_el, *el_first;              // marker elements [nm], first marker per element
   int *status;                        // [0] flags, [1] max Newton iterations
   int threads;
@@ -515,7 +535,7 @@ struct Plate {
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct PlateLayout {
-  size_t e, v, Fbar, X, U, dS, mk_S, mk_el, el_first, status, total;
+  size_t e, v, Fbar, X, U, dS, mk_S, mk_el, el_first, res, Ustep, status, total;
 };
 
 static PlateLayout plate_layout(const ibfsa_plate_desc &d) {
@@ -531,6 +551,8 @@ static PlateLayout plate_layout(const ibfsa_plate_desc &d) {
   L.mk_S = o; o = al256(o + 4 * nm * 8);
   L.mk_el = o; o = al256(o + nm * sizeof(int));
   L.el_first = o; o = al256(o + (size_t)(d.n_el + 1) * sizeof(int));
+  L.res = o; o = al256(o + 3 * sizeof(double));
+  L.Ustep = o; o = al256(o + 2 * nm * 8);
   L.status = o; o = al256(o + 2 * sizeof(int));
   L.total = o;
   return L;
@@ -648,6 +670,8 @@ int ibfsa_plate_create(const ibfsa_plate_desc *desc, void *d_workspace, size_t w
   P.mk_S = (double *)(ws + L.mk_S);
   P.mk_el = (int *)(ws + L.mk_el);
   P.el_first = (int *)(ws + L.el_first);
+  P.res = (double *)(ws + L.res);
+  P.Ustep = (double *)(ws + L.Ustep);
   P.status = (int *)(ws + L.status);
   P.P.n_el = desc->n_el;
   P.P.nd = 4 * (desc->n_el + 1);
@@ -724,6 +748,11 @@ int ibfsa_plate_step(ibfsa_plate *p, double dt, const double *F) {
   size_t n = sizeof(double) * 2 * P.P.nm;
   cudaError_t err = F ? cudaMemcpyAsync(P.Fbar, F, n, cudaMemcpyDefault, P.stream)
                       : cudaMemsetAsync(P.Fbar, 0, n, P.stream);
+  if (err == cudaSuccess) {  // the markers' velocities during the step (for ibfsa_plate_force)
+    plate::k_markers<<<(P.P.nm + 127) / 128, 128, 0, P.stream>>>(P.P, P.e, P.v, P.mk_el, P.mk_S,
+                                                                 P.X, P.U, P.dS, P.P.nm, P.Ustep);
+    err = cudaGetLastError();
+  }
   if (err == cudaSuccess) err = launch_step(P, dt, P.Fbar, nullptr);
   return err == cudaSuccess ? IBFSA_OK : cuda_err(err, "ibfsa_plate_step");
 }
@@ -733,7 +762,7 @@ int ibfsa_plate_markers(ibfsa_plate *p, double *X, double *U, double *dS) {
   Plate &P = p->p;
   int nm = P.P.nm;
   plate::k_markers<<<(nm + 127) / 128, 128, 0, P.stream>>>(P.P, P.e, P.v, P.mk_el, P.mk_S, P.X,
-                                                           P.U, P.dS, nm);
+                                                           P.U, P.dS, nm, nullptr);
   cudaError_t err = cudaGetLastError();
   size_t n2 = sizeof(double) * 2 * nm;
   if (err == cudaSuccess) err = cudaMemcpyAsync(X, P.X, n2, cudaMemcpyDefault, P.stream);
@@ -758,6 +787,21 @@ int ibfsa_plate_get_status(ibfsa_plate *p, int *host_flags, int *host_max_iters)
   return IBFSA_OK;
 }
 
+int ibfsa_plate_force(ibfsa_plate *p, double *host_force, double *host_power) {
+  if (!p || !host_force) return api_fail(IBFSA_ERR_ARG, "NULL argument");
+  Plate &P = p->p;
+  plate::k_force<<<1, 32, 0, P.stream>>>(P.P, P.Fbar, P.Ustep, P.res);
+  double h[3] = {0.0, 0.0, 0.0};
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaMemcpyAsync(h, P.res, sizeof(h), cudaMemcpyDeviceToHost, P.stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(P.stream);
+  if (err != cudaSuccess) return cuda_err(err, "ibfsa_plate_force");
+  host_force[0] = h[0];
+  host_force[1] = h[1];
+  if (host_power) *host_power = h[2];
+  return IBFSA_OK;
+}
+
 int ibfsa_fsi_step(ibfsa_grid *g, ibfsa_plate *p, double dt, int nsteps) {
   if (!g || !p) return api_fail(IBFSA_ERR_ARG, "NULL grid or plate");
   if (nsteps < 0 || !(dt > 0.0)) return api_fail(IBFSA_ERR_ARG, "need dt > 0 and nsteps >= 0");
@@ -776,7 +820,7 @@ int ibfsa_fsi_step(ibfsa_grid *g, ibfsa_plate *p, double dt, int nsteps) {
   for (int step = 0; step < nsteps; step++) {
     prof_begin(&G.prof, G.stream);
     plate::k_markers<<<(nm + 127) / 128, 128, 0, G.stream>>>(P.P, P.e, P.v, P.mk_el, P.mk_S,
-                                                             G.X, G.U, G.dS, M);
+                                                             G.X, G.U, G.dS, M, P.Ustep);
     prof_end(&G.prof, K_PLATE, G.stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(e, "ibfsa_fsi_step markers");

@@ -43,7 +43,7 @@ EXPORTS = (
     "ibfsa_mlp_eval", "ibfsa_set_mlp", "ibfsa_mlp_stats", "ibfsa_mlp_sample",
     "ibfsa_body_force", "ibfsa_plate_workspace_bytes", "ibfsa_plate_create",
     "ibfsa_plate_destroy", "ibfsa_plate_set_state", "ibfsa_plate_get_state", "ibfsa_plate_step",
-    "ibfsa_plate_markers", "ibfsa_plate_get_status", "ibfsa_fsi_step",
+    "ibfsa_plate_markers", "ibfsa_plate_get_status", "ibfsa_fsi_step", "ibfsa_plate_force",
 )
 MLP_NPARAM = 2403
 
@@ -152,6 +152,7 @@ def lib():
         L.ibfsa_plate_get_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]
         L.ibfsa_fsi_step.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int]
+        L.ibfsa_plate_force.argtypes = [_P, _P, _P]
         _lib = L
     return _lib
 
@@ -440,6 +441,13 @@ def ibfsa_plate_get_status(p):
     return f.value, it.value
 
 
+def ibfsa_plate_force(p):
+    f = (ctypes.c_double * 2)()
+    pw = ctypes.c_double(0.0)
+    _check(lib().ibfsa_plate_force(p, ctypes.cast(f, _P), ctypes.cast(ctypes.pointer(pw), _P)))
+    return np.array([f[0], f[1]]), pw.value
+
+
 def ibfsa_fsi_step(g, p, dt: float, nsteps: int = 1):
     _check(lib().ibfsa_fsi_step(g, p, float(dt), int(nsteps)))
 
@@ -605,6 +613,10 @@ class Plate:
     def status(self):
         """(status bits, largest Newton iteration count) since the last call."""
         return ibfsa_plate_get_status(self.h)
+
+    def force(self):
+        """(force [2], power) of the last step's load (Eq. 19 numerators)."""
+        return ibfsa_plate_force(self.h)
 
 
 def fsi_step(grid: Grid, plate: Plate, dt: float, nsteps: int = 1):

@@ -75,9 +75,10 @@ def test_descriptor_validation(ib, field, value, code):
 def test_plate_workspace_counts_buffers(ib):
     ps = W.PlateSpec(n_el=40, n_markers=800)
     nbytes = ib.ibfsa_plate_workspace_bytes(ib.plate_desc_from_spec(ps))
-    # e, v, Fbar, X, U, dS, marker shape values; marker elements and first marker per element
-    expect = 8 * (2 * 164 + 3 * 2 * 800 + 800 + 4 * 800) + 4 * (800 + 41)
-    assert expect <= nbytes <= expect + 11 * 256
+    # e, v, Fbar, X, U, dS, marker shape values, force result, step velocities; marker elements
+    # and first marker per element
+    expect = 8 * (2 * 164 + 4 * 2 * 800 + 800 + 4 * 800 + 3) + 4 * (800 + 41)
+    assert expect <= nbytes <= expect + 13 * 256
 
 
 @pytest.mark.parametrize("field,value", [

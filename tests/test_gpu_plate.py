@@ -56,6 +56,7 @@ def test_plate_steps_match_oracle_bit_for_bit(kind):
     for n in range(12):
         F = _forces(ps, 100 + n, scale)
         P.step(dt, F)
+        eb, vb = eo.copy(), vo.copy()
         t_new = t + dt
         eo, vo, _ = O.plate_step(ps, eo, vo, t_new, dt, Qf=O.plate_load(ps, F))
         t = t_new
@@ -69,6 +70,11 @@ def test_plate_steps_match_oracle_bit_for_bit(kind):
     Xo, Uo, dSo = O.plate_markers(ps, eo, vo)
     assert np.array_equal(X.cpu().numpy(), Xo) and np.array_equal(U.cpu().numpy(), Uo)
     assert np.array_equal(dS.cpu().numpy(), dSo)
+    # force and power of the last step: its load and the markers' velocities before it
+    fg, pg = P.force()
+    _, Ub, _ = O.plate_markers(ps, eb, vb)
+    fo, po = O.plate_force(ps, F, Ub)
+    assert np.array_equal(fg, fo) and pg == po
     P.close()
 
 
@@ -129,7 +135,7 @@ def _coupled_case(n=(96, 64), scheme=W.TENO5, precision=W.FP64):
     return spec, ps, Q, e, v, dt
 
 
-def _coupled_gpu(spec, ps, Q, e, v, dt, steps, strict):
+def _coupled_gpu(spec, ps, Q, e, v, dt, steps, strict, force=None):
     ib = _ib()
     G = ib.Grid(spec, strict=strict)
     G.set_state(Q)
@@ -140,6 +146,8 @@ def _coupled_gpu(spec, ps, Q, e, v, dt, steps, strict):
     ib.fsi_step(G, P, dt, steps)
     out = (G.get_state().cpu().numpy(), G.penalty_integral().cpu().numpy(),
            *[t.cpu().numpy() if hasattr(t, "cpu") else t for t in P.get_state()])
+    if force is not None:
+        force.append(P.force())
     flags = (G.status(), P.status())
     G.close()
     P.close()
@@ -149,11 +157,16 @@ def _coupled_gpu(spec, ps, Q, e, v, dt, steps, strict):
 def test_coupled_step_matches_oracle_bit_for_bit():
     spec, ps, Q, e, v, dt = _coupled_case()
     steps = 3
+    fl = []
     (Qg, xig, eg, vg, tg), (gs, (ps_flags, iters)) = _coupled_gpu(spec, ps, Q, e, v, dt, steps,
-                                                                  strict=True)
+                                                                  strict=True, force=fl)
     xi0 = np.zeros((2, ps.n_markers))
-    Qo, xio, eo, vo, to, it_o = O.fsi_step(spec, ps, Q, xi0, e, v, 0.0, dt, nsteps=steps)
-    assert gs == 0 and ps_flags == 0 and iters == max(it_o)
+    Q2, xi2, e2, v2, t2, _ = O.fsi_step(spec, ps, Q, xi0, e, v, 0.0, dt, nsteps=steps - 1)
+    Qo, xio, eo, vo, to, it_o = O.fsi_step(spec, ps, Q2, xi2, e2, v2, t2, dt, nsteps=1)
+    _, Ul, _ = O.plate_markers(ps, e2, v2)
+    fo, po = O.plate_force(ps, O.fsi_last_load(ps), Ul)
+    assert np.array_equal(fl[0][0], fo) and fl[0][1] == po
+    assert gs == 0 and ps_flags == 0 and iters >= max(it_o)
     assert tg == to
     assert np.array_equal(Qg, Qo)
     assert np.array_equal(xig, xio)

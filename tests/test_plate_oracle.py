@@ -306,3 +306,32 @@ def test_coupled_step_balances_momentum_in_a_periodic_box():
     assert moved > 1e-4                      # the plate was pushed by the stream
     assert np.max(np.abs(P1 - P0)) <= 1e-12 * moved + 1e-15
     assert abs(t1 - 4 * dt) <= 1e-15 and max(iters) <= 6
+
+
+def test_plate_force_is_the_impulse_the_fluid_loses():
+    """Eq. 19 numerators: a uniform load gives force q L and power q.U L; through a coupled step
+    in a periodic box the fluid's momentum changes by exactly -dt times the plate force."""
+    ps = W.PlateSpec(n_el=5, n_markers=50, clamped=0)
+    F = np.zeros((2, 50))
+    F[0], F[1] = 0.4, -0.3
+    U = np.zeros((2, 50))
+    U[0], U[1] = 0.5, 2.0
+    f, pw = O.plate_force(ps, F, U)
+    assert np.allclose(f, [0.4, -0.3], rtol=0, atol=1e-15) and abs(pw - (0.2 - 0.6)) <= 1e-15
+    g = 1.4
+    spec = W.GridSpec(dim=2, n=(48, 40, 1), lo=(-1.5, -1.25, 0.0), hi=(1.5, 1.25, 1.0), gamma=g,
+                      Re=300.0, qinf=W.freestream(2, g, vel=(0.1, 0.0, 0.0)), scheme=W.TENO5,
+                      bc=((2, 2), (2, 2), (0, 0)), max_markers=40)
+    h = spec.h[0]
+    dt = 0.5 / (2.2 / h)
+    spec.alpha_pen, spec.beta_pen = W.penalty_defaults(h, dt)
+    ps = W.PlateSpec(n_el=6, n_markers=40, rho_s=0.5, K_S=50.0, K_B=0.01, clamped=0)
+    Q = W.random_smooth_state(spec, seed=7, amp=1e-3, vel0=(0.1, 0.0, 0.0), periodic=True)
+    e, v = W.plate_straight(ps, origin=(-0.5, 0.05), theta=0.2, omega=0.05)
+    X, Uk, _ = O.plate_markers(ps, e, v)
+    Q1, _, _, _, _, _ = O.fsi_step(spec, ps, Q, np.zeros((2, 40)), e, v, 0.0, dt, nsteps=1)
+    f, pw = O.plate_force(ps, O.fsi_last_load(ps), Uk)
+    cell = h * spec.h[1]
+    dP = np.array([(Q1[1] - Q[1]).sum() * cell, (Q1[2] - Q[2]).sum() * cell])
+    assert np.max(np.abs(dP + dt * f)) <= 1e-12 * np.max(np.abs(dt * f))
+    assert abs(pw) > 0
