@@ -139,6 +139,18 @@ int ibfsa_rhs(ibfsa_grid *g, double *L);
  * each stage evaluated as a Qn + b (Qs + dt L(Qs)).  Markers stay fixed during the call. */
 int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps);
 
+/* Periodic Gaussian pressure source of Sec. 3.6 (Eq. 16), A_p = amp exp(-b ln2 |x - xc|^2)
+ * cos(omega t), entering the energy equation as A_p / (gamma - 1) (a source in the pressure
+ * equation; no mass or momentum source).  xc: [dim] host array.  amp = 0 removes it.  Length
+ * and time in the grid's units (for the paper's values A = 0.01, B = 16, omega = 2 pi in units
+ * of the sphere radius R and R/c: amp = -0.01, b = 16/R^2, omega = 2 pi c/R).  Evaluated at the
+ * stage times t, t + dt, t + dt/2 of each step on the grid's clock. */
+int ibfsa_set_source(ibfsa_grid *g, double amp, double b, double omega, const double *xc);
+/* The grid's clock: ibfsa_rk3_step and ibfsa_fsi_step advance it by dt per step; ibfsa_rhs
+ * evaluates the source at it.  Starts at 0. */
+int ibfsa_set_time(ibfsa_grid *g, double t);
+int ibfsa_get_time(ibfsa_grid *g, double *host_t);
+
 /* Split speeds alpha_d = max over the interior of |u_d| + c of the current state, d < dim,
  * to the host (synchronises), for dt = CFL / sum_d (alpha_d / h_d). */
 int ibfsa_max_wavespeed(ibfsa_grid *g, double *host_alpha);

@@ -19,7 +19,8 @@
  *                                                                after Eq. 5)
  *   4. viscous term: 4th-order central gradients of u, tau_ij, b = u.tau (no heat flux),
  *      then (1/Re) * 4th-order central divergence of [0, tau_.j, b_j] (Eq. 2-5)
- *   5. optional sponge: L -= sigma(n) (Q - Q_inf)
+ *   5. optional sponge: L -= sigma(n) (Q - Q_inf); optional periodic Gaussian pressure source
+ *      of Sec. 3.6 (Eq. 16) in the energy equation
  *   6. immersed boundary: U_ib(X_k) = sum_j u_j delta_h (X_k - x_j) h^d        (Eq. 8)
  *      F_k = alpha_pen xi_k + beta_pen (U_ib - U_k)                           (Eq. 7)
  *      f_j = - sum_k F_k delta_h(X_k - x_j) dS_k   (in marker order)          (Eq. 9)
@@ -387,6 +388,28 @@ static void sponge(const pgrid *G, const orc_desc *d, const double *Q, double *L
       }
 }
 
+/* Periodic Gaussian pressure source of Sec. 3.6 (Eq. 16), A_p = amp exp(-b ln2 r^2) cos(w t):
+ * read as a source in the pressure equation, i.e. A_p / (gamma - 1) in the energy equation
+ * (no mass or momentum source). */
+static void pressure_source(const pgrid *G, const orc_desc *d, double t, double *L) {
+  if (d->src_amp == 0.0) return;
+  const double LN2 = 0.693147180559945309417;
+  size_t Nu = (size_t)G->n[0] * G->n[1] * G->n[2];
+  double scale = (d->src_amp * cos(d->src_omega * t)) / (d->gamma - 1.0);
+  for (int k = 0; k < G->n[2]; k++)
+    for (int j = 0; j < G->n[1]; j++)
+      for (int i = 0; i < G->n[0]; i++) {
+        int I[3] = {i, j, k};
+        double r2 = 0.0;
+        for (int a = 0; a < G->dim; a++) {
+          double x = d->lo[a] + ((double)I[a] + 0.5) * G->h[a];
+          r2 = r2 + (x - d->src_xc[a]) * (x - d->src_xc[a]);
+        }
+        size_t o = (G->nv - 1) * Nu + uidx(G, i, j, k);
+        L[o] = L[o] + exp(-(d->src_b * LN2) * r2) * scale;
+      }
+}
+
 /* ----------------------------------------------------------------------------------------- */
 /* Immersed boundary (Eq. 7-11)                                                               */
 /* ----------------------------------------------------------------------------------------- */
@@ -539,6 +562,7 @@ static int rhs_impl(const orc_desc *d, const double *Q, int nm, const double *X,
   convective(&G, d, W, u, p, alpha, L);
   if (d->Re > 0.0) viscous(&G, d, u, L);
   sponge(&G, d, Q, L);
+  pressure_source(&G, d, d->time, L);
   if (nm > 0) rc = ib_source(&G, d, u, nm, X, U, dS, xi, L, F, rate);
   free(W); free(rho); free(u); free(p);
   return rc;
@@ -547,7 +571,8 @@ static int rhs_impl(const orc_desc *d, const double *Q, int nm, const double *X,
 /* nsteps of third-order TVD Runge-Kutta (Shu-Osher):
  *   Q1 = Qn + dt L(Qn);  Q2 = 3/4 Qn + 1/4 (Q1 + dt L(Q1));  Qn+1 = 1/3 Qn + 2/3 (Q2 + dt L(Q2))
  * written uniformly as Q^(s+1) = a_s Qn + b_s (Q^(s) + dt L(Q^(s))), (a,b) = (0,1),(3/4,1/4),
- * (1/3,2/3), applied to Q and to xi (xi' = U_ib - U).  Markers are fixed during the step. */
+ * (1/3,2/3), applied to Q and to xi (xi' = U_ib - U).  Markers are fixed during the step.  The
+ * stages are evaluated at the times t, t + dt, t + dt/2 from t = d->time (source of Eq. 16). */
 int orc_rk3(const orc_desc *d, double *Q, int nm, const double *X, const double *U,
             const double *dS, double *xi, double dt, int nsteps) {
   int rc = check_desc(d);
@@ -561,18 +586,23 @@ int orc_rk3(const orc_desc *d, double *Q, int nm, const double *X, const double 
   double *xs = calloc(mx, sizeof(double)), *x0 = calloc(mx, sizeof(double));
   double *rate = calloc(mx, sizeof(double));
   const double A[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0}, B[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  const double C[3] = {0.0, 1.0, 0.5}; /* stage times t + C dt */
+  orc_desc ds = *d;
+  double t = d->time;
   for (int step = 0; step < nsteps && rc == 0; step++) {
     memcpy(Q0, Q, sizeof(double) * M);
     memcpy(Qs, Q, sizeof(double) * M);
     if (nm > 0) { memcpy(x0, xi, sizeof(double) * mx); memcpy(xs, xi, sizeof(double) * mx); }
     for (int s = 0; s < 3 && rc == 0; s++) {
-      rc = orc_rhs(d, Qs, nm, X, U, dS, xs, Lb, NULL, rate, NULL);
+      ds.time = t + C[s] * dt;
+      rc = orc_rhs(&ds, Qs, nm, X, U, dS, xs, Lb, NULL, rate, NULL);
       for (size_t o = 0; o < M; o++) Qs[o] = A[s] * Q0[o] + B[s] * (Qs[o] + dt * Lb[o]);
       for (size_t o = 0; o < (size_t)d->dim * nm; o++)
         xs[o] = A[s] * x0[o] + B[s] * (xs[o] + dt * rate[o]);
     }
     memcpy(Q, Qs, sizeof(double) * M);
     if (nm > 0) memcpy(xi, xs, sizeof(double) * (size_t)d->dim * nm);
+    t = t + dt;
   }
   free(Qs); free(Lb); free(Q0); free(xs); free(x0); free(rate);
   return rc;

@@ -18,6 +18,10 @@ typedef struct {
   int sponge_cells;     /* 0: no sponge */
   double sponge_sigma;  /* sigma_max */
   double alpha_pen, beta_pen; /* Eq. 7 constants */
+  /* periodic Gaussian pressure source (Sec. 3.6, Eq. 16), added to the energy equation:
+   * S_E = src_amp exp(-src_b ln2 |x - src_xc|^2) cos(src_omega t) / (gamma - 1); src_amp = 0: none */
+  double src_amp, src_b, src_omega, src_xc[3];
+  double time;          /* time at which orc_rhs evaluates the source; start time of orc_rk3 */
 } orc_desc;
 
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_BOUNDS = -4, ORC_ERR_NOMEM = -7 };

@@ -49,6 +49,11 @@ class OrcDesc(ctypes.Structure):
         ("sponge_sigma", ctypes.c_double),
         ("alpha_pen", ctypes.c_double),
         ("beta_pen", ctypes.c_double),
+        ("src_amp", ctypes.c_double),
+        ("src_b", ctypes.c_double),
+        ("src_omega", ctypes.c_double),
+        ("src_xc", ctypes.c_double * 3),
+        ("time", ctypes.c_double),
     ]
 
 
@@ -78,7 +83,7 @@ def lib():
     return _lib
 
 
-def desc(spec) -> OrcDesc:
+def desc(spec, t: float = 0.0) -> OrcDesc:
     d = OrcDesc()
     d.dim = spec.dim
     for a in range(3):
@@ -96,6 +101,12 @@ def desc(spec) -> OrcDesc:
     d.sponge_sigma = spec.sponge_sigma
     d.alpha_pen = spec.alpha_pen
     d.beta_pen = spec.beta_pen
+    d.src_amp = float(spec.src_amp)
+    d.src_b = float(spec.src_b)
+    d.src_omega = float(spec.src_omega)
+    for a in range(3):
+        d.src_xc[a] = float(spec.src_xc[a])
+    d.time = float(t)
     return d
 
 
@@ -135,15 +146,15 @@ def _markers(spec, X, U, dS, xi):
     return nm, X, U, dS, xi
 
 
-def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False):
-    """RHS L(Q) + S of every interior cell, shape [nv][nz][ny][nx]."""
+def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0):
+    """RHS L(Q) + S of every interior cell at time t, shape [nv][nz][ny][nx]."""
     Q = _f64(Q)
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     L = np.zeros_like(Q)
     F = np.zeros((spec.dim, max(nm, 1)))
     rate = np.zeros((spec.dim, max(nm, 1)))
     alpha = np.zeros(3)
-    d = desc(spec)
+    d = desc(spec, t)
     rc = lib().orc_rhs(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi), _p(L), _p(F),
                        _p(rate), _p(alpha))
     if rc != ORC_OK:
@@ -167,12 +178,12 @@ def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None):
     return L
 
 
-def rk3(spec, Q, dt, nsteps=1, X=None, U=None, dS=None, xi=None):
-    """nsteps SSP-RK3 steps; returns (Q, xi)."""
+def rk3(spec, Q, dt, nsteps=1, X=None, U=None, dS=None, xi=None, t=0.0):
+    """nsteps SSP-RK3 steps from time t; returns (Q, xi)."""
     Q = _f64(Q).copy()
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     xi = xi.copy() if xi is not None else None
-    d = desc(spec)
+    d = desc(spec, t)
     rc = lib().orc_rk3(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi), float(dt),
                        int(nsteps))
     if rc != ORC_OK:
@@ -366,14 +377,15 @@ def plate_static(ps, e0, Qf):
     return e, it.value
 
 
-def fsi_step(spec, ps, Q, xi, e, v, t, dt, nsteps=1):
-    """nsteps coupled plate-fluid steps; returns (Q, xi, e, v, t, Newton iterations per step)."""
+def fsi_step(spec, ps, Q, xi, e, v, t, dt, nsteps=1, tf=None):
+    """nsteps coupled plate-fluid steps (plate clock t, fluid clock tf, default t); returns
+    (Q, xi, e, v, t, Newton iterations per step)."""
     Q = _f64(Q).copy()
     xi = _f64(xi).copy()
     e, v = _f64(e).copy(), _f64(v).copy()
     tt = ctypes.c_double(float(t))
     iters = (ctypes.c_int * max(1, nsteps))()
-    d = desc(spec)
+    d = desc(spec, t if tf is None else tf)
     pd = plate_desc(ps)
     rc = _plate_lib().orc_fsi_step(ctypes.byref(d), ctypes.byref(pd), _p(Q), _p(xi), _p(e), _p(v),
                                    ctypes.cast(ctypes.pointer(tt), _D), float(dt), int(nsteps),

@@ -548,6 +548,9 @@ int orc_fsi_step(const orc_desc *d, const orc_plate *p, double *Q, double *xi, d
   double *Qf = calloc(nd, sizeof(double));
   const double A[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0}, B[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
   const double W[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+  const double C[3] = {0.0, 1.0, 0.5};
+  orc_desc ds = *d;
+  double tf = d->time;  /* the fluid's clock (pressure source of Eq. 16) */
   for (int step = 0; step < nsteps && rc == ORC_OK; step++) {
     orc_plate_markers(p, e, v, X, U, dS);
     memcpy(Q0, Q, sizeof(double) * M);
@@ -555,7 +558,8 @@ int orc_fsi_step(const orc_desc *d, const orc_plate *p, double *Q, double *xi, d
     memcpy(x0, xi, sizeof(double) * 2 * nm);
     memcpy(xs, xi, sizeof(double) * 2 * nm);
     for (int s = 0; s < 3 && rc == ORC_OK; s++) {
-      rc = orc_rhs(d, Qs, nm, X, U, dS, xs, Lb, F, rate, NULL);
+      ds.time = tf + C[s] * dt;
+      rc = orc_rhs(&ds, Qs, nm, X, U, dS, xs, Lb, F, rate, NULL);
       for (size_t o = 0; o < (size_t)2 * nm; o++)
         Fbar[o] = s == 0 ? W[0] * F[o] : Fbar[o] + W[s] * F[o];
       for (size_t o = 0; o < M; o++) Qs[o] = A[s] * Q0[o] + B[s] * (Qs[o] + dt * Lb[o]);
@@ -575,6 +579,7 @@ int orc_fsi_step(const orc_desc *d, const orc_plate *p, double *Q, double *xi, d
     rc = orc_plate_step(p, e, v, t_new, dt, Qf, &it);
     if (iters) iters[step] = it;
     *t = t_new;
+    tf = tf + dt;
   }
   free(Qs); free(Lb); free(Q0); free(xs); free(x0); free(rate); free(F); free(Fbar);
   free(X); free(U); free(dS); free(Qf);

@@ -21,7 +21,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr"]
 
 UNITS = {
-    "api.cu": [],
+    "api.cu": ["-Xcompiler", "-ffp-contract=off"],
     "stage_fp64_strict.cu": ["--fmad=false"],
     "stage_fp64_fast.cu": ["--fmad=true"],
     "stage_fp32.cu": ["--fmad=true"],

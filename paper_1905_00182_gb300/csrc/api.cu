@@ -2,6 +2,7 @@
 // object, and the host sequence of stages of the third-order SSP Runge-Kutta step
 // (arXiv:1905.00182, Sec. 2, text after Eq. 5).
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -226,6 +227,10 @@ static cudaError_t run_stage(Grid *G, const StageArgs &s) {
 
 cudaError_t grid_stage(Grid *G, const StageArgs &s) { return run_stage(G, s); }
 
+double source_scale(const Grid &G, double t) {
+  return G.p.src_on ? (G.src_amp * cos(G.src_omega * t)) / (G.d.gamma - 1.0) : 0.0;
+}
+
 int api_fail(int code, const char *msg) { return fail(code, "%s", msg); }
 
 }  // namespace ibfsa
@@ -300,6 +305,9 @@ int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t wor
   G.p.probe_scratch = (double *)(w + L.reduce);
   G.p.mlp_floor = 1e-9f;
   G.mlp_set = false;
+  G.t = 0.0;
+  G.src_amp = 0.0;
+  G.src_omega = 0.0;
   G.p.nm = 0;
   cudaError_t e = cudaMemsetAsync(G.p.status, 0, sizeof(int) * 4, G.stream);
   if (e == cudaSuccess)
@@ -449,6 +457,7 @@ int ibfsa_rhs(ibfsa_grid *g, double *L) {
   s.Lout = L;
   s.xis = G.xi;
   s.stage = -1;
+  s.src_scale = source_scale(G, G.t);
   s.prof = &G.prof;
   if (G.d.scheme == IBFSA_MLP_TENO5 && !G.mlp_set)
     return fail(IBFSA_ERR_ARG, "IBFSA_MLP_TENO5 grid without weights: call ibfsa_set_mlp");
@@ -464,6 +473,7 @@ int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps) {
     return fail(IBFSA_ERR_ARG, "IBFSA_MLP_TENO5 grid without weights: call ibfsa_set_mlp");
   // Shu-Osher coefficients: Q^(s+1) = a_s Qn + b_s (Q^(s) + dt L(Q^(s)))
   const double A[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0}, B[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+  const double C[3] = {0.0, 1.0, 0.5};  // stage times t + C dt
   for (int step = 0; step < nsteps; step++) {
     const double *in[3] = {G.Q, G.Q1, G.Q2};
     double *outs[3] = {G.Q1, G.Q2, G.Q};  // stage 3 overwrites Qn cell by cell (pointwise read)
@@ -481,11 +491,38 @@ int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps) {
       a.b = B[s];
       a.dt = dt;
       a.stage = s;
+      a.src_scale = source_scale(G, G.t + C[s] * dt);
       a.prof = &G.prof;
       cudaError_t e = run_stage(&G, a);
       if (e != cudaSuccess) return cuda_fail(e, "ibfsa_rk3_step");
     }
+    G.t = G.t + dt;
   }
+  return IBFSA_OK;
+}
+
+int ibfsa_set_source(ibfsa_grid *g, double amp, double b, double omega, const double *xc) {
+  if (!g) return fail(IBFSA_ERR_ARG, "NULL grid");
+  Grid &G = g->g;
+  if (amp != 0.0 && (!xc || !(b > 0.0) || !isfinite(amp) || !isfinite(omega)))
+    return fail(IBFSA_ERR_ARG, "pressure source needs b > 0, finite amp and omega, and a centre");
+  G.src_amp = amp;
+  G.src_omega = omega;
+  G.p.src_on = amp != 0.0;
+  G.p.src_b = b;
+  for (int a = 0; a < 3; a++) G.p.src_xc[a] = (amp != 0.0 && a < G.p.dim) ? xc[a] : 0.0;
+  return IBFSA_OK;
+}
+
+int ibfsa_set_time(ibfsa_grid *g, double t) {
+  if (!g || !isfinite(t)) return fail(IBFSA_ERR_ARG, "NULL grid or non-finite time");
+  g->g.t = t;
+  return IBFSA_OK;
+}
+
+int ibfsa_get_time(ibfsa_grid *g, double *host_t) {
+  if (!g || !host_t) return fail(IBFSA_ERR_ARG, "NULL argument");
+  *host_t = g->g.t;
   return IBFSA_OK;
 }
 

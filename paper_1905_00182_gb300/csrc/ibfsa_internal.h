@@ -30,6 +30,10 @@ struct Plan {
   int sponge_cells;
   double sponge_sigma;
   double alpha_pen, beta_pen;
+  // periodic Gaussian pressure source (Sec. 3.6, Eq. 16) in the energy equation:
+  // src_scale exp(-src_b ln2 |x - src_xc|^2), src_scale = amp cos(omega t_stage) / (gamma - 1)
+  int src_on;
+  double src_b, src_xc[3], src_scale;
   double hprod;        // product of h over active directions
   // TENO: 1/sum of kept linear weights per cut-off mask (bit k = stencil k kept)
   double teno_w[8][3];
@@ -103,6 +107,8 @@ struct Grid {
   int max_probes;
   bool qn32_valid;  // FP32 form: qn32 matches Qn
   bool mlp_set;     // learned weights attached (ibfsa_set_mlp)
+  double t;         // the grid's clock (stage times t, t + dt, t + dt/2 of a step)
+  double src_amp, src_omega;  // pressure source amplitude and angular frequency
   Prof prof;
 };
 
@@ -128,6 +134,7 @@ struct StageArgs {
   double *xio;
   double a, b, dt;
   int stage;
+  double src_scale;   // amp cos(omega t_stage) / (gamma - 1) of the pressure source (0: none)
   Prof *prof;
 };
 cudaError_t strict_stage(const Plan &p, const StageArgs &s, cudaStream_t st);
@@ -152,6 +159,8 @@ cudaError_t fast_probe(const Plan &p, const double *Q, int np, const double *xp,
 
 // One stage (or right-hand side) of a grid in its arithmetic form (api.cu).
 cudaError_t grid_stage(Grid *G, const StageArgs &s);
+// The pressure source's stage factor amp cos(omega t) / (gamma - 1) at time t (api.cu).
+double source_scale(const Grid &G, double t);
 int api_fail(int code, const char *msg);  // records the message, returns code
 
 }  // namespace ibfsa

@@ -817,6 +817,7 @@ int ibfsa_fsi_step(ibfsa_grid *g, ibfsa_plate *p, double dt, int nsteps) {
   const int M = G.d.max_markers, nm = P.P.nm;
   const double A[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0}, B[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
   const double Wt[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+  const double C[3] = {0.0, 1.0, 0.5};  // stage times of the fluid's clock
   for (int step = 0; step < nsteps; step++) {
     prof_begin(&G.prof, G.stream);
     plate::k_markers<<<(nm + 127) / 128, 128, 0, G.stream>>>(P.P, P.e, P.v, P.mk_el, P.mk_S,
@@ -841,6 +842,7 @@ int ibfsa_fsi_step(ibfsa_grid *g, ibfsa_plate *p, double dt, int nsteps) {
       a.b = B[s];
       a.dt = dt;
       a.stage = s;
+      a.src_scale = source_scale(G, G.t + C[s] * dt);
       a.prof = &G.prof;
       e = grid_stage(&G, a);
       if (e != cudaSuccess) return cuda_err(e, "ibfsa_fsi_step stage");
@@ -853,6 +855,7 @@ int ibfsa_fsi_step(ibfsa_grid *g, ibfsa_plate *p, double dt, int nsteps) {
     }
     e = launch_step(P, dt, P.Fbar, &G.prof);
     if (e != cudaSuccess) return cuda_err(e, "ibfsa_fsi_step plate");
+    G.t = G.t + dt;
   }
   return IBFSA_OK;
 }

@@ -866,6 +866,17 @@ __global__ void __launch_bounds__(128) k_spread32(Plan p, const double *__restri
 //   mode 0: L out (FP64 copy);  mode 1: dout = b (din + dt L);
 //   mode 2: Qn += b (din + dt L) in FP64 and qn32 = (float)(Qn - q_inf)
 // ------------------------------------------------------------------------------------------
+// periodic Gaussian pressure source (Sec. 3.6, Eq. 16) of cell (i, j, k): energy-equation term
+__device__ __forceinline__ float pressure_source32(const Plan &p, int dim, int i, int j, int k) {
+  const int I[3] = {i, j, k};
+  float r2 = 0.f;
+  for (int a = 0; a < dim; a++) {
+    float dx = (float)(p.lo[a] + ((double)I[a] + 0.5) * p.h[a] - p.src_xc[a]);
+    r2 += dx * dx;
+  }
+  return expf(-(float)(p.src_b * 0.693147180559945309417) * r2) * (float)p.src_scale;
+}
+
 template <int DIM, bool VISC>
 __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__restrict__ din,
                                                       float *__restrict__ dout, double *Qn,
@@ -915,6 +926,11 @@ __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__res
         Lc[c] -= sig * qp;
       }
     }
+  }
+  if (p.src_on) {
+    int i = (int)(t % p.n[0]);
+    long long r = t / p.n[0];
+    Lc[NV - 1] += pressure_source32(p, DIM, i, (int)(r % p.n[1]), (int)(r / p.n[1]));
   }
   if (mode == 0) {
 #pragma unroll
@@ -1130,6 +1146,7 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
           for (int cc = 0; cc < 5; cc++) Lc[cc] -= sig * (p.qn32[cc * p.N + t] + Dnext[cc]);
         }
       }
+      if (p.src_on) Lc[4] += pressure_source32(p, 3, X, Y, d);
       if (mode == 0) {
 #pragma unroll
         for (int cc = 0; cc < 5; cc++) Lout[cc * p.N + t] = (double)Lc[cc];
@@ -1321,6 +1338,8 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   int mode = !advance ? 0 : (s.stage < 2 ? 1 : 2);
+  Plan q = p;
+  q.src_scale = s.src_scale;
   prof_begin(pr, st);
   if (p.Re > 0.0 && DIM == 3) {
     using namespace vm;
@@ -1328,14 +1347,14 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
                              (int)SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((p.n[0] + TX - 1) / TX, (p.n[1] + TY - 1) / TY, (p.n[2] + ZC - 1) / ZC);
-    k_visc_march32<<<grid, VT, SMEM, st>>>(p, din, dout, const_cast<double *>(Qn), s.Lout,
+    k_visc_march32<<<grid, VT, SMEM, st>>>(q, din, dout, const_cast<double *>(Qn), s.Lout,
                                                (float)s.b, (float)s.dt, mode);
   } else if (p.Re > 0.0)
     k_finish32<DIM, true><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(
-        p, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
+        q, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
   else
     k_finish32<DIM, false><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(
-        p, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
+        q, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);
   prof_end(pr, K_FINISH, st);
   return cudaGetLastError();
 }

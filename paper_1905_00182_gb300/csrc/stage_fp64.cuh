@@ -615,6 +615,16 @@ __global__ void __launch_bounds__(THREADS) k_finish(Plan p, const double *__rest
       for (int c = 0; c < NV; c++) Lc[c] = Lc[c] - sig * (Qs[c * p.N + t] - p.qinf[c]);
     }
   }
+  if (p.src_on) {  // periodic Gaussian pressure source (Sec. 3.6, Eq. 16), energy equation
+    const double LN2 = 0.693147180559945309417;
+    double r2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      double x = p.lo[a] + ((double)I[a] + 0.5) * p.h[a];
+      r2 = r2 + (x - p.src_xc[a]) * (x - p.src_xc[a]);
+    }
+    Lc[NV - 1] = Lc[NV - 1] + exp(-(p.src_b * LN2) * r2) * p.src_scale;
+  }
   if constexpr (STRICT) {
     if (p.nm > 0) {
       long long s = pad_index(p, I[0], I[1], I[2]);
@@ -754,7 +764,9 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   }
   double *out = advance ? s.Qo : s.Lout;
   prof_begin(pr, st);
-  k_finish<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(p, s.Qs, s.Qn, out, s.a, s.b, s.dt,
+  Plan q = p;
+  q.src_scale = s.src_scale;
+  k_finish<DIM><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(q, s.Qs, s.Qn, out, s.a, s.b, s.dt,
                                                              advance);
   prof_end(pr, K_FINISH, st);
   return cudaGetLastError();

@@ -44,6 +44,7 @@ EXPORTS = (
     "ibfsa_body_force", "ibfsa_plate_workspace_bytes", "ibfsa_plate_create",
     "ibfsa_plate_destroy", "ibfsa_plate_set_state", "ibfsa_plate_get_state", "ibfsa_plate_step",
     "ibfsa_plate_markers", "ibfsa_plate_get_status", "ibfsa_fsi_step", "ibfsa_plate_force",
+    "ibfsa_set_source", "ibfsa_set_time", "ibfsa_get_time",
 )
 MLP_NPARAM = 2403
 
@@ -153,6 +154,9 @@ def lib():
                                              ctypes.POINTER(ctypes.c_int)]
         L.ibfsa_fsi_step.argtypes = [_P, _P, ctypes.c_double, ctypes.c_int]
         L.ibfsa_plate_force.argtypes = [_P, _P, _P]
+        L.ibfsa_set_source.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]
+        L.ibfsa_set_time.argtypes = [_P, ctypes.c_double]
+        L.ibfsa_get_time.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
 
@@ -448,6 +452,21 @@ def ibfsa_plate_force(p):
     return np.array([f[0], f[1]]), pw.value
 
 
+def ibfsa_set_source(g, amp: float, b: float, omega: float, xc):
+    c = (ctypes.c_double * 3)(*[float(x) for x in list(xc) + [0.0] * (3 - len(xc))])
+    _check(lib().ibfsa_set_source(g, float(amp), float(b), float(omega), ctypes.cast(c, _P)))
+
+
+def ibfsa_set_time(g, t: float):
+    _check(lib().ibfsa_set_time(g, float(t)))
+
+
+def ibfsa_get_time(g) -> float:
+    t = ctypes.c_double(0.0)
+    _check(lib().ibfsa_get_time(g, ctypes.byref(t)))
+    return t.value
+
+
 def ibfsa_fsi_step(g, p, dt: float, nsteps: int = 1):
     _check(lib().ibfsa_fsi_step(g, p, float(dt), int(nsteps)))
 
@@ -479,6 +498,8 @@ class Grid:
         self.ws_ptr = (base + 255) & ~255
         self.h = ibfsa_create_grid(self.desc, self.ws_ptr, self.ws_bytes, self.stream.cuda_stream)
         self.nm = 0
+        if spec.src_amp != 0.0:
+            ibfsa_set_source(self.h, spec.src_amp, spec.src_b, spec.src_omega, spec.src_xc)
         self._state_src = None
         self._marker_src = None
 
@@ -548,6 +569,12 @@ class Grid:
 
     def status(self) -> int:
         return ibfsa_get_status(self.h)
+
+    def time(self) -> float:
+        return ibfsa_get_time(self.h)
+
+    def set_time(self, t: float):
+        ibfsa_set_time(self.h, t)
 
 
 class Plate:

@@ -51,6 +51,11 @@ class GridSpec:
     alpha_pen: float = 0.0
     beta_pen: float = 0.0
     max_markers: int = 0
+    # periodic Gaussian pressure source (Sec. 3.6, Eq. 16): amp exp(-b ln2 |x - xc|^2) cos(omega t)
+    src_amp: float = 0.0
+    src_b: float = 0.0
+    src_omega: float = 0.0
+    src_xc: tuple = (0.0, 0.0, 0.0)
 
     @property
     def nv(self) -> int:
@@ -316,11 +321,7 @@ def rotating_cylinder_2d(n: int = 2048, markers: int = 1024, scheme: int = WENO5
     return dict(spec=spec, Q=Q, X=X, U=U, dS=dS, dt=dt, steps=20000, probes=probes)
 
 
-def sphere_pulse_3d(n: int = 512, markers: int = 20000, Re: float = 1e4, scheme: int = TENO5,
-                    precision: int = FP64, probes: int = 1000, L: float = 8.0):
-    """Acoustic pulse scattered by a rigid sphere (Sec. 3.6 analogue): [-L,L]^3 (h = 2L/n), sphere
-    D = 1 at the origin with Fibonacci markers, Gaussian pulse (1e-3, half-width 0.2) at (2,0,0),
-    TENO5, zero-gradient boundaries, probes on a Fibonacci sphere r = 6 (scaled with L)."""
+def _sphere_setup(n, markers, Re, scheme, precision, probes, L):
     g = 1.4
     spec = GridSpec(dim=3, n=(n, n, n), lo=(-L, -L, -L), hi=(L, L, L), gamma=g, Re=Re,
                     qinf=freestream(3, g), scheme=scheme, precision=precision,
@@ -328,9 +329,19 @@ def sphere_pulse_3d(n: int = 512, markers: int = 20000, Re: float = 1e4, scheme:
     h = spec.h[0]
     dt = 0.5 / (3.0 / h)
     spec.alpha_pen, spec.beta_pen = penalty_defaults(h, dt)
-    Q = gaussian_pulse_state(spec, (2.0, 0.0, 0.0))
     X, U, dS = fibonacci_sphere(markers, 0.5)
     pr, _, _ = fibonacci_sphere(probes, 6.0 * L / 8.0)
+    return spec, dt, X, U, dS, pr
+
+
+def sphere_pulse_3d(n: int = 512, markers: int = 20000, Re: float = 1e4, scheme: int = TENO5,
+                    precision: int = FP64, probes: int = 1000, L: float = 8.0, state: bool = True):
+    """Acoustic pulse scattered by a rigid sphere (Sec. 3.6 analogue): [-L,L]^3 (h = 2L/n), sphere
+    D = 1 at the origin with Fibonacci markers, Gaussian pulse (1e-3, half-width 0.2) at (2,0,0),
+    TENO5, zero-gradient boundaries, probes on a Fibonacci sphere r = 6 (scaled with L).
+    state=False skips building the host state (Q = None)."""
+    spec, dt, X, U, dS, pr = _sphere_setup(n, markers, Re, scheme, precision, probes, L)
+    Q = gaussian_pulse_state(spec, (2.0, 0.0, 0.0)) if state else None
     return dict(spec=spec, Q=Q, X=X, U=U, dS=dS, dt=dt, steps=2000, probes=pr)
 
 
@@ -368,6 +379,28 @@ def flapping_plate_2d(n=(4096, 2048), n_el: int = 40, markers: int = 800,
     Q = random_smooth_state(spec, seed=3, amp=0.0, modes=1, vel0=(U0, 0.0, 0.0))
     probes = ring_probes(360, 8.0, center=(-0.5, 0.0))
     return dict(spec=spec, plate=ps, Q=Q, e=e, v=v, dt=dt, probes=probes, U_ref=U)
+
+
+def sphere_source_3d(n: int = 512, markers: int = 20000, Re: float = 1e4, scheme: int = TENO5,
+                     precision: int = FP64, probes: int = 1000, L: float = 8.0):
+    """Sound of a periodic Gaussian source scattered by a rigid sphere (Sec. 3.6): the sphere
+    workload at rest with the source of Eq. 16 instead of the initial pulse.  The paper's values
+    in units of the radius R = 0.5 and of R/c: A = 0.01, B = 16, omega = 2 pi, centre (2R, 0, 0)
+    -- here amp = -0.01, b = 16 / R^2, omega = 2 pi / R, xc = (1, 0, 0)."""
+    spec, dt, X, U, dS, pr = _sphere_setup(n, markers, Re, scheme, precision, probes, L)
+    R = 0.5
+    spec.src_amp, spec.src_b, spec.src_omega = -0.01, 16.0 / (R * R), 2.0 * math.pi / R
+    spec.src_xc = (2.0 * R, 0.0, 0.0)
+    # the fluid starts at rest (rho = 1, u = 0, p = 1/gamma): rest_state(spec)
+    return dict(spec=spec, Q=None, X=X, U=U, dS=dS, dt=dt, steps=2000, probes=pr)
+
+
+def rest_state(spec: GridSpec) -> np.ndarray:
+    """Uniform free-stream state of the grid (host)."""
+    Q = np.empty(spec.shape())
+    for c in range(spec.nv):
+        Q[c] = spec.qinf[c]
+    return Q
 
 
 def gaussian_pulse_state_torch(spec: GridSpec, center, amp: float = 1e-3, halfwidth: float = 0.2,
