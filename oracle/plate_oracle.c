@@ -29,9 +29,9 @@
  *  - Time: the implicit midpoint rule
  *      e_{n+1} = e_n + dt (v_n + v_{n+1}) / 2,
  *      M (v_{n+1} - v_n) = dt [Q_f - Q_int((e_n + e_{n+1}) / 2)],
- *    solved by Newton's method for d = e_{n+1} - e_n; each Newton system is factorised by a
- *    banded LDL^T decomposition (half-bandwidth 7).  The multiply-adds of the element dot
- *    products, of the elimination and of the forward substitution are single fused
+ *    solved by Newton's method for d = e_{n+1} - e_n; each Newton system, block tridiagonal
+ *    in the nodes, is solved by block cyclic reduction with 4 x 4 L D L^T blocks.  The
+ *    multiply-adds of the element dot products and of the reduction are single fused
  *    operations (C99 fma, one rounding); everything else is rounded operation by operation.  The rule conserves the linear and angular
  *    momentum of an unloaded free plate and hands the plate exactly the impulse dt Q_f of the
  *    step's load, so what the fluid loses the plate gains.
@@ -281,38 +281,97 @@ int orc_plate_internal(const orc_plate *p, const double *e, double *Qint, double
   return ORC_OK;
 }
 
-/* Banded LDL^T factorisation of the symmetric matrix A (A[i][k] = A(i, i + k), k = 0..BW, n
- * rows) in place: afterwards A[i][k], k >= 1, holds L(i + k, i), and rinv[i] = 1 / D(i).
- * Returns 0, or -1 on a zero or non-finite pivot. */
-static int band_ldlt_factor(double (*A)[BW + 1], double *rinv, int n) {
-  for (int i = 0; i < n; i++) {
-    double d = A[i][0];
+/* The Newton matrix is block tridiagonal in the nodes: D_j (4 x 4, node j with itself) and
+ * Br_j (node j with node j + 1).  It is solved by block cyclic reduction: at the level of stride
+ * s the blocks i = s, 3s, 5s, ... are eliminated (each needs D_i^-1 applied to its couplings and
+ * right-hand side), the blocks k = 0, 2s, 4s, ... take their Schur complements, until block 0
+ * is alone; then the eliminated blocks are recovered from coarse to fine.  A 4 x 4 block is
+ * factorised as L D L^T (upper triangle, reciprocal pivots).  Multiply-adds are fused (C99 fma)
+ * and every sum is taken in the order written. */
+static int ldlt4(double M[4][4], double rinv[4]) {
+  for (int i = 0; i < 4; i++) {
+    double d = M[i][i];
     if (!(d != 0.0) || !isfinite(d)) return -1;
     double r = 1.0 / d;
     rinv[i] = r;
-    double lk[BW + 1];
-    for (int k = 1; k <= BW && i + k < n; k++) lk[k] = A[i][k] * r;
-    for (int k = 1; k <= BW && i + k < n; k++)
-      for (int m = k; m <= BW && i + m < n; m++)
-        A[i + k][m - k] = fma(-lk[k], A[i][m], A[i + k][m - k]);
-    for (int k = 1; k <= BW && i + k < n; k++) A[i][k] = lk[k];
+    double lk[4];
+    for (int k = 1; i + k < 4; k++) lk[k] = M[i][i + k] * r;
+    for (int k = 1; i + k < 4; k++)
+      for (int m = k; i + m < 4; m++) M[i + k][i + m] = fma(-lk[k], M[i][i + m], M[i + k][i + m]);
+    for (int k = 1; i + k < 4; k++) M[i][i + k] = lk[k];
   }
   return 0;
 }
 
-/* Solve L D L^T x = b with the factors; b is overwritten by x.  In the back substitution the
- * seven products of a row are summed pairwise, ((p1 + p2) + (p3 + p4)) + ((p5 + p6) + p7), a
- * missing product (past the last row) counting as zero. */
-static void band_ldlt_solve(double (*A)[BW + 1], const double *rinv, double *b, int n) {
-  for (int i = 0; i < n; i++)
-    for (int k = 1; k <= BW && i + k < n; k++) b[i + k] = fma(-A[i][k], b[i], b[i + k]);
-  for (int i = 0; i < n; i++) b[i] = b[i] * rinv[i];
-  for (int i = n - 1; i >= 0; i--) {
-    double pr[BW + 2];
-    for (int k = 1; k <= BW + 1; k++) pr[k] = (k <= BW && i + k < n) ? A[i][k] * b[i + k] : 0.0;
-    double s = ((pr[1] + pr[2]) + (pr[3] + pr[4])) + ((pr[5] + pr[6]) + (pr[7] + pr[8]));
-    b[i] = b[i] - s;
+/* v <- (L D L^T)^-1 v with the factors of ldlt4 */
+static void solve4(double M[4][4], const double rinv[4], double v[4]) {
+  for (int i = 0; i < 4; i++)
+    for (int k = 1; i + k < 4; k++) v[i + k] = fma(-M[i][i + k], v[i], v[i + k]);
+  for (int i = 0; i < 4; i++) v[i] = v[i] * rinv[i];
+  for (int i = 3; i >= 0; i--)
+    for (int k = 1; i + k < 4; k++) v[i] = fma(-M[i][i + k], v[i + k], v[i]);
+}
+
+typedef double blk4[4][4];
+
+/* Solve the nb-block system (D, Br, b) into x; D, Br, b are overwritten.  Y, Z, y, rinv:
+ * scratch of nb blocks.  Returns 0, or -1 on a zero or non-finite pivot. */
+static int bcr_solve(int nb, blk4 *D, blk4 *Br, double (*b)[4], double (*x)[4], blk4 *Y,
+                     blk4 *Z, double (*y)[4], double (*rinv)[4]) {
+  int s;
+  for (s = 1; s < nb; s *= 2) {
+    for (int i = s; i < nb; i += 2 * s) { /* eliminated: odd multiples of s */
+      if (ldlt4(D[i], rinv[i])) return -1;
+      int right = i + s < nb;
+      for (int c = 0; c < 4; c++) {
+        double col[4];
+        for (int q = 0; q < 4; q++) col[q] = right ? Br[i][q][c] : 0.0;
+        solve4(D[i], rinv[i], col);
+        for (int q = 0; q < 4; q++) Y[i][q][c] = col[q]; /* D_i^-1 Br_i */
+        for (int q = 0; q < 4; q++) col[q] = Br[i - s][c][q];
+        solve4(D[i], rinv[i], col);
+        for (int q = 0; q < 4; q++) Z[i][q][c] = col[q]; /* D_i^-1 Br_{i-s}^T */
+      }
+      for (int q = 0; q < 4; q++) y[i][q] = b[i][q];
+      solve4(D[i], rinv[i], y[i]);                         /* D_i^-1 b_i */
+    }
+    for (int k = 0; k < nb; k += 2 * s) { /* survivors take the Schur complements */
+      int il = k - s, ir = k + s;
+      int hl = il >= 0, hr = ir < nb, hn = hr && ir + s < nb;
+      double Dn[4][4], bn[4], Bn[4][4];
+      for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) {
+          double t = D[k][r][c];
+          if (hl) for (int q = 0; q < 4; q++) t = fma(-Br[il][q][r], Y[il][q][c], t);
+          if (hr) for (int q = 0; q < 4; q++) t = fma(-Br[k][r][q], Z[ir][q][c], t);
+          Dn[r][c] = t;
+          double u = 0.0;
+          if (hn) for (int q = 0; q < 4; q++) u = fma(-Br[k][r][q], Y[ir][q][c], u);
+          Bn[r][c] = u;
+        }
+      for (int r = 0; r < 4; r++) {
+        double t = b[k][r];
+        if (hl) for (int q = 0; q < 4; q++) t = fma(-Br[il][q][r], y[il][q], t);
+        if (hr) for (int q = 0; q < 4; q++) t = fma(-Br[k][r][q], y[ir][q], t);
+        bn[r] = t;
+      }
+      memcpy(D[k], Dn, sizeof(Dn));
+      memcpy(Br[k], Bn, sizeof(Bn));
+      memcpy(b[k], bn, sizeof(bn));
+    }
   }
+  if (ldlt4(D[0], rinv[0])) return -1;
+  for (int q = 0; q < 4; q++) x[0][q] = b[0][q];
+  solve4(D[0], rinv[0], x[0]);
+  for (s = s / 2; s >= 1; s /= 2)
+    for (int i = s; i < nb; i += 2 * s)
+      for (int r = 0; r < 4; r++) {
+        double t = y[i][r];
+        for (int q = 0; q < 4; q++) t = fma(-Z[i][r][q], x[i - s][q], t);
+        if (i + s < nb) for (int q = 0; q < 4; q++) t = fma(-Y[i][r][q], x[i + s][q], t);
+        x[i][r] = t;
+      }
+  return 0;
 }
 
 /* Newton solve shared by the dynamic step (dt > 0) and the static solve (dt = 0).
@@ -335,9 +394,13 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
   element_mass(p, Ms);
   double *d = calloc(nd, sizeof(double)), *em = calloc(nd, sizeof(double));
   double *g = calloc(nd, sizeof(double)), *R = calloc(nd, sizeof(double));
-  double *x = calloc(nf, sizeof(double)), *rinv = calloc(nf, sizeof(double));
+  int nb = ne + 1; /* node blocks; a clamped plate's block 0 is sigma, padded to 4 x 4 */
+  double *x = calloc(nf, sizeof(double));
   double (*Ag)[BW + 1] = calloc((size_t)nd, sizeof(*Ag));
-  double (*A)[BW + 1] = calloc((size_t)nf, sizeof(*A));
+  blk4 *BD = calloc(nb, sizeof(blk4)), *BB = calloc(nb, sizeof(blk4));
+  blk4 *BY = calloc(nb, sizeof(blk4)), *BZ = calloc(nb, sizeof(blk4));
+  double (*bb)[4] = calloc(nb, sizeof(*bb)), (*bx)[4] = calloc(nb, sizeof(*bx));
+  double (*by)[4] = calloc(nb, sizeof(*by)), (*br)[4] = calloc(nb, sizeof(*br));
   double (*Rel)[8] = calloc((size_t)ne, sizeof(*Rel));
   double (*Jel)[8][8] = calloc((size_t)ne, sizeof(*Jel));
   int dynamic = dt > 0.0;
@@ -403,28 +466,38 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
         for (int c = r; c < 8; c++) Ag[I][c - r] = Ag[I][c - r] + Jel[el][r][c];
       }
     for (int I = 0; I < nd; I++) R[I] = R[I] - (dynamic ? c_load * Qf[I] : Qf[I]);
-    /* the free system: right-hand side -R and the band */
+    /* the free system in node blocks: right-hand side -R, D_j, Br_j from the band */
     if (clamped) {
       x[0] = -(tc * R[2] + ts * R[3]);
       for (int i = 1; i < nf; i++) x[i] = -R[i + 3];
     } else {
       for (int i = 0; i < nf; i++) x[i] = -R[i];
     }
-    if (clamped) {
-      A[0][0] = tc * (tc * Ag[2][0] + ts * Ag[2][1]) + ts * (tc * Ag[2][1] + ts * Ag[3][0]);
-      for (int k = 1; k <= BW; k++) {
-        int J = k + 3;
-        double a2 = J - 2 <= BW ? Ag[2][J - 2] : 0.0;
-        A[0][k] = tc * a2 + ts * Ag[3][J - 3];
+    for (int j = 0; j < nb; j++)
+      for (int r = 0; r < 4; r++) {
+        for (int c = 0; c < 4; c++) {
+          int lo = r < c ? r : c, off = r < c ? c - r : r - c;
+          BD[j][r][c] = Ag[4 * j + lo][off];
+          BB[j][r][c] = j + 1 < nb ? Ag[4 * j + r][4 + c - r] : 0.0;
+        }
+        bb[j][r] = clamped ? (j == 0 ? 0.0 : x[4 * j - 3 + r]) : x[4 * j + r];
       }
-      for (int i = 1; i < nf; i++)
-        for (int k = 0; k <= BW; k++) A[i][k] = Ag[i + 3][k];
-    } else {
-      for (int i = 0; i < nf; i++)
-        for (int k = 0; k <= BW; k++) A[i][k] = Ag[i][k];
+    if (clamped) { /* block 0: sigma and three idle unknowns */
+      for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) {
+          BD[0][r][c] = r == c ? 1.0 : 0.0;
+          BB[0][r][c] = r == 0 ? tc * Ag[2][2 + c] + ts * Ag[3][1 + c] : 0.0;
+        }
+      BD[0][0][0] = tc * (tc * Ag[2][0] + ts * Ag[2][1]) + ts * (tc * Ag[2][1] + ts * Ag[3][0]);
+      bb[0][0] = x[0];
     }
-    if (band_ldlt_factor(A, rinv, nf) != 0) { rc = ORC_PLATE_NOCONV; break; }
-    band_ldlt_solve(A, rinv, x, nf);
+    if (bcr_solve(nb, BD, BB, bb, bx, BY, BZ, by, br) != 0) { rc = ORC_PLATE_NOCONV; break; }
+    if (clamped) {
+      x[0] = bx[0][0];
+      for (int i = 1; i < nf; i++) x[i] = bx[(i + 3) / 4][(i + 3) % 4];
+    } else {
+      for (int i = 0; i < nf; i++) x[i] = bx[i / 4][i % 4];
+    }
     /* update: sigma moves the clamped slope along t */
     double *u = dynamic ? d : e;
     double inc = 0.0;
@@ -457,8 +530,8 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
       }
     }
   }
-  free(d); free(em); free(g); free(R); free(x); free(rinv); free(Ag); free(A); free(Rel);
-  free(Jel);
+  free(d); free(em); free(g); free(R); free(x); free(Ag); free(BD); free(BB); free(BY); free(BZ);
+  free(bb); free(bx); free(by); free(br); free(Rel); free(Jel);
   return rc;
 }
 

@@ -205,26 +205,39 @@ struct StepArgs {
 // matrices.  Per element and Gauss point: r_s, K_S (1 - 1/|r_s|) w l (times r_s) and the four
 // tangent factors s_ab = c2 r_a r_b (+ c1 on the diagonal).
 struct Smem {
-  double *en, *vn, *d, *em, *g, *R, *Qf, *x, *rinv;
+  double *en, *vn, *d, *em, *g, *R, *Qf, *x;
   double (*Ag)[BW + 1];
-  double (*A)[BW + 1];
   double (*Rel)[8];
+  // element scratch (element rows, Gauss-point factors) and, after assembly, the node blocks of
+  // the reduction share one region
   double (*Jel)[64];
   double (*gt)[5][2];   // per element, Gauss point: (w l c1) r_a
   double (*gs)[5][4];   // per element, Gauss point: s_ab, ab = 00, 01, 10, 11
+  double (*BD)[16];     // per node block: D_j (factor after elimination)
+  double (*BB)[16];     // Br_j, coupling to the next active block
+  double (*BY)[16];     // D_i^-1 Br_i
+  double (*BZ)[16];     // D_i^-1 Br_{i-s}^T
+  double (*BT)[16];     // new couplings of a level
+  double (*bb)[4], (*bx)[4], (*by)[4], (*br)[4];  // rhs, solution, D_i^-1 b_i, 1 / pivots
   double *D;            // [5][4]
   double *PD;           // [5][4][4]
   double *Ms, *Kb;      // [4][4]
   int *flags;
 };
 
+__host__ __device__ inline size_t union_doubles(int n_el) {
+  size_t ne = (size_t)n_el, nb = ne + 1;
+  size_t elem = 94 * ne, blocks = 96 * nb;
+  return elem > blocks ? elem : blocks;
+}
+
 __host__ __device__ inline size_t smem_doubles(int n_el) {
   size_t nd = 4 * (size_t)(n_el + 1), ne = (size_t)n_el;
-  return 9 * nd + 8 * nd + 8 * nd + 8 * ne + 64 * ne + 10 * ne + 20 * ne + 20 + 80 + 32 + 4;
+  return 8 * nd + 8 * nd + 8 * ne + union_doubles(n_el) + 20 + 80 + 32 + 4;
 }
 
 __device__ inline Smem carve(double *base, int n_el) {
-  int nd = 4 * (n_el + 1);
+  int nd = 4 * (n_el + 1), nb = n_el + 1;
   Smem s;
   double *p = base;
   s.en = p; p += nd;
@@ -235,19 +248,198 @@ __device__ inline Smem carve(double *base, int n_el) {
   s.R = p; p += nd;
   s.Qf = p; p += nd;
   s.x = p; p += nd;
-  s.rinv = p; p += nd;
   s.Ag = reinterpret_cast<double(*)[BW + 1]>(p); p += 8 * nd;
-  s.A = reinterpret_cast<double(*)[BW + 1]>(p); p += 8 * nd;
   s.Rel = reinterpret_cast<double(*)[8]>(p); p += 8 * n_el;
-  s.Jel = reinterpret_cast<double(*)[64]>(p); p += 64 * n_el;
-  s.gt = reinterpret_cast<double(*)[5][2]>(p); p += 10 * n_el;
-  s.gs = reinterpret_cast<double(*)[5][4]>(p); p += 20 * n_el;
+  double *u = p;
+  s.Jel = reinterpret_cast<double(*)[64]>(u);
+  s.gt = reinterpret_cast<double(*)[5][2]>(u + 64 * n_el);
+  s.gs = reinterpret_cast<double(*)[5][4]>(u + 74 * n_el);
+  s.BD = reinterpret_cast<double(*)[16]>(u);
+  s.BB = reinterpret_cast<double(*)[16]>(u + 16 * nb);
+  s.BY = reinterpret_cast<double(*)[16]>(u + 32 * nb);
+  s.BZ = reinterpret_cast<double(*)[16]>(u + 48 * nb);
+  s.BT = reinterpret_cast<double(*)[16]>(u + 64 * nb);
+  s.bb = reinterpret_cast<double(*)[4]>(u + 80 * nb);
+  s.bx = reinterpret_cast<double(*)[4]>(u + 84 * nb);
+  s.by = reinterpret_cast<double(*)[4]>(u + 88 * nb);
+  s.br = reinterpret_cast<double(*)[4]>(u + 92 * nb);
+  p += union_doubles(n_el);
   s.D = p; p += 20;
   s.PD = p; p += 80;
   s.Ms = p; p += 16;
   s.Kb = p; p += 16;
   s.flags = reinterpret_cast<int *>(p);
   return s;
+}
+
+// v <- (L D L^T)^-1 v for one 4 x 4 block factored in place (M row-major, upper triangle)
+__device__ __forceinline__ void solve4(const double *M, const double *rinv, double v[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int k = 1; i + k < 4; k++) v[i + k] = __fma_rn(-M[i * 4 + i + k], v[i], v[i + k]);
+#pragma unroll
+  for (int i = 0; i < 4; i++) v[i] = v[i] * rinv[i];
+#pragma unroll
+  for (int i = 3; i >= 0; i--)
+#pragma unroll
+    for (int k = 1; i + k < 4; k++) v[i] = __fma_rn(-M[i * 4 + i + k], v[i + k], v[i]);
+}
+
+// Block cyclic reduction of the node-block system (S.BD, S.BB, S.bb) into S.bx, all threads of
+// the block; returns false on a zero or non-finite pivot.  Per level: eliminated blocks
+// i = s, 3s, ... one per half-warp (4 x 4 L D L^T with the pivot's updates in parallel lanes,
+// then nine solves, one per lane); survivors k = 0, 2s, ... one item per thread for each
+// entry of D_k, Br_k (new) and b_k; then back substitution from coarse to fine.
+__device__ bool bcr_solve(const Smem &S, int nb, int *flag) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = nt >> 5, half = lane >> 4, hl = lane & 15;
+  // pivot pairs (k, m), 1 <= k <= m <= 3 - pi, for the 16 lanes of a half-warp
+  if (tid == 0) *flag = 0;
+  __syncthreads();
+  int s;
+  for (s = 1; s < nb; s *= 2) {
+    const int nelim = (nb - 1 - s) / (2 * s) + 1;
+    for (int base = 0; base < nelim; base += 2 * nwarps) {
+      const int t = base + 2 * warp + half;
+      const bool act = t < nelim;
+      const int i = s + 2 * s * t;
+      double *M = S.BD[act ? i : 0];
+      bool bad = false;
+#pragma unroll
+      for (int pi = 0; pi < 4; pi++) {
+        double dpiv = act ? M[pi * 4 + pi] : 1.0;
+        bad = bad || !(dpiv != 0.0) || !isfinite(dpiv);
+        double r = 1.0 / dpiv;
+        int n = 3 - pi;  // entries right of the pivot
+        // pair index hl -> (k, m) with 1 <= k <= m <= n
+        int k = 0, m = 0, q = hl;
+        for (int kk = 1; kk <= n; kk++) {
+          if (k == 0 && q < n - kk + 1) { k = kk; m = kk + q; }
+          else if (k == 0) q -= n - kk + 1;
+        }
+        double lk = 0.0;
+        if (act && k > 0) {
+          lk = M[pi * 4 + pi + k] * r;
+          M[(pi + k) * 4 + pi + m] = __fma_rn(-lk, M[pi * 4 + pi + m], M[(pi + k) * 4 + pi + m]);
+        }
+        __syncwarp();
+        if (act && k > 0 && m == k) M[pi * 4 + pi + k] = lk;
+        if (act && hl == 0) S.br[i][pi] = r;
+        __syncwarp();
+      }
+      if (act && bad && hl == 0) atomicOr(flag, 1);
+      if (act && hl < 9) {
+        double v[4];
+        const bool right = i + s < nb;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          if (hl < 4) v[q] = right ? S.BB[i][q * 4 + hl] : 0.0;
+          else if (hl < 8) v[q] = S.BB[i - s][(hl - 4) * 4 + q];
+          else v[q] = S.bb[i][q];
+        }
+        solve4(M, S.br[i], v);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          if (hl < 4) S.BY[i][q * 4 + hl] = v[q];
+          else if (hl < 8) S.BZ[i][q * 4 + hl - 4] = v[q];
+          else S.by[i][q] = v[q];
+        }
+      }
+    }
+    __syncthreads();
+    if (*flag) return false;
+    // survivors: D_k, b_k in place (each item owns its entry), new couplings into BT
+    const int nsurv = (nb - 1) / (2 * s) + 1;
+    for (int it = tid; it < nsurv * 36; it += nt) {
+      const int k = (it / 36) * 2 * s, e = it % 36;
+      const int il = k - s, ir = k + s;
+      const bool hl_ = il >= 0, hr = ir < nb, hn = hr && ir + s < nb;
+      if (e < 16) {
+        const int r = e / 4, c = e % 4;
+        double v = S.BD[k][e];
+        if (hl_)
+#pragma unroll
+          for (int q = 0; q < 4; q++) v = __fma_rn(-S.BB[il][q * 4 + r], S.BY[il][q * 4 + c], v);
+        if (hr)
+#pragma unroll
+          for (int q = 0; q < 4; q++) v = __fma_rn(-S.BB[k][r * 4 + q], S.BZ[ir][q * 4 + c], v);
+        S.BD[k][e] = v;
+      } else if (e < 32) {
+        const int r = (e - 16) / 4, c = (e - 16) % 4;
+        double u = 0.0;
+        if (hn)
+#pragma unroll
+          for (int q = 0; q < 4; q++) u = __fma_rn(-S.BB[k][r * 4 + q], S.BY[ir][q * 4 + c], u);
+        S.BT[k][r * 4 + c] = u;
+      } else {
+        const int r = e - 32;
+        double v = S.bb[k][r];
+        if (hl_)
+#pragma unroll
+          for (int q = 0; q < 4; q++) v = __fma_rn(-S.BB[il][q * 4 + r], S.by[il][q], v);
+        if (hr)
+#pragma unroll
+          for (int q = 0; q < 4; q++) v = __fma_rn(-S.BB[k][r * 4 + q], S.by[ir][q], v);
+        S.bb[k][r] = v;
+      }
+    }
+    __syncthreads();
+    for (int it = tid; it < nsurv * 16; it += nt) {
+      const int k = (it / 16) * 2 * s;
+      S.BB[k][it % 16] = S.BT[k][it % 16];
+    }
+    __syncthreads();
+  }
+  // block 0 alone (one half-warp), then back substitution
+  if (tid < 16) {
+    double *M = S.BD[0];
+    bool bad = false;
+#pragma unroll
+    for (int pi = 0; pi < 4; pi++) {
+      double dpiv = M[pi * 4 + pi];
+      bad = bad || !(dpiv != 0.0) || !isfinite(dpiv);
+      double r = 1.0 / dpiv;
+      int n = 3 - pi, k = 0, m = 0, q = tid;
+      for (int kk = 1; kk <= n; kk++) {
+        if (k == 0 && q < n - kk + 1) { k = kk; m = kk + q; }
+        else if (k == 0) q -= n - kk + 1;
+      }
+      double lk = 0.0;
+      if (k > 0) {
+        lk = M[pi * 4 + pi + k] * r;
+        M[(pi + k) * 4 + pi + m] = __fma_rn(-lk, M[pi * 4 + pi + m], M[(pi + k) * 4 + pi + m]);
+      }
+      __syncwarp(0xffffu);
+      if (k > 0 && m == k) M[pi * 4 + pi + k] = lk;
+      if (tid == 0) S.br[0][pi] = r;
+      __syncwarp(0xffffu);
+    }
+    if (tid == 0) {
+      if (bad) *flag = 1;
+      double v[4];
+      for (int q = 0; q < 4; q++) v[q] = S.bb[0][q];
+      solve4(M, S.br[0], v);
+      for (int q = 0; q < 4; q++) S.bx[0][q] = v[q];
+    }
+  }
+  __syncthreads();
+  if (*flag) return false;
+  for (s = s / 2; s >= 1; s /= 2) {
+    const int nelim = (nb - 1 - s) / (2 * s) + 1;
+    for (int it = tid; it < nelim * 4; it += nt) {
+      const int i = s + 2 * s * (it / 4), r = it % 4;
+      double v = S.by[i][r];
+#pragma unroll
+      for (int q = 0; q < 4; q++) v = __fma_rn(-S.BZ[i][r * 4 + q], S.bx[i - s][q], v);
+      if (i + s < nb)
+#pragma unroll
+        for (int q = 0; q < 4; q++) v = __fma_rn(-S.BY[i][r * 4 + q], S.bx[i + s][q], v);
+      S.bx[i][r] = v;
+    }
+    __syncthreads();
+  }
+  return true;
 }
 
 __global__ void __launch_bounds__(512) k_step(Params P, StepArgs A) {
@@ -386,83 +578,44 @@ __global__ void __launch_bounds__(512) k_step(Params P, StepArgs A) {
       for (int k = 0; k <= BW; k++) S.Ag[I][k] = band[k];
     }
     __syncthreads();
-    // the free system
-    for (int i = tid; i < nf; i += nt) {
-      if (clamped && i == 0) {
-        S.x[0] = -(tc * S.R[2] + ts * S.R[3]);
-        S.A[0][0] = tc * (tc * S.Ag[2][0] + ts * S.Ag[2][1]) +
-                    ts * (tc * S.Ag[2][1] + ts * S.Ag[3][0]);
-        for (int k = 1; k <= BW; k++) {
-          int J = k + 3;
-          double a2 = J - 2 <= BW ? S.Ag[2][J - 2] : 0.0;
-          S.A[0][k] = tc * a2 + ts * S.Ag[3][J - 3];
+    // the free system in node blocks: -R and D_j, Br_j from the band; a clamped plate's
+    // block 0 is sigma with three idle unknowns
+    const int nb = ne + 1;
+    for (int it = tid; it < nb * 36; it += nt) {
+      const int j = it / 36, e = it % 36;
+      if (e < 32) {
+        const int r = (e % 16) / 4, c = e % 4;
+        double v;
+        if (e < 16) {  // D_j
+          int lo = r < c ? r : c, off = r < c ? c - r : r - c;
+          v = S.Ag[4 * j + lo][off];
+          if (clamped && j == 0) v = r == c ? 1.0 : 0.0;
+          if (clamped && j == 0 && r == 0 && c == 0)
+            v = tc * (tc * S.Ag[2][0] + ts * S.Ag[2][1]) + ts * (tc * S.Ag[2][1] + ts * S.Ag[3][0]);
+          S.BD[j][r * 4 + c] = v;
+        } else {       // Br_j
+          v = j + 1 < nb ? S.Ag[4 * j + r][4 + c - r] : 0.0;
+          if (clamped && j == 0) v = r == 0 ? tc * S.Ag[2][2 + c] + ts * S.Ag[3][1 + c] : 0.0;
+          S.BB[j][r * 4 + c] = v;
         }
       } else {
-        int I = clamped ? i + 3 : i;
-        S.x[i] = -S.R[I];
-        for (int k = 0; k <= BW; k++) S.A[i][k] = S.Ag[I][k];
+        const int r = e - 32;
+        double v;
+        if (clamped)
+          v = j == 0 ? (r == 0 ? -(tc * S.R[2] + ts * S.R[3]) : 0.0) : -S.R[4 * j + r];
+        else
+          v = -S.R[4 * j + r];
+        S.bb[j][r] = v;
       }
     }
     __syncthreads();
-    // banded LDL^T (one warp: the 28 updates of a pivot in parallel), then the two triangular
-    // solves with the unknowns of the band held in the lanes' registers
-    if (tid < 32) {
-      const unsigned FULL = 0xffffffffu;
-      const int lane = tid;
-      int pk = 0, pm = 0;  // pair (k, m), 1 <= k <= m <= 7, for lanes 0..27
-      if (lane < 28) {
-        int q = lane;
-        pk = 1;
-        while (q >= 8 - pk) {
-          q -= 8 - pk;
-          pk++;
-        }
-        pm = pk + q;
+    {
+      bool okb = bcr_solve(S, nb, &S.flags[2]);
+      for (int i = tid; i < nf; i += nt) {
+        int I = clamped ? (i == 0 ? 0 : i + 3) : i;
+        S.x[i] = S.bx[I / 4][I % 4];
       }
-      bool bad = false;
-      for (int i = 0; i < nf; i++) {
-        double dpiv = S.A[i][0];
-        bad = !(dpiv != 0.0) || !isfinite(dpiv);
-        if (bad) break;  // uniform: every lane read the same pivot
-        double r = 1.0 / dpiv;
-        double lk = 0.0;
-        if (lane < 28 && i + pm < nf) {
-          lk = S.A[i][pk] * r;
-          S.A[i + pk][pm - pk] = __fma_rn(-lk, S.A[i][pm], S.A[i + pk][pm - pk]);
-        }
-        __syncwarp();
-        if (lane < 28 && pm == pk && i + pk < nf) S.A[i][pk] = lk;  // L(i + k, i)
-        if (lane == 0) S.rinv[i] = r;
-        __syncwarp();
-      }
-      if (!bad) {
-        // forward: lane k holds b[i + k]
-        double w = lane <= BW && lane < nf ? S.x[lane] : 0.0;
-        for (int i = 0; i < nf; i++) {
-          double bi = __shfl_sync(FULL, w, 0);
-          if (lane >= 1 && lane <= BW && i + lane < nf) w = __fma_rn(-S.A[i][lane], bi, w);
-          if (lane == 0) S.x[i] = bi;
-          double nx = __shfl_down_sync(FULL, w, 1);
-          w = lane < BW ? nx : (i + 1 + BW < nf ? S.x[i + 1 + BW] : 0.0);
-        }
-        __syncwarp();
-        for (int i = lane; i < nf; i += 32) S.x[i] = S.x[i] * S.rinv[i];
-        __syncwarp();
-        // backward: lane k holds x[i + k + 1]; the row's products summed pairwise
-        double xv = 0.0;
-        for (int i = nf - 1; i >= 0; i--) {
-          int k = lane + 1;
-          double pr = (k <= BW && i + k < nf) ? S.A[i][k] * xv : 0.0;
-          double t = pr + __shfl_down_sync(FULL, pr, 1);
-          double u = t + __shfl_down_sync(FULL, t, 2);
-          double sum = u + __shfl_down_sync(FULL, u, 4);
-          double xi = __shfl_sync(FULL, S.x[i] - sum, 0);
-          if (lane == 0) S.x[i] = xi;
-          double prev = __shfl_up_sync(FULL, xv, 1);
-          xv = lane == 0 ? xi : prev;
-        }
-      }
-      if (lane == 0) S.flags[1] = bad ? 1 : 0;
+      if (tid == 0) S.flags[1] = okb ? 0 : 1;
     }
     __syncthreads();
     if (S.flags[1]) break;
