@@ -77,3 +77,32 @@ def test_cylinder_pulse_both_schemes_strict(scheme):
     Q = g.get_state().cpu().numpy()
     Qo, _ = O.rk3(w["spec"], w["Q"], w["dt"], 10, w["X"], w["U"], w["dS"])
     np.testing.assert_array_equal(Q, Qo)
+
+
+def test_sphere_pulse_far_field_probes_fp32_vs_fp64():
+    """3D acoustic pulse scattered by a rigid sphere on the 512^3 set-up's domain at half its
+    resolution (256^3, h = 1/16, 20000 markers, TENO5, Re 1e4): the FP32 perturbation form and the
+    FP64 path over 480 SSP-RK3 steps (t = 5, the scattered pulse crosses the 1000 far-field probes
+    on r = 6), probe histories within 1e-3 relative RMS -- the workload's accuracy target."""
+    w = W.sphere_pulse_3d(n=256, state=False)
+    spec = w["spec"]
+    ib = _ib()
+    hist = {}
+    for prec in (W.FP64, W.FP32_PERTURB):
+        s = dataclasses.replace(spec, precision=prec)
+        g = ib.Grid(s, max_probes=w["probes"].shape[1])
+        g.set_state(W.gaussian_pulse_state_torch(s, (2.0, 0.0, 0.0)))
+        g.set_markers(w["X"], w["U"], w["dS"])
+        h = []
+        for _ in range(48):
+            g.rk3_step(w["dt"], 10)
+            h.append(g.probe(w["probes"]).cpu().numpy())
+        assert g.status() == 0
+        hist[prec] = np.array(h)
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    h64, h32 = hist[W.FP64], hist[W.FP32_PERTURB]
+    assert np.max(np.abs(h64)) > 1e-5  # the pulse reached the probes
+    rel = np.sqrt(np.sum((h32 - h64) ** 2) / np.sum(h64 ** 2))
+    assert rel <= 1e-3, rel
