@@ -43,7 +43,7 @@ FP32_FLOP_PER_CLK_PER_SM = 256  # 128 FP32 FMA lanes per SM per clock
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=512)
@@ -159,12 +159,18 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                 "-lms", "100", "-i", str(gpu_index)], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def wait_first(self, timeout=3.0):
+        """Block until the sampler has produced its first row (so the timed region is covered)."""
+        t0 = time.time()
+        while self.proc is not None and not self.rows and time.time() - t0 < timeout:
+            time.sleep(0.02)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -418,12 +424,21 @@ def run_ours(args, rank, world, local_rank):
         g.rk3_step(dt, 1)
     torch.cuda.synchronize()
     clocks = Clocks(local_rank)
+    clocks.wait_first()
     ms, prof = timed_steps(ib, g, dt, args.steps, barrier, profile=True)
     clk = clocks.stop()
     status = g.status()
     value, ms = job_throughput(ms, spec.cells * 3 * args.steps, dist, "cuda")
-    steps_done = args.warmup + args.steps
-    p_head = pressure(spec, g.get_state()) if (fp32 and args.compare) else None
+    # the FP32 and FP64 forms are compared after the same 8 steps from the initial state
+    steps_done = 8
+    p_head = None
+    if fp32 and args.compare:
+        gc, _, _, _, _ = make_grid(ib, args, prec)
+        gc.rk3_step(dt, steps_done)
+        p_head = pressure(spec, gc.get_state())
+        gc.close()
+        del gc
+        torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers: markers in, one step, probes out
     e2e = None
@@ -495,7 +510,7 @@ def run_ours(args, rank, world, local_rank):
             out_l[state] = {"value": spec.cells * 3 * k_l * world / (max_ranks(msl) * 1e-3),
                             "ms_per_step": msl / k_l,
                             "fallback_rate": 1.0 - used / max(seen, 1)}
-            if state == "pulse":
+            if state == "pulse" and steps_done - args.warmup - k_l >= 0:
                 for _ in range(steps_done - args.warmup - k_l):
                     gl.rk3_step(dt, 1)
                 p_l = pressure(spec, gl.get_state())
