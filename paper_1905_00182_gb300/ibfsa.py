@@ -594,6 +594,7 @@ class Plate:
         self.h = ibfsa_plate_create(self.desc, self.ws_ptr, self.ws_bytes,
                                     self.stream.cuda_stream)
         self._src = None
+        self._load = None
 
     def close(self):
         if self.h is not None:
@@ -621,12 +622,13 @@ class Plate:
         return e, v, t
 
     def step(self, dt, F=None):
+        """One step under marker forces F [2][n_markers] (None: no load)."""
         if F is None:
             ibfsa_plate_step(self.h, dt, 0)
         else:
             F = _dev_f64(F, self.device)
             ibfsa_plate_step(self.h, dt, F.data_ptr())
-            self._src = self._src + (F,) if self._src else (F,)
+            self._load = F  # the copy into the workspace is asynchronous
 
     def markers(self):
         import torch
