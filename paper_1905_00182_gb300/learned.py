@@ -1,7 +1,8 @@
 """Training of the learned reconstruction weights on stencils the solver itself generates.
 
-Data: the FP32 perturbation form runs the 2D acoustic-pulse / cylinder workload and the
-rotating-cylinder workload (at reduced resolution) and, at several times, ibfsa_mlp_sample draws
+Data: the FP32 perturbation form runs the 2D acoustic-pulse / cylinder workload, the
+rotating-cylinder workload and the flexible flapping plate (coupled to its FP64 plate; the last
+two at reduced resolution) and, at several times, ibfsa_mlp_sample draws
 random faces, directions, components and split-flux signs where the learned form would use the
 network (TENO5 keeps all three stencils, amplitude above the floor).  The target of each stencil
 is the face value of the ninth-order upwind-biased reconstruction of the same split flux along
@@ -45,6 +46,30 @@ def _sample_run(spec, Q, X, U, dS, dt, steps, every, per_snapshot, seed, out_S, 
     return fill
 
 
+def _sample_fsi_run(w, steps, every, per_snapshot, seed, out_S, out_T, fill):
+    import torch
+    g = ib.Grid(dataclasses.replace(w["spec"], precision=W.FP32_PERTURB, scheme=W.TENO5))
+    g.set_state(w["Q"])
+    P = ib.Plate(w["plate"])
+    P.set_state(w["e"], w["v"], 0.0)
+    X, U, dS = P.markers()
+    g.set_markers(X, U, dS)
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cap = out_S.shape[0]
+    for s in range(0, steps + 1, every):
+        if fill >= cap:
+            break
+        if s > 0:
+            ib.fsi_step(g, P, w["dt"], every)
+        n_max = min(per_snapshot, cap - fill)
+        ib.ibfsa_mlp_sample(g.h, n_max, seed * 1000003 + s, 8, out_S[fill:].data_ptr(),
+                            out_T[fill:].data_ptr(), count.data_ptr())
+        fill += min(int(count.item()), n_max)
+    g.close()
+    P.close()
+    return fill
+
+
 def generate_dataset(n_total: int, seed: int = 0):
     """n_total stencils [n, 5] and targets [n] (float32, on the GPU) from solver runs."""
     import torch
@@ -58,6 +83,11 @@ def generate_dataset(n_total: int, seed: int = 0):
         target = fill + int(half * frac)
         fill = _sample_run(w["spec"], w["Q"], w["X"], w["U"], w["dS"], w["dt"], 400, 20,
                            max(1, (target - fill) // 20), seed + n, S[:target], T[:target], fill)
+    # flexible plate flapping in a stream (1024 x 512 on the 4096 x 2048 workload's domain)
+    w = W.flapping_plate_2d(n=(1024, 512))
+    target = fill + (n_total - fill) // 2
+    fill = _sample_fsi_run(w, 600, 30, max(1, (target - fill) // 20), seed + 11, S[:target],
+                           T[:target], fill)
     # rotating cylinder in a Mach 0.2 stream (512^2 on [-40,40]^2 is too coarse for the body;
     # a [-10,10]^2 window keeps the wake and the spinning surface)
     w = W.rotating_cylinder_2d(n=512, markers=256)
