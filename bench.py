@@ -56,6 +56,10 @@ def parse():
                     help="skip the FP64 comparison run of the fp32 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--form", default="teno", choices=["teno", "learned"],
+                    help="learned: the timed run uses the learned weights (FP32 form)")
+    ap.add_argument("--state", default="pulse", choices=["pulse", "stress"],
+                    help="initial state of the timed run")
     ap.add_argument("--workload", default="sphere", choices=["sphere", "fsi"],
                     help="sphere: the 512^3 headline; fsi: only the coupled flapping-plate step "
                          "(4096x2048), e.g. for profiling")
@@ -82,8 +86,13 @@ def config_dict(args, n):
     else:
         form = f"FP64 {'strict' if args.strict else 'fused-multiply-add'}"
         prec = "fp64-strict" if args.strict else "fp64"
+    if getattr(args, "form", "teno") == "learned":
+        form += ", learned reconstruction weights behind the TENO5 guard"
+    state = getattr(args, "state", "pulse")
+    what = ("3D acoustic pulse scattered by a rigid sphere" if state == "pulse" else
+            "3D stress state (smooth random modes everywhere + 10 % contact step) around a rigid sphere")
     return {
-        "workload": f"3D acoustic pulse scattered by a rigid sphere, {n}^3 on [-8,8]^3, "
+        "workload": f"{what}, {n}^3 on [-8,8]^3, "
                     f"{args.scheme.upper()}, {args.markers} markers, Re 1e4, SSP-RK3, {form}",
         "grid": [n, n, n], "scheme": args.scheme, "markers": args.markers,
         "precision": prec,
@@ -419,7 +428,10 @@ def run_ours(args, rank, world, local_rank):
 
     fp32 = args.precision == "fp32"
     prec = W.FP32_PERTURB if fp32 else W.FP64
-    g, spec, dt, (X, U, dS), probes = make_grid(ib, args, prec, strict=args.strict and not fp32)
+    net = learned_weights(ib) if (fp32 and args.form == "learned") else None
+    g, spec, dt, (X, U, dS), probes = make_grid(ib, args, prec, strict=args.strict and not fp32,
+                                                scheme=W.MLP_TENO5 if net is not None else None,
+                                                state=args.state, mlp=net)
     for _ in range(args.warmup):
         g.rk3_step(dt, 1)
     torch.cuda.synchronize()

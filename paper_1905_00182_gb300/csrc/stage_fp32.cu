@@ -204,8 +204,8 @@ __device__ __forceinline__ float teno5_fast(const Plan &tw, float a, float b, fl
 // test takes the full scalar TENO5.  Returns h+ + h-.
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-__device__ __forceinline__ float teno5_pm(const Plan &tw, float2 a, float2 b, float2 c,
-                                          float2 d, float2 e) {
+__device__ __forceinline__ float teno5_pm_k(const Plan &tw, float2 a, float2 b, float2 c,
+                                            float2 d, float2 e, bool &kx, bool &ky) {
   float2 t0 = __fadd2_rn(__ffma2_rn(f2(-2.f), b, a), c);
   float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.f), c, b), d);
   float2 t2 = __fadd2_rn(__ffma2_rn(f2(-2.f), d, c), e);
@@ -217,8 +217,8 @@ __device__ __forceinline__ float teno5_pm(const Plan &tw, float2 a, float2 b, fl
   float2 b1 = __ffma2_rn(__fmul2_rn(k13, t1), t1, __fmul2_rn(__fmul2_rn(q, u1), u1));
   float2 b2 = __ffma2_rn(__fmul2_rn(k13, t2), t2, __fmul2_rn(__fmul2_rn(q, u2), u2));
   float2 tau = __ffma2_rn(f2(-1.f), b2, b0);
-  bool kx = fabsf(tau.x) <= 4.f * (fminf(b0.x, fminf(b1.x, b2.x)) + 1e-30f);
-  bool ky = fabsf(tau.y) <= 4.f * (fminf(b0.y, fminf(b1.y, b2.y)) + 1e-30f);
+  kx = fabsf(tau.x) <= 4.f * (fminf(b0.x, fminf(b1.x, b2.x)) + 1e-30f);
+  ky = fabsf(tau.y) <= 4.f * (fminf(b0.y, fminf(b1.y, b2.y)) + 1e-30f);
   float2 lin = __fmul2_rn(f2(2.f / 60.f), a);
   lin = __ffma2_rn(f2(-13.f / 60.f), b, lin);
   lin = __ffma2_rn(f2(47.f / 60.f), c, lin);
@@ -228,6 +228,12 @@ __device__ __forceinline__ float teno5_pm(const Plan &tw, float2 a, float2 b, fl
   float hx = kx ? lin.x : teno5(tw, a.x, b.x, c.x, d.x, e.x);
   float hy = ky ? lin.y : teno5(tw, a.y, b.y, c.y, d.y, e.y);
   return hx + hy;
+}
+
+__device__ __forceinline__ float teno5_pm(const Plan &tw, float2 a, float2 b, float2 c,
+                                          float2 d, float2 e) {
+  bool kx, ky;
+  return teno5_pm_k(tw, a, b, c, d, e, kx, ky);
 }
 
 template <int SCHEME>
@@ -467,24 +473,58 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
     unsigned char *img = reinterpret_cast<unsigned char *>(smf + 2 * NV * T::ROWS * T::LEN);
     unsigned used = 0, seen = 0;
 #pragma unroll
-    for (int ps = 0; ps < MAXP; ps++) {
+    // Rolled loop over (pass, component) with one call site of the warp-wide network
+    // (unrolled, the network's code was copied 2 x NV x MAXP times and the kernel ran out of the
+    // instruction cache).  Both split-flux sides first take packed TENO5; where no lane of the
+    // warp would use the network (TENO5 keeping all three stencils and an amplitude above the
+    // floor), that is the result, else both sides go through the network's reconstruction.
+#pragma unroll
+    for (int ps = 0; ps < MAXP; ps++)
+#pragma unroll
+      for (int c = 0; c < NV; c++) Fh[ps][c] = 0.f;
+#pragma unroll 1
+    for (int it = 0; it < MAXP * NV; it++) {
+      const int ps = it / NV, c = it % NV;
       int e = threadIdx.x + ps * THREADS;
       int row, fi;
       if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
       else { row = e % T::ROWS; fi = e / T::ROWS; }
       bool valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
       if (!valid) { row = 0; fi = 0; }  // in-bounds reads; results discarded
-      int b = fi + 2;
+      const int b = fi + 2;
+      const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
+      const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
+      bool kx, ky;
+      float hlin = teno5_pm_k(p, make_float2(fp[b - 2], fm[b + 3]),
+                              make_float2(fp[b - 1], fm[b + 2]), make_float2(fp[b], fm[b + 1]),
+                              make_float2(fp[b + 1], fm[b]), make_float2(fp[b + 2], fm[b - 1]),
+                              kx, ky);
+      // eligibility exactly as recon_mlp decides it
+      bool el[2];
 #pragma unroll
-      for (int c = 0; c < NV; c++) {
-        const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
-        const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
-        float hp = recon_mlp(p, img, valid, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2],
-                             used, seen);
-        float hm = recon_mlp(p, img, valid, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1],
-                             used, seen);
-        Fh[ps][c] = hp + hm;
+      for (int sgn = 0; sgn < 2; sgn++) {
+        const float *f = sgn ? fm : fp;
+        const int o = sgn ? b + 3 : b - 2, st = sgn ? -1 : 1;
+        float v0 = f[o], v1 = f[o + st], v2 = f[o + 2 * st], v3 = f[o + 3 * st], v4 = f[o + 4 * st];
+        float amp = fmaxf(fmaxf(fabsf(v0 - v2), fabsf(v1 - v2)), fmaxf(fabsf(v3 - v2), fabsf(v4 - v2)));
+        bool kept = sgn ? ky : kx;
+        if (!kept && valid) kept = teno_mask(candidates(v0, v1, v2, v3, v4)) == 7;
+        el[sgn] = valid && kept && amp > p.mlp_floor;
       }
+      if (__ballot_sync(0xffffffffu, el[0] || el[1]) == 0u) {
+        Fh[ps][c] = hlin;
+        seen += 2 * __popc(__ballot_sync(0xffffffffu, valid));
+        continue;
+      }
+      float h = 0.f;
+#pragma unroll 1
+      for (int sgn = 0; sgn < 2; sgn++) {
+        const float *f = sgn ? fm : fp;
+        const int o = sgn ? b + 3 : b - 2, st = sgn ? -1 : 1;
+        h += recon_mlp(p, img, valid, f[o], f[o + st], f[o + 2 * st], f[o + 3 * st],
+                       f[o + 4 * st], used, seen);
+      }
+      Fh[ps][c] = h;
     }
     if ((threadIdx.x & 31) == 0 && seen) {
       atomicAdd(&p.mlp_counts[0], (unsigned long long)used);
