@@ -1063,10 +1063,7 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
     }
   };
   // gradients g[i][j] = du_i/dx_j at staged position (sx, sy) of plane c
-  auto grads = [&](int c, int sx, int sy, float g[3][3], float u[3]) {
-    const float *pl[5];
-#pragma unroll
-    for (int o = 0; o < 5; o++) pl[o] = ring + ((c - 2 + o + 8) % 5) * PLANE;
+  auto grads = [&](const float *const pl[5], int sx, int sy, float g[3][3], float u[3]) {
     int e = sy * SX + sx;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
@@ -1121,10 +1118,14 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
   fetch(zs + 1);
   __syncthreads();
   for (int c = zs - 2; c < ze + 2; c++) {
+    // ring slots of planes c-2 .. c+2, once per plane
+    const float *pl[5];
+#pragma unroll
+    for (int o = 0; o < 5; o++) pl[o] = ring + ((c + 6 + o) % 5) * PLANE;
     // own cell: all three fluxes; halo points: F_v,x (x offsets -2,-1,32,33) or F_v,y
     {
       float g[3][3], u[3], f[4];
-      grads(c, tx + 4, ty + 4, g, u);
+      grads(pl, tx + 4, ty + 4, g, u);
       vflux(0, g, u, f);
 #pragma unroll
       for (int k = 0; k < 4; k++) fx[(k * TY + ty) * PX + tx + 2] = f[k];
@@ -1144,13 +1145,13 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
       float g[3][3], u[3], f[4];
       if (e < 4 * TY) {  // x-halo point
         int r = e / 4, h = e % 4, px = h < 2 ? h : TX + h;  // 0,1,TX+2,TX+3
-        grads(c, px + 2, r + 4, g, u);
+        grads(pl, px + 2, r + 4, g, u);
         vflux(0, g, u, f);
 #pragma unroll
         for (int k = 0; k < 4; k++) fx[(k * TY + r) * PX + px] = f[k];
       } else {           // y-halo point
         int e2 = e - 4 * TY, col = e2 % TX, h = e2 / TX, py = h < 2 ? h : TY + h;
-        grads(c, col + 4, py + 2, g, u);
+        grads(pl, col + 4, py + 2, g, u);
         vflux(1, g, u, f);
 #pragma unroll
         for (int k = 0; k < 4; k++) fy[(k * PY + py) * TX + col] = f[k];
