@@ -321,6 +321,31 @@ def rotating_cylinder_2d(n: int = 2048, markers: int = 1024, scheme: int = WENO5
     return dict(spec=spec, Q=Q, X=X, U=U, dS=dS, dt=dt, steps=20000, probes=probes)
 
 
+def stationary_cylinder_2d(n: int = 1024, L: float = 20.0, scheme: int = TENO5,
+                           precision: int = FP32_PERTURB):
+    """Flow past a stationary cylinder (Sec. 3.2): Re = rho U0 D / mu = 150, M = U0 / c = 0.2,
+    D = 1 at the origin, uniform grid on [-L, L]^2 (D/h = n / 2L), free-stream ghosts and a
+    20-cell sponge, markers every quarter cell.  The paper starts the asymmetric vortex street
+    with an initial velocity perturbation in the near wake: here a transverse velocity bump of
+    0.1 U0 exp(-((x - 1.5)^2 + y^2) / 0.5)."""
+    g = 1.4
+    U0 = 0.2
+    h = 2.0 * L / n
+    markers = 4 * int(math.pi / h)
+    spec = GridSpec(dim=2, n=(n, n, 1), lo=(-L, -L, 0.0), hi=(L, L, 1.0), gamma=g,
+                    Re=150.0 / U0, qinf=freestream(2, g, vel=(U0, 0.0, 0.0)), scheme=scheme,
+                    precision=precision, bc=((1, 1), (1, 1), (0, 0)), sponge_cells=20,
+                    max_markers=markers)
+    dt = 0.5 / ((1.0 + U0) / h + 1.0 / h)
+    spec.alpha_pen, spec.beta_pen = penalty_defaults(h, dt)
+    spec.sponge_sigma = 0.5 * (1.0 + U0) / h
+    X, Y, _ = mesh(spec)
+    v = 0.1 * U0 * np.exp(-((X - 1.5) ** 2 + Y ** 2) / 0.5)
+    Q = conservative(spec, np.ones_like(X), [np.full(X.shape, U0), v], np.full(X.shape, 1.0 / g))
+    Xm, Um, dS = circle_markers(markers, 0.5, seed=0)
+    return dict(spec=spec, Q=Q, X=Xm, U=Um, dS=dS, dt=dt, U0=U0)
+
+
 def _sphere_setup(n, markers, Re, scheme, precision, probes, L):
     g = 1.4
     spec = GridSpec(dim=3, n=(n, n, n), lo=(-L, -L, -L), hi=(L, L, L), gamma=g, Re=Re,

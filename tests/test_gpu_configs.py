@@ -106,3 +106,40 @@ def test_sphere_pulse_far_field_probes_fp32_vs_fp64():
     assert np.max(np.abs(h64)) > 1e-5  # the pulse reached the probes
     rel = np.sqrt(np.sum((h32 - h64) ** 2) / np.sum(h64 ** 2))
     assert rel <= 1e-3, rel
+
+
+def test_stationary_cylinder_forces_match_the_paper():
+    """Sec. 3.2 (flow past a stationary cylinder, Re 150, M 0.2): the paper prints a mean drag
+    coefficient of 1.40, a lift amplitude of 0.525 and a Strouhal number of about 0.178 (on a
+    stretched mesh with D/40 near the body).  The FP32 form on a uniform 1024^2 grid of
+    [-20, 20]^2 (D/h = 25.6), coefficients from the penalty forces (ibfsa_body_force) every 0.1
+    D/U over t U/D = 70..100 after the vortex street has formed: within 4 % (drag), 6 % (lift)
+    and 5 % (Strouhal) of the paper's values (measured: 1.43, 0.51, 0.173)."""
+    w = W.stationary_cylinder_2d()
+    ib = _ib()
+    g = ib.Grid(w["spec"])
+    g.set_state(w["Q"])
+    g.set_markers(w["X"], w["U"], w["dS"])
+    U0, dt = w["U0"], w["dt"]
+    q = 0.5 * U0 * U0
+    chunk = int(round(0.1 / U0 / dt))
+    ts, cd, cl = [], [], []
+    t = 0.0
+    while t < 100.0:
+        g.rk3_step(dt, chunk)
+        t += chunk * dt * U0
+        f, _ = ib.ibfsa_body_force(g.h)
+        ts.append(t)
+        cd.append(f[0] / q)
+        cl.append(f[1] / q)
+    assert g.status() == 0
+    ts, cd, cl = map(np.array, (ts, cd, cl))
+    sel = ts >= 70.0
+    c = cl[sel] - cl[sel].mean()
+    up = [ts[sel][i] for i in range(len(c) - 1) if c[i] < 0.0 <= c[i + 1]]
+    St = (len(up) - 1) / (up[-1] - up[0])
+    CD, CL = cd[sel].mean(), 0.5 * (cl[sel].max() - cl[sel].min())
+    print(f"C_D {CD:.4f} (paper 1.40), C_L amplitude {CL:.4f} (0.525), St {St:.4f} (0.178)")
+    assert abs(CD / 1.40 - 1.0) <= 0.04
+    assert abs(CL / 0.525 - 1.0) <= 0.06
+    assert abs(St / 0.178 - 1.0) <= 0.05
