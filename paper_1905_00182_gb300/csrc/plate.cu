@@ -3,16 +3,19 @@
 // fluid grid through the penalty forces (Eq. 7-9).
 //
 // Compiled with --fmad=false and host -ffp-contract=off: every FP64 operation is rounded on its
-// own, in the order written, except the explicit fused multiply-adds (__fma_rn) of the dot
-// products, the elimination and the forward substitution -- so a sequential evaluation of the
-// same formulas with the same fused operations reproduces the results bit for bit.  On GB300
-// a warp's FP64 instruction occupies its SM quarter's FP64 pipe for tens of cycles however
-// few lanes are active, so the serial parts are written to issue as few FP64 instructions as
-// possible (fused operations, one reciprocal per pivot, products of a row in parallel lanes).  The structure solve is tiny (4 (n_el + 1) unknowns, half-bandwidth 7) and
-// sequential by nature (Newton, banded factorisation), so it runs in ONE thread block: element
-// residuals and Jacobians one thread per (element, row), assembly one thread per coordinate, the
-// LDL^T factorisation one warp (the 28 updates of a pivot in parallel), all state in shared
-// memory; the host never waits on it.
+// own, in the order written, except the explicit fused multiply-adds (__fma_rn) of the element
+// dot products and of the cyclic reduction -- so a sequential evaluation of the same formulas
+// with the same fused operations reproduces the results bit for bit.
+//
+// The structure solve is tiny (4 (n_el + 1) unknowns) and sequential by nature (Newton), so it
+// runs in ONE thread block with all state in shared memory, and the host never waits on it:
+// Gauss-point factors one thread per (element, point), element residual rows and Jacobian rows
+// one thread per (element, row), assembly one thread per coordinate, and the Newton system --
+// block tridiagonal in the nodes -- by block cyclic reduction: at each of ~log2(n_el) levels the
+// eliminated 4 x 4 blocks are factorised by half-warps in parallel, so the dependent chain is a
+// few levels long instead of one pivot per unknown.  On GB300 a warp's FP64 instruction holds its
+// SM quarter's narrow FP64 pipe for tens of cycles however few lanes are active, which is what
+// makes the length of that chain, not the amount of work, the cost.
 //
 // Discretisation (Eq. 1 read as the Euler-Lagrange equation of
 // 1/2 int rho_s |r_t|^2 ds - 1/2 int [K_S (|r_s| - 1)^2 + K_B |r_ss|^2] ds):
