@@ -415,3 +415,17 @@ def fsi_last_load(ps):
     if rc != ORC_OK:
         raise RuntimeError("no coupled step ran")
     return F
+
+
+def probe_stats(history):
+    """Time statistics of probe signals, Sec. 3.2: for each probe (columns of history [T][np]),
+    the time mean of dp and the root mean square of dp~ = dp - mean, by the definition (two
+    passes over the samples, population form).  A probe with no samples gives 0 and 0."""
+    h = np.asarray(history, dtype=np.float64)
+    if h.ndim != 2:
+        raise ValueError("history must be [T][np]")
+    if h.shape[0] == 0:
+        return np.zeros(h.shape[1]), np.zeros(h.shape[1])
+    mean = h.sum(axis=0) / h.shape[0]
+    dev = h - mean
+    return mean, np.sqrt((dev * dev).sum(axis=0) / h.shape[0])

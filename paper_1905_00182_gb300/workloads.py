@@ -267,6 +267,14 @@ def ring_probes(n: int, radius: float, center=(0.0, 0.0)):
     return np.stack([center[0] + radius * np.cos(th), center[1] + radius * np.sin(th)])
 
 
+def doppler_ring_probes(n: int, radius: float, mach: float, center=(0.0, 0.0)):
+    """Probes at r = radius (1 - M cos theta), theta = 2 pi k / n: the ring of Sec. 3.3, drawn
+    in by the convective Doppler factor downstream (theta = 0) of a stream along +x."""
+    th = 2.0 * math.pi * np.arange(n) / n
+    r = radius * (1.0 - mach * np.cos(th))
+    return np.stack([center[0] + r * np.cos(th), center[1] + r * np.sin(th)])
+
+
 def penalty_defaults(h: float, dt: float, kappa: float = 0.5, rho: float = 1.0):
     """Penalty constants of Eq. 7 (the paper gives none): a dense marker sheet feeds back a slip
     fraction of about dt * beta * (3/8) / (rho h) per stage, so beta = kappa rho h / ((3/8) dt)
