@@ -160,6 +160,19 @@ int ibfsa_max_wavespeed(ibfsa_grid *g, double *host_alpha);
  * (device or host) into out [np] (device or host; synchronises when out is host memory). */
 int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out);
 
+/* Time statistics of probe signals (Sec. 3.2): the fluctuating pressure about its time mean,
+ * dp~ = dp - mean_t(dp), and the root mean square of dp~ that Sec. 3.3 and 4 plot on rings of
+ * probes.  ibfsa_probe_accumulate samples dp at np points exactly as ibfsa_probe does (out, device
+ * or host, may be NULL) and folds the samples into acc, caller-owned device memory of 3*np
+ * doubles laid out [count | mean | M2] (Welford's running update, accurate when the mean
+ * dominates the fluctuation), zero-filled by the caller before the first sample.
+ * ibfsa_probe_stats writes, per probe, the time mean of dp and the RMS of dp~ (population form,
+ * sqrt(M2 / count); both 0 for a probe without samples) to mean and rms [np], device memory.
+ * FP64, each operation rounded on its own; stream-ordered on the grid's stream.  Host pointers
+ * for acc, mean or rms: IBFSA_ERR_ARG. */
+int ibfsa_probe_accumulate(ibfsa_grid *g, int np, const double *xp, double *out, double *acc);
+int ibfsa_probe_stats(ibfsa_grid *g, int np, const double *acc, double *mean, double *rms);
+
 /* Force on the body and power delivered to it, from the penalty forces of the last evaluated
  * stage (Eq. 7): host_force[d] = sum_k F_k,d dS_k (d < dim), *host_power = sum_k (F_k . U_k) dS_k
  * (may be NULL).  The force the body exerts on the fluid is the opposite (Eq. 9); the drag,

@@ -27,6 +27,7 @@ UNITS = {
     "stage_fp32.cu": ["--fmad=true"],
     "mlp.cu": ["--fmad=true"],
     "noalloc.cu": [],
+    "stats.cu": [],
     "plate.cu": ["--fmad=false", "-Xcompiler", "-ffp-contract=off"],
 }
 

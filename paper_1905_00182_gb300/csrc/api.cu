@@ -560,6 +560,38 @@ int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out) {
   return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_probe");
 }
 
+int ibfsa_probe_accumulate(ibfsa_grid *g, int np, const double *xp, double *out, double *acc) {
+  if (!g || (np > 0 && (!xp || !acc))) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  if (np < 0 || np > G.max_probes)
+    return fail(IBFSA_ERR_ARG, "probe count %d outside [0, %d]", np, G.max_probes);
+  if (np == 0) return IBFSA_OK;
+  if (is_host_pointer(acc)) return fail(IBFSA_ERR_ARG, "acc must be device memory");
+  cudaError_t e = cudaMemcpyAsync(G.probe_xp, xp, sizeof(double) * G.p.dim * np,
+                                  cudaMemcpyDefault, G.stream);
+  if (e == cudaSuccess)
+    e = G.d.precision == IBFSA_FP32_PERTURB
+            ? fp32_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
+        : G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
+                        : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof);
+  if (e == cudaSuccess) e = probe_fold(np, G.probe_out, acc, G.stream);
+  if (e == cudaSuccess && out)
+    e = cudaMemcpyAsync(out, G.probe_out, sizeof(double) * np, cudaMemcpyDefault, G.stream);
+  if (e == cudaSuccess && out && is_host_pointer(out)) e = cudaStreamSynchronize(G.stream);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_probe_accumulate");
+}
+
+int ibfsa_probe_stats(ibfsa_grid *g, int np, const double *acc, double *mean, double *rms) {
+  if (!g || (np > 0 && (!acc || !mean || !rms))) return fail(IBFSA_ERR_ARG, "NULL argument");
+  Grid &G = g->g;
+  if (np < 0) return fail(IBFSA_ERR_ARG, "negative probe count %d", np);
+  if (np == 0) return IBFSA_OK;
+  if (is_host_pointer(acc) || is_host_pointer(mean) || is_host_pointer(rms))
+    return fail(IBFSA_ERR_ARG, "acc, mean and rms must be device memory");
+  cudaError_t e = probe_moments(np, acc, mean, rms, G.stream);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_probe_stats");
+}
+
 int ibfsa_set_mlp(ibfsa_grid *g, const void *d_state) {
   if (!g || !d_state) return fail(IBFSA_ERR_ARG, "NULL argument");
   Grid &G = g->g;

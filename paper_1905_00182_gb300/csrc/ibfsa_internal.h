@@ -156,6 +156,9 @@ cudaError_t strict_probe(const Plan &p, const double *Q, int np, const double *x
                          cudaStream_t st, Prof *pr);
 cudaError_t fast_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,
                        cudaStream_t st, Prof *pr);
+// Time statistics of probe signals (stats.cu): acc is [count | mean | M2] per probe.
+cudaError_t probe_fold(int np, const double *dp, double *acc, cudaStream_t st);
+cudaError_t probe_moments(int np, const double *acc, double *mean, double *rms, cudaStream_t st);
 
 // One stage (or right-hand side) of a grid in its arithmetic form (api.cu).
 cudaError_t grid_stage(Grid *G, const StageArgs &s);

@@ -37,7 +37,8 @@ EXPORTS = (
     "ibfsa_workspace_bytes", "ibfsa_create_grid", "ibfsa_destroy_grid", "ibfsa_set_state",
     "ibfsa_get_state", "ibfsa_set_markers", "ibfsa_get_marker_forces",
     "ibfsa_get_penalty_integral", "ibfsa_set_penalty_integral", "ibfsa_rhs", "ibfsa_rk3_step",
-    "ibfsa_max_wavespeed", "ibfsa_probe", "ibfsa_get_status", "ibfsa_last_error",
+    "ibfsa_max_wavespeed", "ibfsa_probe", "ibfsa_probe_accumulate", "ibfsa_probe_stats",
+    "ibfsa_get_status", "ibfsa_last_error",
     "ibfsa_profile_enable", "ibfsa_profile_read", "ibfsa_rhs_noalloc",
     "ibfsa_mlp_state_bytes", "ibfsa_mlp_init", "ibfsa_mlp_train_step", "ibfsa_mlp_read",
     "ibfsa_mlp_eval", "ibfsa_set_mlp", "ibfsa_mlp_stats", "ibfsa_mlp_sample",
@@ -126,6 +127,8 @@ def lib():
         L.ibfsa_rk3_step.argtypes = [_P, ctypes.c_double, ctypes.c_int]
         L.ibfsa_max_wavespeed.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
         L.ibfsa_probe.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.ibfsa_probe_accumulate.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+        L.ibfsa_probe_stats.argtypes = [_P, ctypes.c_int, _P, _P, _P]
         L.ibfsa_get_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int)]
         L.ibfsa_last_error.restype = ctypes.c_char_p
         L.ibfsa_profile_enable.argtypes = [_P, ctypes.c_int]
@@ -250,6 +253,14 @@ def ibfsa_max_wavespeed(g):
 
 def ibfsa_probe(g, np_: int, xp: int, out: int):
     _check(lib().ibfsa_probe(g, int(np_), _P(xp), _P(out)))
+
+
+def ibfsa_probe_accumulate(g, np_: int, xp: int, out: int, acc: int):
+    _check(lib().ibfsa_probe_accumulate(g, int(np_), _P(xp), _P(out), _P(acc)))
+
+
+def ibfsa_probe_stats(g, np_: int, acc: int, mean: int, rms: int):
+    _check(lib().ibfsa_probe_stats(g, int(np_), _P(acc), _P(mean), _P(rms)))
 
 
 def ibfsa_get_status(g) -> int:
@@ -566,6 +577,28 @@ class Grid:
         out = torch.empty(xp.shape[1], dtype=torch.float64, device=self.device)
         ibfsa_probe(self.h, xp.shape[1], xp.data_ptr(), out.data_ptr())
         return out
+
+    def probe_accumulate(self, xp, acc):
+        """Samples dp at xp [dim][np] into a fresh tensor and folds it into acc, a zero-filled
+        float64 device tensor of 3*np entries (count, running mean, running M2)."""
+        import torch
+        xp = _dev_f64(xp, self.device)
+        npr = xp.shape[1]
+        if acc.dtype != torch.float64 or acc.device != self.device or acc.numel() != 3 * npr \
+                or not acc.is_contiguous():
+            raise ValueError("acc must be a contiguous float64 tensor of 3*np entries on the grid's device")
+        out = torch.empty(npr, dtype=torch.float64, device=self.device)
+        ibfsa_probe_accumulate(self.h, npr, xp.data_ptr(), out.data_ptr(), acc.data_ptr())
+        return out
+
+    def probe_stats(self, acc):
+        """(time mean of dp, RMS of dp about that mean) per probe from an accumulator."""
+        import torch
+        npr = acc.numel() // 3
+        mean = torch.empty(npr, dtype=torch.float64, device=self.device)
+        rms = torch.empty_like(mean)
+        ibfsa_probe_stats(self.h, npr, acc.data_ptr(), mean.data_ptr(), rms.data_ptr())
+        return mean, rms
 
     def status(self) -> int:
         return ibfsa_get_status(self.h)
