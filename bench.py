@@ -256,6 +256,36 @@ def cpu_baseline(args):
                       f"{el:.1f} s"}
 
 
+def _oracle_pool_init():
+    from oracle import oracle as O
+    O.build()
+
+
+def _oracle_pool_task(job):
+    return oracle_sample(*job)
+
+
+def cpu_baseline_all_cores(args):
+    """The same oracle sample run concurrently in one process per host core (spawned, so no
+    GPU state is inherited): the oracle as it stands, each process single-threaded, the way the
+    paper's CPU code spreads one problem over a node's cores."""
+    import multiprocessing as mp
+    P = os.cpu_count() or 1
+    n_s, steps = 96, 2
+    with mp.get_context("spawn").Pool(P, initializer=_oracle_pool_init) as pool:
+        pool.map(_oracle_pool_task, [(48, 1, args.scheme, 64)] * P, chunksize=1)  # all started
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_pool_task, [(n_s, steps, args.scheme, args.markers)] * P,
+                       chunksize=1)
+        wall = time.perf_counter() - t0
+    cells = n_s ** 3
+    value = P * cells * 3 * steps / wall
+    return {"value": value, "unit": "cell-updates/s", "cores": P, "kind": "oracle",
+            "sample": f"{P} concurrent single-threaded processes, each the single-thread "
+                      f"sample ({n_s}^3, {steps} SSP-RK3 steps); {wall:.1f} s wall, slowest "
+                      f"process {max(r[1] for r in res):.1f} s"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -614,6 +644,7 @@ def run_ours(args, rank, world, local_rank):
         out["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args)
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args)
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -586,7 +586,8 @@ class Grid:
         npr = xp.shape[1]
         if acc.dtype != torch.float64 or acc.device != self.device or acc.numel() != 3 * npr \
                 or not acc.is_contiguous():
-            raise ValueError("acc must be a contiguous float64 tensor of 3*np entries on the grid's device")
+            raise ValueError("acc must be a contiguous float64 tensor of 3*np entries on the "
+                             "grid's device")
         out = torch.empty(npr, dtype=torch.float64, device=self.device)
         ibfsa_probe_accumulate(self.h, npr, xp.data_ptr(), out.data_ptr(), acc.data_ptr())
         return out
