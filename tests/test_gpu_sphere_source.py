@@ -1,0 +1,82 @@
+"""Sec. 3.6 on the GPU: the periodic Gaussian source of Eq. 16 (the paper's A, B, omega and
+centre, in units of the sphere radius R = 0.5) beside a rigid sphere, against the exact
+time-harmonic linear-acoustics solution of tests/sphere_scattering.py.
+
+The FP32 perturbation form (as bench.py times it; FP32 against FP64 is covered by the parity
+tests) on [-8, 8]^3 with 20000 markers, inviscid so that the comparison is with inviscid
+acoustics, at R/h = 8, 12 and 16 (n = 256, 384, 512).  Probes on the lines of the paper's
+figures: y = z = 0 (through the sphere and the source) and x = z = 0, at 0.75 <= r <= 2.5.  The
+settled complex amplitude P at each probe is the least-squares fit of a cos(wt) + b sin(wt) + c
+to the pressure fluctuation over t in [4, 5] (two periods, after the last retarded arrival at
+every probe and long before any wave returns from the boundary at distance 7), P = a + i b."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1905_00182_gb300 import workloads as W
+from tests import sphere_scattering as S
+
+torch = pytest.importorskip("torch")
+pytest.importorskip("scipy.special")
+pytestmark = pytest.mark.gpu
+
+R = 0.5
+
+
+def _probes():
+    s = np.round(np.arange(0.75, 2.5001, 0.05), 10)
+    xl = np.concatenate([-s[::-1], s])
+    x_line = np.stack([xl, np.zeros_like(xl), np.zeros_like(xl)])
+    y_line = np.stack([np.zeros_like(s), s, np.zeros_like(s)])
+    return np.concatenate([x_line, y_line], axis=1)
+
+
+def _settled_amplitude(ib, n, xp, t0=4.0, t1=5.0, sample=0.0105):
+    w = W.sphere_source_3d(n=n, markers=20000, Re=0.0, precision=W.FP32_PERTURB, probes=1)
+    spec, dt = w["spec"], w["dt"]
+    g = ib.Grid(spec, max_probes=xp.shape[1])
+    Q = torch.empty(spec.shape(), dtype=torch.float64, device=g.device)
+    for c in range(spec.nv):
+        Q[c].fill_(spec.qinf[c])
+    g.set_state(Q)
+    del Q
+    g.set_markers(w["X"], w["U"], w["dS"])
+    every = max(1, int(round(sample / dt)))
+    g.rk3_step(dt, int(math.ceil(t0 / dt)))
+    ts, hist = [], []
+    while g.time() < t1:
+        g.rk3_step(dt, every)
+        ts.append(g.time())
+        hist.append(g.probe(xp).cpu().numpy())
+    assert g.status() == 0
+    om = spec.src_omega
+    ts = np.array(ts)
+    M = np.stack([np.cos(om * ts), np.sin(om * ts), np.ones_like(ts)], axis=1)
+    coef, *_ = np.linalg.lstsq(M, np.array(hist), rcond=None)
+    return coef[0] + 1j * coef[1], spec
+
+
+def test_sphere_source_converges_to_the_exact_solution():
+    from paper_1905_00182_gb300 import ibfsa as ib
+    ib.lib()
+    xp = _probes()
+    # away from the source's core (distance >= 0.3 from its centre) the scattered wave is half
+    # of the field; the error there is the measure, the error over all probes is reported
+    far = np.hypot(xp[0] - 2.0 * R, xp[1]) >= 0.3
+    err, err_all = {}, {}
+    for n in (256, 384, 512):
+        P, spec = _settled_amplitude(ib, n, xp)
+        want = S.sphere_source_field(xp, R, spec.src_omega, spec.src_amp, spec.src_b,
+                                     spec.src_xc)
+        err[n] = float(np.linalg.norm((P - want)[far]) / np.linalg.norm(want[far]))
+        err_all[n] = float(np.linalg.norm(P - want) / np.linalg.norm(want))
+        torch.cuda.empty_cache()
+    free = S.sphere_source_field(xp, 0.0, spec.src_omega, spec.src_amp, spec.src_b, spec.src_xc)
+    sc = float(np.linalg.norm((want - free)[far]) / np.linalg.norm(want[far]))
+    print("relative L2 error of the settled amplitude vs exact, away from the source core: " +
+          ", ".join(f"R/h {n // 32}: {e:.4f}" for n, e in err.items()) +
+          "; all probes: " + ", ".join(f"{e:.4f}" for e in err_all.values()) +
+          f" (scattered part {sc:.3f} of the field there)")
+    assert err[256] > err[384] > err[512], err
+    assert err[512] <= 0.35, err
