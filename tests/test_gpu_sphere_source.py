@@ -86,7 +86,9 @@ def test_sphere_front_side_converges_to_the_exact_solution():
     """With the rigid sphere: on the source's side of it (the x line at x >= 0.75, outside the
     source's core) the field converges to the exact one.  Behind the sphere (the axis of its
     bright spot) and on the y line the error does not fall from R/h 8 to 16, nor with a
-    penalty three or six times stiffer: printed, not asserted."""
+    penalty three or six times stiffer: the fluid inside the sphere, fed through the kernel's
+    support, rings as a dipole along the source's axis and re-radiates.  Printed, not
+    asserted."""
     from paper_1905_00182_gb300 import ibfsa as ib
     ib.lib()
     xp = _probes()
