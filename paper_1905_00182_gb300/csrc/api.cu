@@ -541,19 +541,24 @@ int ibfsa_max_wavespeed(ibfsa_grid *g, double *host_alpha) {
   return IBFSA_OK;
 }
 
+// Stages the np probe points and samples dp at them into G.probe_out (stream-ordered).
+static cudaError_t sample_probes(Grid &G, int np, const double *xp) {
+  cudaError_t e = cudaMemcpyAsync(G.probe_xp, xp, sizeof(double) * G.p.dim * np,
+                                  cudaMemcpyDefault, G.stream);
+  if (e != cudaSuccess) return e;
+  return G.d.precision == IBFSA_FP32_PERTURB
+             ? fp32_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
+         : G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
+                         : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof);
+}
+
 int ibfsa_probe(ibfsa_grid *g, int np, const double *xp, double *out) {
   if (!g || (np > 0 && (!xp || !out))) return fail(IBFSA_ERR_ARG, "NULL argument");
   Grid &G = g->g;
   if (np < 0 || np > G.max_probes)
     return fail(IBFSA_ERR_ARG, "probe count %d outside [0, %d]", np, G.max_probes);
   if (np == 0) return IBFSA_OK;
-  cudaError_t e = cudaMemcpyAsync(G.probe_xp, xp, sizeof(double) * G.p.dim * np,
-                                  cudaMemcpyDefault, G.stream);
-  if (e == cudaSuccess)
-    e = G.d.precision == IBFSA_FP32_PERTURB
-            ? fp32_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
-        : G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
-                        : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof);
+  cudaError_t e = sample_probes(G, np, xp);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, G.probe_out, sizeof(double) * np, cudaMemcpyDefault, G.stream);
   if (e == cudaSuccess && is_host_pointer(out)) e = cudaStreamSynchronize(G.stream);
@@ -567,13 +572,7 @@ int ibfsa_probe_accumulate(ibfsa_grid *g, int np, const double *xp, double *out,
     return fail(IBFSA_ERR_ARG, "probe count %d outside [0, %d]", np, G.max_probes);
   if (np == 0) return IBFSA_OK;
   if (is_host_pointer(acc)) return fail(IBFSA_ERR_ARG, "acc must be device memory");
-  cudaError_t e = cudaMemcpyAsync(G.probe_xp, xp, sizeof(double) * G.p.dim * np,
-                                  cudaMemcpyDefault, G.stream);
-  if (e == cudaSuccess)
-    e = G.d.precision == IBFSA_FP32_PERTURB
-            ? fp32_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
-        : G.d.strict_fp ? strict_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof)
-                        : fast_probe(G.p, G.Q, np, G.probe_xp, G.probe_out, G.stream, &G.prof);
+  cudaError_t e = sample_probes(G, np, xp);
   if (e == cudaSuccess) e = probe_fold(np, G.probe_out, acc, G.stream);
   if (e == cudaSuccess && out)
     e = cudaMemcpyAsync(out, G.probe_out, sizeof(double) * np, cudaMemcpyDefault, G.stream);
