@@ -43,3 +43,29 @@ def test_fp32_finish_bytes_by_stage_mean():
     # stage 3: increment in 20, FP64 state read and written 80, FP32 copy 20 -> mean 92 B
     b = bench.bytes_per_cell("fp32")
     assert math.isclose(b["finish"], 92.0)
+
+
+class _Fake:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+    def join(self, timeout=None):
+        pass
+
+
+def test_clock_record_parsing():
+    c = object.__new__(bench.Clocks)
+    c.proc, c.th = _Fake(), _Fake()
+    row = "0, {sm}, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, {cap}"
+    c.rows = [[x.strip() for x in row.format(sm=sm, cap=cap).split(",")]
+              for sm, cap in ((2070, "Not Active"), (1980, "Active"), (2070, "Not Active"))]
+    out = c.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
+    # no sampler at all: stated, not silently empty
+    c2 = object.__new__(bench.Clocks)
+    c2.proc = None
+    assert c2.stop()["reasons"] == ["nvidia-smi unavailable"]
