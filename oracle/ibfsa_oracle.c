@@ -14,7 +14,8 @@
  *                                                                free stream, periodic)
  *   2. alpha_d = max over interior of |u_d| + c                 (global Lax-Friedrichs split)
  *   3. convective term: f+- = (F_d(Q) +- alpha_d Q)/2, fifth-order WENO5-JS or TENO5
- *      reconstruction of every component at every face, then -(Fhat_{i+1/2}-Fhat_{i-1/2})/h
+ *      reconstruction of every component at every face (or, as an option, of every
+ *      characteristic field at the face's Roe average), then -(Fhat_{i+1/2}-Fhat_{i-1/2})/h
  *                                                                (Sec. 2, Eq. 2 and the text
  *                                                                after Eq. 5)
  *   4. viscous term: 4th-order central gradients of u, tau_ij, b = u.tau (no heat flux),
@@ -33,7 +34,9 @@
  * TENO's ENO cut-off on a step, fifth-order convergence of the reconstruction, fourth-order
  * convergence of the viscous operator against the continuous PDE, free-stream preservation,
  * entropy-wave exact solution, third-order RK3, convergence of the Sec. 3.1 pulse to the exact
- * linear-acoustics solution, and penalty enforcement of no slip.
+ * linear-acoustics solution, and penalty enforcement of no slip; for the characteristic-wise
+ * option, the eigen-system against the flux Jacobian, Roe's property of the face average and
+ * Sod's shock tube against the exact Riemann solution.
  */
 #include <math.h>
 #include <stdint.h>
@@ -282,6 +285,159 @@ static void convective(const pgrid *G, const orc_desc *d, const double *W, const
         }
     free(fp); free(fm); free(Fh);
   }
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* Characteristic-wise variant: the split fluxes of the stencil are projected on the left      */
+/* eigenvectors of the Euler flux Jacobian along the face normal (Roe average of the face's    */
+/* two cells), each characteristic field is reconstructed as above, and the face flux is       */
+/* projected back with the right eigenvectors.  The splitting stays the global one.            */
+/* ----------------------------------------------------------------------------------------- */
+int orc_char_eigen(int dim, double gamma, int a, const double *Ql, const double *Qr, double *R,
+                   double *Lv, double *lam) {
+  if ((dim != 2 && dim != 3) || a < 0 || a >= dim || !(gamma > 1.0)) return ORC_ERR_ARG;
+  int nv = dim + 2;
+  if (!(Ql[0] > 0.0) || !(Qr[0] > 0.0)) return ORC_ERR_ARG;
+  /* Roe average: sqrt(rho)-weighted velocity and total enthalpy */
+  double sl = sqrt(Ql[0]), sr = sqrt(Qr[0]);
+  double u[3] = {0.0, 0.0, 0.0}, kel = 0.0, ker = 0.0;
+  for (int b = 0; b < dim; b++) {
+    double ul = Ql[1 + b] / Ql[0], ur = Qr[1 + b] / Qr[0];
+    u[b] = (sl * ul + sr * ur) / (sl + sr);
+    kel = kel + Ql[1 + b] * ul;
+    ker = ker + Qr[1 + b] * ur;
+  }
+  double pl = (gamma - 1.0) * (Ql[nv - 1] - 0.5 * kel);
+  double pr = (gamma - 1.0) * (Qr[nv - 1] - 0.5 * ker);
+  double Hl = (Ql[nv - 1] + pl) / Ql[0], Hr = (Qr[nv - 1] + pr) / Qr[0];
+  double H = (sl * Hl + sr * Hr) / (sl + sr);
+  double q2 = 0.0;
+  for (int b = 0; b < dim; b++) q2 = q2 + u[b] * u[b];
+  double c2 = (gamma - 1.0) * (H - 0.5 * q2);
+  if (!(c2 > 0.0)) return ORC_ERR_ARG;
+  double c = sqrt(c2);
+  double b1 = (gamma - 1.0) / c2, b2 = 0.5 * q2 * b1;
+  double ua = u[a];
+  /* transverse directions in increasing order */
+  int tr[2], nt = 0;
+  for (int b = 0; b < dim; b++)
+    if (b != a) tr[nt++] = b;
+  for (int i = 0; i < nv * nv; i++) {
+    R[i] = 0.0;
+    Lv[i] = 0.0;
+  }
+  /* columns of R (entry [row * nv + col]) */
+  int km = 0, ke = 1, kp = nv - 1;
+  R[0 * nv + km] = 1.0;
+  R[0 * nv + ke] = 1.0;
+  R[0 * nv + kp] = 1.0;
+  for (int b = 0; b < dim; b++) {
+    R[(1 + b) * nv + km] = u[b] - (b == a ? c : 0.0);
+    R[(1 + b) * nv + ke] = u[b];
+    R[(1 + b) * nv + kp] = u[b] + (b == a ? c : 0.0);
+  }
+  R[(nv - 1) * nv + km] = H - ua * c;
+  R[(nv - 1) * nv + ke] = 0.5 * q2;
+  R[(nv - 1) * nv + kp] = H + ua * c;
+  for (int t = 0; t < nt; t++) {
+    R[(1 + tr[t]) * nv + 2 + t] = 1.0;
+    R[(nv - 1) * nv + 2 + t] = u[tr[t]];
+  }
+  /* rows of L */
+  Lv[km * nv + 0] = 0.5 * (b2 + ua / c);
+  Lv[kp * nv + 0] = 0.5 * (b2 - ua / c);
+  Lv[ke * nv + 0] = 1.0 - b2;
+  for (int b = 0; b < dim; b++) {
+    Lv[km * nv + 1 + b] = 0.5 * (-b1 * u[b] - (b == a ? 1.0 / c : 0.0));
+    Lv[kp * nv + 1 + b] = 0.5 * (-b1 * u[b] + (b == a ? 1.0 / c : 0.0));
+    Lv[ke * nv + 1 + b] = b1 * u[b];
+  }
+  Lv[km * nv + nv - 1] = 0.5 * b1;
+  Lv[kp * nv + nv - 1] = 0.5 * b1;
+  Lv[ke * nv + nv - 1] = -b1;
+  for (int t = 0; t < nt; t++) {
+    Lv[(2 + t) * nv + 0] = -u[tr[t]];
+    Lv[(2 + t) * nv + 1 + tr[t]] = 1.0;
+  }
+  if (lam) {
+    lam[km] = ua - c;
+    lam[kp] = ua + c;
+    for (int k = 1; k < nv - 1; k++) lam[k] = ua;
+  }
+  return ORC_OK;
+}
+
+static int convective_charwise(const pgrid *G, const orc_desc *d, const double *W,
+                               const double *u, const double *p, const double alpha[3],
+                               double *L) {
+  int nv = G->nv;
+  size_t Nu = (size_t)G->n[0] * G->n[1] * G->n[2];
+  for (int a = 0; a < G->dim; a++) {
+    int na = G->n[a], len = na + 2 * NG;
+    double *fp = malloc(sizeof(double) * nv * len);
+    double *fm = malloc(sizeof(double) * nv * len);
+    double *Fh = malloc(sizeof(double) * nv * (na + 1));
+    int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+    for (int t2 = 0; t2 < G->n[b2]; t2++)
+      for (int t1 = 0; t1 < G->n[b1]; t1++) {
+        for (int l = -NG; l < na + NG; l++) {
+          int I[3];
+          I[a] = l; I[b1] = t1; I[b2] = t2;
+          size_t s = pidx(G, I[0], I[1], I[2]);
+          for (int c = 0; c < nv; c++) {
+            double F = flux(G, W, u, p, a, c, s);
+            double q = W[c * G->N + s];
+            fp[c * len + l + NG] = 0.5 * (F + alpha[a] * q);
+            fm[c * len + l + NG] = 0.5 * (F - alpha[a] * q);
+          }
+        }
+        for (int m = -1; m < na; m++) {
+          /* the face between cells m and m+1 */
+          double Ql[5], Qr[5], R[25], Lv[25];
+          int I[3];
+          I[a] = m; I[b1] = t1; I[b2] = t2;
+          size_t sl = pidx(G, I[0], I[1], I[2]);
+          I[a] = m + 1;
+          size_t sr = pidx(G, I[0], I[1], I[2]);
+          for (int c = 0; c < nv; c++) {
+            Ql[c] = W[c * G->N + sl];
+            Qr[c] = W[c * G->N + sr];
+          }
+          if (orc_char_eigen(G->dim, d->gamma, a, Ql, Qr, R, Lv, NULL) != ORC_OK) {
+            free(fp); free(fm); free(Fh);
+            return ORC_ERR_ARG;
+          }
+          double h[5];
+          for (int k = 0; k < nv; k++) {
+            double vp[5], vm[5];
+            for (int r = 0; r < 5; r++) {
+              double sp = 0.0, sm = 0.0;
+              for (int c = 0; c < nv; c++) {
+                sp = sp + Lv[k * nv + c] * fp[c * len + m - 2 + r + NG];
+                sm = sm + Lv[k * nv + c] * fm[c * len + m + 3 - r + NG];
+              }
+              vp[r] = sp;
+              vm[r] = sm;
+            }
+            h[k] = recon(d->scheme, vp) + recon(d->scheme, vm);
+          }
+          for (int c = 0; c < nv; c++) {
+            double s = 0.0;
+            for (int k = 0; k < nv; k++) s = s + R[c * nv + k] * h[k];
+            Fh[c * (na + 1) + m + 1] = s;
+          }
+        }
+        for (int c = 0; c < nv; c++)
+          for (int m = 0; m < na; m++) {
+            int I[3];
+            I[a] = m; I[b1] = t1; I[b2] = t2;
+            size_t o = c * Nu + uidx(G, I[0], I[1], I[2]);
+            L[o] = L[o] - (Fh[c * (na + 1) + m + 1] - Fh[c * (na + 1) + m]) / G->h[a];
+          }
+      }
+    free(fp); free(fm); free(Fh);
+  }
+  return ORC_OK;
 }
 
 /* 4th-order central first derivative from f_{-2..+2}: (8(f1 - f_-1) - (f2 - f_-2)) / (12 h) */
@@ -559,7 +715,12 @@ static int rhs_impl(const orc_desc *d, const double *Q, int nm, const double *X,
     for (int a = 0; a < 3; a++) alpha[a] = alpha_in[a];
   if (alpha_out) for (int a = 0; a < 3; a++) alpha_out[a] = alpha[a];
   for (size_t o = 0; o < (size_t)G.nv * Nu; o++) L[o] = 0.0;
-  convective(&G, d, W, u, p, alpha, L);
+  if (d->charwise) {
+    rc = convective_charwise(&G, d, W, u, p, alpha, L);
+    if (rc) { free(W); free(rho); free(u); free(p); return rc; }
+  } else {
+    convective(&G, d, W, u, p, alpha, L);
+  }
   if (d->Re > 0.0) viscous(&G, d, u, L);
   sponge(&G, d, Q, L);
   pressure_source(&G, d, d->time, L);

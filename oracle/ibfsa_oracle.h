@@ -22,9 +22,18 @@ typedef struct {
    * S_E = src_amp exp(-src_b ln2 |x - src_xc|^2) cos(src_omega t) / (gamma - 1); src_amp = 0: none */
   double src_amp, src_b, src_omega, src_xc[3];
   double time;          /* time at which orc_rhs evaluates the source; start time of orc_rk3 */
+  /* 0: component-wise reconstruction of the split fluxes; 1: characteristic-wise, projected on
+   * the eigenvectors of the Euler flux Jacobian at the Roe average of the two cells of each face */
+  int charwise;
 } orc_desc;
 
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_BOUNDS = -4, ORC_ERR_NOMEM = -7 };
+
+/* Roe average of the conservative states Ql, Qr (nv = dim + 2) and the right (columns) and
+ * left (rows) eigenvectors of the flux Jacobian along direction a there, row-major nv x nv;
+ * lam (may be NULL) receives the eigenvalues u_a - c, u_a (entropy, then shear), u_a + c. */
+int orc_char_eigen(int dim, double gamma, int a, const double *Ql, const double *Qr, double *R,
+                   double *Lv, double *lam);
 
 int orc_rhs(const orc_desc *d, const double *Q, int nm, const double *X, const double *U,
             const double *dS, const double *xi, double *L, double *F, double *rate,

@@ -54,6 +54,7 @@ class OrcDesc(ctypes.Structure):
         ("src_omega", ctypes.c_double),
         ("src_xc", ctypes.c_double * 3),
         ("time", ctypes.c_double),
+        ("charwise", ctypes.c_int),
     ]
 
 
@@ -83,7 +84,7 @@ def lib():
     return _lib
 
 
-def desc(spec, t: float = 0.0) -> OrcDesc:
+def desc(spec, t: float = 0.0, charwise: bool = False) -> OrcDesc:
     d = OrcDesc()
     d.dim = spec.dim
     for a in range(3):
@@ -107,6 +108,7 @@ def desc(spec, t: float = 0.0) -> OrcDesc:
     for a in range(3):
         d.src_xc[a] = float(spec.src_xc[a])
     d.time = float(t)
+    d.charwise = 1 if charwise else 0
     return d
 
 
@@ -146,15 +148,16 @@ def _markers(spec, X, U, dS, xi):
     return nm, X, U, dS, xi
 
 
-def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0):
-    """RHS L(Q) + S of every interior cell at time t, shape [nv][nz][ny][nx]."""
+def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0, charwise=False):
+    """RHS L(Q) + S of every interior cell at time t, shape [nv][nz][ny][nx] (charwise: the
+    characteristic-wise reconstruction)."""
     Q = _f64(Q)
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     L = np.zeros_like(Q)
     F = np.zeros((spec.dim, max(nm, 1)))
     rate = np.zeros((spec.dim, max(nm, 1)))
     alpha = np.zeros(3)
-    d = desc(spec, t)
+    d = desc(spec, t, charwise)
     rc = lib().orc_rhs(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi), _p(L), _p(F),
                        _p(rate), _p(alpha))
     if rc != ORC_OK:
@@ -178,12 +181,12 @@ def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None):
     return L
 
 
-def rk3(spec, Q, dt, nsteps=1, X=None, U=None, dS=None, xi=None, t=0.0):
+def rk3(spec, Q, dt, nsteps=1, X=None, U=None, dS=None, xi=None, t=0.0, charwise=False):
     """nsteps SSP-RK3 steps from time t; returns (Q, xi)."""
     Q = _f64(Q).copy()
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     xi = xi.copy() if xi is not None else None
-    d = desc(spec, t)
+    d = desc(spec, t, charwise)
     rc = lib().orc_rk3(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi), float(dt),
                        int(nsteps))
     if rc != ORC_OK:
@@ -429,3 +432,19 @@ def probe_stats(history):
     mean = h.sum(axis=0) / h.shape[0]
     dev = h - mean
     return mean, np.sqrt((dev * dev).sum(axis=0) / h.shape[0])
+
+
+def char_eigen(dim, gamma, a, Ql, Qr=None):
+    """(R, L, lam): right eigenvectors (columns), left eigenvectors (rows) and eigenvalues of the
+    Euler flux Jacobian along direction a at the Roe average of Ql and Qr (Qr = Ql: at Ql)."""
+    nv = dim + 2
+    Ql = _f64(Ql)
+    Qr = Ql if Qr is None else _f64(Qr)
+    R = np.zeros((nv, nv))
+    L = np.zeros((nv, nv))
+    lam = np.zeros(nv)
+    rc = lib().orc_char_eigen(int(dim), ctypes.c_double(gamma), int(a), _p(Ql), _p(Qr), _p(R),
+                              _p(L), _p(lam))
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle eigen-system failed: {rc}")
+    return R, L, lam
