@@ -7,8 +7,9 @@
  *   compressible Navier-Stokes, Eq. 2-5, on a uniform Cartesian grid with cell-centred nodes
  *   x_i = lo + (i + 1/2) h, h = (hi - lo)/n;  Q = [rho, rho u, rho v, (rho w), E];
  *   convective fluxes split by a global Lax-Friedrichs splitting f+- = (F +- alpha_d Q)/2 with
- *   alpha_d = max(|u_d| + c) of the stage input, reconstructed component-wise at every face by
- *   fifth-order WENO5-JS or TENO5 (text after Eq. 5), differenced conservatively;
+ *   alpha_d = max(|u_d| + c) of the stage input, reconstructed component-wise (or, as an
+ *   option, characteristic-wise) at every face by fifth-order WENO5-JS or TENO5 (text after
+ *   Eq. 5), differenced conservatively;
  *   viscous fluxes [0, tau_{.d}, b_d] (Eq. 5, no heat flux) by fourth-order central
  *   differences (gradients, then divergence), scaled by 1/Re;
  *   penalty immersed boundary: U_ib = sum_j u_j delta_h(X - x_j) h^d (Eq. 8),
@@ -95,6 +96,13 @@ typedef struct {
   double beta_pen;         /* beta of Eq. 7 */
   int max_markers;         /* capacity for Lagrangian markers */
   int max_probes;          /* capacity for probe points */
+  int charwise;            /* 0: each split-flux component reconstructed on its own (the
+                              paper is silent; the default); 1: characteristic-wise -- the
+                              split fluxes of each stencil projected on the left eigenvectors
+                              of the Euler flux Jacobian along the face normal at the Roe
+                              average of the face's two cells, reconstructed per field and
+                              projected back.  FP64 forms only (IBFSA_ERR_UNSUPPORTED
+                              otherwise). */
 } ibfsa_grid_desc;
 
 /* Bytes of device workspace a grid with this descriptor needs (for the caller to allocate). */

@@ -108,7 +108,7 @@ def desc(spec, t: float = 0.0, charwise: bool = False) -> OrcDesc:
     for a in range(3):
         d.src_xc[a] = float(spec.src_xc[a])
     d.time = float(t)
-    d.charwise = 1 if charwise else 0
+    d.charwise = 1 if (charwise or getattr(spec, "charwise", False)) else 0
     return d
 
 

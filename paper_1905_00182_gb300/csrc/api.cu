@@ -64,6 +64,9 @@ static int check_desc(const ibfsa_grid_desc *d) {
     return fail(IBFSA_ERR_UNSUPPORTED, "strict_fp applies to the FP64 arithmetic only");
   if (d->sponge_cells < 0 || d->max_markers < 0 || d->max_probes < 0)
     return fail(IBFSA_ERR_ARG, "negative sponge width or capacity");
+  if (d->charwise != 0 && d->charwise != 1) return fail(IBFSA_ERR_ARG, "charwise must be 0 or 1");
+  if (d->charwise && d->precision != IBFSA_FP64)
+    return fail(IBFSA_ERR_UNSUPPORTED, "characteristic-wise reconstruction is FP64 only");
   (void)cells;
   return IBFSA_OK;
 }
@@ -72,6 +75,7 @@ void plan_geometry(const ibfsa_grid_desc &d, Plan &p) {
   memset(&p, 0, sizeof(p));
   p.dim = d.dim;
   p.nv = d.dim + 2;
+  p.charwise = d.charwise;
   p.N = 1;
   p.NP = 1;
   p.NB = 1;

@@ -15,6 +15,7 @@ constexpr int NG = 4;  // ghost layers: a fourth-order derivative of a fourth-or
 // direction (one layer of extent 1 in an inactive z), x fastest.
 struct Plan {
   int dim, nv;
+  int charwise;   // characteristic-wise reconstruction (FP64 forms)
   int n[3];       // interior extents (n[2] = 1 in 2D)
   int P[3];       // padded extents
   int g[3];       // ghost layers per direction (4 or 0)

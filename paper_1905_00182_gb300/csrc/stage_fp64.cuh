@@ -260,6 +260,83 @@ __global__ void __launch_bounds__(THREADS) k_pad(Plan p, const double *__restric
 // convective term along direction A: split fluxes of a tile of lines staged in shared memory,
 // one face per thread per pass, conservative difference into L
 // ------------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------------
+// characteristic-wise option: eigenvectors of the Euler flux Jacobian along A at the Roe
+// average of the face's two cells (sqrt(rho)-weighted velocity and total enthalpy).  Right
+// eigenvectors are the columns of R, left ones the rows of Lv, in the order u-c, entropy,
+// shears (transverse directions in increasing order), u+c.  Written operation by operation in
+// the order of the formulas, so that the strict form is reproducible.
+// ------------------------------------------------------------------------------------------
+template <int DIM, int A>
+__device__ __forceinline__ void roe_eigen(const Plan &p, const double *Ql, const double *Qr,
+                                          double R[DIM + 2][DIM + 2],
+                                          double Lv[DIM + 2][DIM + 2]) {
+  constexpr int NV = DIM + 2;
+  const double gm1 = p.gm1;
+  double sl = sqrt(Ql[0]), sr = sqrt(Qr[0]);
+  double u[DIM], kel = 0.0, ker = 0.0;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    double ul = Ql[1 + b] / Ql[0], ur = Qr[1 + b] / Qr[0];
+    u[b] = (sl * ul + sr * ur) / (sl + sr);
+    kel = kel + Ql[1 + b] * ul;
+    ker = ker + Qr[1 + b] * ur;
+  }
+  double pl = gm1 * (Ql[NV - 1] - 0.5 * kel);
+  double pr = gm1 * (Qr[NV - 1] - 0.5 * ker);
+  double Hl = (Ql[NV - 1] + pl) / Ql[0], Hr = (Qr[NV - 1] + pr) / Qr[0];
+  double H = (sl * Hl + sr * Hr) / (sl + sr);
+  double q2 = 0.0;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) q2 = q2 + u[b] * u[b];
+  double c2 = gm1 * (H - 0.5 * q2);
+  double c = sqrt(c2);
+  double b1 = gm1 / c2, b2 = 0.5 * q2 * b1;
+  double ua = u[A];
+#pragma unroll
+  for (int i = 0; i < NV; i++)
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+      R[i][j] = 0.0;
+      Lv[i][j] = 0.0;
+    }
+  constexpr int km = 0, ke = 1, kp = NV - 1;
+  R[0][km] = 1.0;
+  R[0][ke] = 1.0;
+  R[0][kp] = 1.0;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    R[1 + b][km] = u[b] - (b == A ? c : 0.0);
+    R[1 + b][ke] = u[b];
+    R[1 + b][kp] = u[b] + (b == A ? c : 0.0);
+  }
+  R[NV - 1][km] = H - ua * c;
+  R[NV - 1][ke] = 0.5 * q2;
+  R[NV - 1][kp] = H + ua * c;
+  Lv[km][0] = 0.5 * (b2 + ua / c);
+  Lv[kp][0] = 0.5 * (b2 - ua / c);
+  Lv[ke][0] = 1.0 - b2;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    Lv[km][1 + b] = 0.5 * (-b1 * u[b] - (b == A ? 1.0 / c : 0.0));
+    Lv[kp][1 + b] = 0.5 * (-b1 * u[b] + (b == A ? 1.0 / c : 0.0));
+    Lv[ke][1 + b] = b1 * u[b];
+  }
+  Lv[km][NV - 1] = 0.5 * b1;
+  Lv[kp][NV - 1] = 0.5 * b1;
+  Lv[ke][NV - 1] = -b1;
+  int t = 0;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    if (b == A) continue;
+    R[1 + b][2 + t] = 1.0;
+    R[NV - 1][2 + t] = u[b];
+    Lv[2 + t][0] = -u[b];
+    Lv[2 + t][1 + b] = 1.0;
+    t++;
+  }
+}
+
 template <int A>
 struct ConvTile {
   // A == 0: 4 lines (y/z) of 63 cells; otherwise 32 lines (consecutive x) of 15 cells
@@ -275,7 +352,7 @@ __host__ __device__ constexpr size_t conv_smem_bytes() {
   return sizeof(double) * 2 * (DIM + 2) * ConvTile<A>::ROWS * ConvTile<A>::LEN;
 }
 
-template <int DIM, int A, int SCHEME>
+template <int DIM, int A, int SCHEME, bool CHAR>
 __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
   constexpr int NV = DIM + 2;
   using T = ConvTile<A>;
@@ -360,12 +437,62 @@ __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
       else { row = e % T::ROWS; fi = e / T::ROWS; }
       // staged index of cell m is (m - seg0) + 3 = fi + 2
       int b = fi + 2;
+      if constexpr (CHAR) {
+        // characteristic fields of the stencil at the Roe average of cells m and m+1 (only
+        // the faces -1/2 .. n-1/2 are used)
+        int I[3];
+        bool ok = cell_of(row, fi - 1, I) && I[A] <= p.n[A] - 1;
+        if (ok) {
+          long long sl = pad_index(p, I[0], I[1], I[2]);
+          I[A] += 1;
+          long long sr = pad_index(p, I[0], I[1], I[2]);
+          double Ql[NV], Qr[NV];
 #pragma unroll
-      for (int c = 0; c < NV; c++) {
-        const double *fp = sfp + (c * T::ROWS + row) * T::LEN;
-        const double *fm = sfm + (c * T::ROWS + row) * T::LEN;
-        Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
-                    recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+          for (int c = 0; c < NV; c++) {
+            Ql[c] = p.Qp[c * p.NP + sl];
+            Qr[c] = p.Qp[c * p.NP + sr];
+          }
+          double R[NV][NV], Lv[NV][NV];
+          roe_eigen<DIM, A>(p, Ql, Qr, R, Lv);
+          double hk[NV];
+#pragma unroll
+          for (int k = 0; k < NV; k++) {
+            double vp[5], vm[5];
+#pragma unroll
+            for (int r = 0; r < 5; r++) {
+              double sp = 0.0, sn = 0.0;
+#pragma unroll
+              for (int c = 0; c < NV; c++) {
+                const double *fp = sfp + (c * T::ROWS + row) * T::LEN;
+                const double *fm = sfm + (c * T::ROWS + row) * T::LEN;
+                sp = sp + Lv[k][c] * fp[b - 2 + r];
+                sn = sn + Lv[k][c] * fm[b + 3 - r];
+              }
+              vp[r] = sp;
+              vm[r] = sn;
+            }
+            hk[k] = recon<SCHEME>(p, vp[0], vp[1], vp[2], vp[3], vp[4]) +
+                    recon<SCHEME>(p, vm[0], vm[1], vm[2], vm[3], vm[4]);
+          }
+#pragma unroll
+          for (int c = 0; c < NV; c++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < NV; k++) acc = acc + R[c][k] * hk[k];
+            Fh[ps][c] = acc;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < NV; c++) Fh[ps][c] = 0.0;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NV; c++) {
+          const double *fp = sfp + (c * T::ROWS + row) * T::LEN;
+          const double *fm = sfm + (c * T::ROWS + row) * T::LEN;
+          Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
+                      recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+        }
       }
     }
   }
@@ -690,8 +817,11 @@ template <int DIM, int A, int SCHEME>
 cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
   using T = ConvTile<A>;
   constexpr size_t smem = conv_smem_bytes<DIM, A>();
-  cudaError_t e = cudaFuncSetAttribute(k_conv<DIM, A, SCHEME>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = p.charwise
+                      ? cudaFuncSetAttribute(k_conv<DIM, A, SCHEME, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                      : cudaFuncSetAttribute(k_conv<DIM, A, SCHEME, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid;
   if (A == 0) {
@@ -701,7 +831,8 @@ cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
     int nx = (p.n[0] + T::ROWS - 1) / T::ROWS;
     grid = dim3(nseg * nx, A == 1 ? p.n[2] : p.n[1]);
   }
-  k_conv<DIM, A, SCHEME><<<grid, THREADS, smem, st>>>(p, first);
+  if (p.charwise) k_conv<DIM, A, SCHEME, true><<<grid, THREADS, smem, st>>>(p, first);
+  else k_conv<DIM, A, SCHEME, false><<<grid, THREADS, smem, st>>>(p, first);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,7 @@ class GridDesc(ctypes.Structure):
         ("beta_pen", ctypes.c_double),
         ("max_markers", ctypes.c_int),
         ("max_probes", ctypes.c_int),
+        ("charwise", ctypes.c_int),
     ]
 
 
@@ -191,6 +192,7 @@ def desc_from_spec(spec: W.GridSpec, strict: bool = False, max_probes: int = 0) 
     d.beta_pen = float(spec.beta_pen)
     d.max_markers = int(spec.max_markers)
     d.max_probes = int(max_probes)
+    d.charwise = int(spec.charwise)
     return d
 
 

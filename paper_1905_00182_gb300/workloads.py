@@ -56,6 +56,8 @@ class GridSpec:
     src_b: float = 0.0
     src_omega: float = 0.0
     src_xc: tuple = (0.0, 0.0, 0.0)
+    # characteristic-wise reconstruction (FP64 forms) instead of component-wise
+    charwise: bool = False
 
     @property
     def nv(self) -> int:

@@ -56,6 +56,7 @@ def test_workspace_bytes_counts_buffers(ib):
     ("dim", 4, -1), ("n", (0, 12, 8), -1), ("hi", (0.0, 1.0, 1.0), -1),
     ("bc", ((2, 0), (0, 0), (0, 0)), -1), ("bc", ((2, 2), (0, 0), (0, 0)), None),
     ("n", (3, 12, 8), None), ("gamma", 1.0, -1), ("scheme", 7, -5), ("precision", 9, -5),
+    ("charwise", True, None), ("charwise", 2, -1),
 ])
 def test_descriptor_validation(ib, field, value, code):
     spec = _good()
@@ -70,6 +71,15 @@ def test_descriptor_validation(ib, field, value, code):
         ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec))
     assert e.value.code == code
     assert ib.lib().ibfsa_last_error()
+
+
+def test_charwise_is_fp64_only(ib):
+    spec = _good()
+    spec.charwise = True
+    spec.precision = W.FP32_PERTURB
+    with pytest.raises(ib.IbfsaError) as e:
+        ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec))
+    assert e.value.code == ib.IBFSA_ERR_UNSUPPORTED
 
 
 def test_plate_workspace_counts_buffers(ib):
