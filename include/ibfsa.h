@@ -144,7 +144,9 @@ int ibfsa_rhs(ibfsa_grid *g, double *L);
 
 /* Advance the state and xi by nsteps third-order SSP Runge-Kutta steps of size dt:
  *   Q1 = Qn + dt L(Qn);  Q2 = 3/4 Qn + 1/4 (Q1 + dt L(Q1));  Qn+1 = 1/3 Qn + 2/3 (Q2 + dt L(Q2)),
- * each stage evaluated as a Qn + b (Qs + dt L(Qs)).  Markers stay fixed during the call. */
+ * each stage evaluated as a Qn + b (Qs + dt L(Qs)).  Markers stay fixed during the call; the
+ * stages see the source at t, t + dt, t + dt/2 and the grid's clock advances by dt per step.
+ * dt must be finite and positive, nsteps >= 0 (IBFSA_ERR_ARG otherwise). */
 int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps);
 
 /* Periodic Gaussian pressure source of Sec. 3.6 (Eq. 16), A_p = amp exp(-b ln2 |x - xc|^2)

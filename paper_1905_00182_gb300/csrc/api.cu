@@ -471,7 +471,8 @@ int ibfsa_rhs(ibfsa_grid *g, double *L) {
 
 int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps) {
   if (!g) return fail(IBFSA_ERR_ARG, "NULL grid");
-  if (nsteps < 0 || !(dt > 0.0)) return fail(IBFSA_ERR_ARG, "need dt > 0 and nsteps >= 0");
+  if (nsteps < 0 || !(dt > 0.0) || !isfinite(dt))
+    return fail(IBFSA_ERR_ARG, "need a finite dt > 0 and nsteps >= 0");
   Grid &G = g->g;
   if (G.d.scheme == IBFSA_MLP_TENO5 && !G.mlp_set)
     return fail(IBFSA_ERR_ARG, "IBFSA_MLP_TENO5 grid without weights: call ibfsa_set_mlp");
