@@ -8,7 +8,9 @@
  * source, header, table or helper with the CUDA path.
  *
  * Every step is written as a direct loop over a ghost-padded FP64 array, in the order the
- * method states it (compile with -O2 -ffp-contract=off so that no multiply-add is fused):
+ * method states it (compile with -O2 -ffp-contract=off so that no multiply-add is fused).
+ * On a stretched grid (the non-uniform mesh of Sec. 2, given as node coordinates and dx/dxi per
+ * direction) every difference is taken in the computational coordinate and divided by dx/dxi:
  *
  *   1. ghost fill (4 layers) per boundary rule                 (readings: zero-gradient,
  *                                                                free stream, periodic)
@@ -127,6 +129,8 @@ typedef struct {
   int g[3];   /* ghost layers per direction (0 for an inactive z) */
   size_t N;   /* padded cell count */
   double h[3];
+  double lo[3];
+  const double *xn[3], *xm[3]; /* stretched grid (NULL: uniform) */
 } pgrid;
 
 static void pgrid_init(pgrid *G, const orc_desc *d) {
@@ -140,7 +144,20 @@ static void pgrid_init(pgrid *G, const orc_desc *d) {
     G->P[a] = G->n[a] + 2 * G->g[a];
     G->N *= (size_t)G->P[a];
     G->h[a] = act ? (d->hi[a] - d->lo[a]) / d->n[a] : 1.0;
+    G->lo[a] = d->lo[a];
+    G->xn[a] = act ? d->xnode[a] : NULL;
+    G->xm[a] = act ? d->xmetric[a] : NULL;
   }
+}
+
+/* dx/dxi at node i of direction a (the spacing h on a uniform grid) */
+static double met(const pgrid *G, int a, int i) {
+  return G->xm[a] ? G->xm[a][i + NG] : G->h[a];
+}
+
+/* coordinate of node i of direction a */
+static double node(const pgrid *G, int a, int i) {
+  return G->xn[a] ? G->xn[a][i + NG] : G->lo[a] + ((double)i + 0.5) * G->h[a];
 }
 
 /* linear offset of cell (i,j,k), interior-based indices (may be negative down to -g) */
@@ -280,7 +297,7 @@ static void convective(const pgrid *G, const orc_desc *d, const double *W, const
             int I[3];
             I[a] = m; I[b1] = t1; I[b2] = t2;
             size_t o = c * Nu + uidx(G, I[0], I[1], I[2]);
-            L[o] = L[o] - (Fh[m + 1] - Fh[m]) / G->h[a];
+            L[o] = L[o] - (Fh[m + 1] - Fh[m]) / met(G, a, m);
           }
         }
     free(fp); free(fm); free(Fh);
@@ -432,7 +449,7 @@ static int convective_charwise(const pgrid *G, const orc_desc *d, const double *
             int I[3];
             I[a] = m; I[b1] = t1; I[b2] = t2;
             size_t o = c * Nu + uidx(G, I[0], I[1], I[2]);
-            L[o] = L[o] - (Fh[c * (na + 1) + m + 1] - Fh[c * (na + 1) + m]) / G->h[a];
+            L[o] = L[o] - (Fh[c * (na + 1) + m + 1] - Fh[c * (na + 1) + m]) / met(G, a, m);
           }
       }
     free(fp); free(fm); free(Fh);
@@ -471,7 +488,8 @@ static void viscous(const pgrid *G, const orc_desc *d, const double *u, double *
             double f_m1 = ui[pidx(G, i - o[0], j - o[1], k - o[2])];
             double f_p1 = ui[pidx(G, i + o[0], j + o[1], k + o[2])];
             double f_p2 = ui[pidx(G, i + 2 * o[0], j + 2 * o[1], k + 2 * o[2])];
-            gr[(ci * 3 + dj) * G->N + s] = d4(f_m2, f_m1, f_p1, f_p2, G->h[dj]);
+            int at = dj == 0 ? i : (dj == 1 ? j : k);
+            gr[(ci * 3 + dj) * G->N + s] = d4(f_m2, f_m1, f_p1, f_p2, met(G, dj, at));
           }
       }
   /* viscous fluxes Fv[a][c] at the same box: tau_ij = g_ij + g_ji - 2/3 delta_ij div u */
@@ -506,7 +524,8 @@ static void viscous(const pgrid *G, const orc_desc *d, const double *u, double *
             sum += d4(F[pidx(G, i - 2 * o[0], j - 2 * o[1], k - 2 * o[2])],
                       F[pidx(G, i - o[0], j - o[1], k - o[2])],
                       F[pidx(G, i + o[0], j + o[1], k + o[2])],
-                      F[pidx(G, i + 2 * o[0], j + 2 * o[1], k + 2 * o[2])], G->h[a]);
+                      F[pidx(G, i + 2 * o[0], j + 2 * o[1], k + 2 * o[2])],
+                      met(G, a, a == 0 ? i : (a == 1 ? j : k)));
           }
           int c = fc + 1; /* momentum components 1..dim, energy nv-1 */
           (void)nv;
@@ -558,7 +577,7 @@ static void pressure_source(const pgrid *G, const orc_desc *d, double t, double 
         int I[3] = {i, j, k};
         double r2 = 0.0;
         for (int a = 0; a < G->dim; a++) {
-          double x = d->lo[a] + ((double)I[a] + 0.5) * G->h[a];
+          double x = node(G, a, I[a]);
           r2 = r2 + (x - d->src_xc[a]) * (x - d->src_xc[a]);
         }
         size_t o = (G->nv - 1) * Nu + uidx(G, i, j, k);
@@ -569,18 +588,40 @@ static void pressure_source(const pgrid *G, const orc_desc *d, double t, double 
 /* ----------------------------------------------------------------------------------------- */
 /* Immersed boundary (Eq. 7-11)                                                               */
 /* ----------------------------------------------------------------------------------------- */
-/* the 4 support nodes along direction a of position x: first index and the 4 weights */
-static int support(const pgrid *G, const orc_desc *d, int a, double x, double w[4]) {
-  double s = (x - d->lo[a]) / G->h[a] - 0.5; /* position in node-index units */
+/* the 4 support nodes along direction a of position x: first index and the 4 weights; *hl
+ * (may be NULL) receives the spacing there.  On a stretched grid the position is inverted
+ * through the node coordinates and the support must lie where the metric is constant (else
+ * the returned index is -NG - 4, outside every interior). */
+static int support(const pgrid *G, const orc_desc *d, int a, double x, double w[4],
+                   double *hl) {
+  if (!G->xn[a]) {
+    double s = (x - d->lo[a]) / G->h[a] - 0.5; /* position in node-index units */
+    int j0 = (int)floor(s) - 1;
+    for (int r = 0; r < 4; r++) w[r] = orc_lambda(s - (double)(j0 + r));
+    if (hl) *hl = G->h[a];
+    return j0;
+  }
+  int n = G->n[a];
+  if (!(x >= node(G, a, -NG)) || !(x < node(G, a, n + NG - 1))) return -NG - 4;
+  int i = -NG;
+  while (node(G, a, i + 1) <= x) i++;
+  double m = met(G, a, i);
+  double s = (double)i + (x - node(G, a, i)) / m;
   int j0 = (int)floor(s) - 1;
+  for (int r = -1; r < 5; r++) {
+    int jj = j0 + r;
+    if (jj < -NG || jj > n + NG - 1) return -NG - 4;
+    if (fabs(met(G, a, jj) - m) > 1e-12 * m) return -NG - 4;
+  }
   for (int r = 0; r < 4; r++) w[r] = orc_lambda(s - (double)(j0 + r));
+  if (hl) *hl = m;
   return j0;
 }
 
 static int marker_inside(const pgrid *G, const orc_desc *d, const double *X, int nm, int k) {
   for (int a = 0; a < G->dim; a++) {
     double w[4];
-    int j0 = support(G, d, a, X[a * nm + k], w);
+    int j0 = support(G, d, a, X[a * nm + k], w, NULL);
     if (j0 < 0 || j0 + 3 > G->n[a] - 1) return 0;
   }
   return 1;
@@ -593,7 +634,7 @@ static double interp_field(const pgrid *G, const orc_desc *d, const double *phi,
   int j0[3] = {0, 0, 0};
   int cnt[3] = {1, 1, 1};
   for (int a = 0; a < G->dim; a++) {
-    j0[a] = support(G, d, a, X[a * nm + k], w[a]);
+    j0[a] = support(G, d, a, X[a * nm + k], w[a], NULL);
     cnt[a] = 4;
   }
   double acc = 0.0;
@@ -610,8 +651,6 @@ static int ib_source(const pgrid *G, const orc_desc *d, const double *u, int nm,
                      double *rate) {
   int dim = G->dim, nv = G->nv;
   size_t Nu = (size_t)G->n[0] * G->n[1] * G->n[2];
-  double hprod = 1.0;
-  for (int a = 0; a < dim; a++) hprod *= G->h[a];
   for (int k = 0; k < nm; k++)
     if (!marker_inside(G, d, X, nm, k)) return ORC_ERR_BOUNDS;
   double *f = calloc((size_t)3 * Nu, sizeof(double));
@@ -628,9 +667,12 @@ static int ib_source(const pgrid *G, const orc_desc *d, const double *u, int nm,
   for (int k = 0; k < nm; k++) {
     double w[3][4] = {{1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}};
     int j0[3] = {0, 0, 0}, cnt[3] = {1, 1, 1};
+    double hprod = 1.0; /* the delta's h^d at the marker (Eq. 10) */
     for (int a = 0; a < dim; a++) {
-      j0[a] = support(G, d, a, X[a * nm + k], w[a]);
+      double hl;
+      j0[a] = support(G, d, a, X[a * nm + k], w[a], &hl);
       cnt[a] = 4;
+      hprod *= hl;
     }
     for (int r2 = 0; r2 < cnt[2]; r2++)
       for (int r1 = 0; r1 < cnt[1]; r1++)
@@ -838,16 +880,17 @@ int orc_spread_scalar(const orc_desc *d, int nm, const double *X, const double *
   pgrid G;
   pgrid_init(&G, d);
   size_t Nu = (size_t)G.n[0] * G.n[1] * G.n[2];
-  double hprod = 1.0;
-  for (int a = 0; a < d->dim; a++) hprod *= G.h[a];
   for (size_t o = 0; o < Nu; o++) f[o] = 0.0;
   for (int k = 0; k < nm; k++) {
     if (!marker_inside(&G, d, X, nm, k)) return ORC_ERR_BOUNDS;
     double w[3][4] = {{1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}};
     int j0[3] = {0, 0, 0}, cnt[3] = {1, 1, 1};
+    double hprod = 1.0;
     for (int a = 0; a < d->dim; a++) {
-      j0[a] = support(&G, d, a, X[a * nm + k], w[a]);
+      double hl;
+      j0[a] = support(&G, d, a, X[a * nm + k], w[a], &hl);
       cnt[a] = 4;
+      hprod *= hl;
     }
     for (int r2 = 0; r2 < cnt[2]; r2++)
       for (int r1 = 0; r1 < cnt[1]; r1++)

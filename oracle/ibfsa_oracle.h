@@ -25,6 +25,11 @@ typedef struct {
   /* 0: component-wise reconstruction of the split fluxes; 1: characteristic-wise, projected on
    * the eigenvectors of the Euler flux Jacobian at the Roe average of the two cells of each face */
   int charwise;
+  /* stretched (non-uniform) grid, per direction; NULL: uniform.  Node coordinates x_i and the
+   * metric dx/dxi at the nodes for i = -4 .. n+3, stored at i + 4 (n + 8 entries), of a mapping
+   * x(xi) of a computational coordinate with unit spacing per cell.  Immersed-boundary markers
+   * and probes must have their four-point support where the metric is constant. */
+  const double *xnode[3], *xmetric[3];
 } orc_desc;
 
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_BOUNDS = -4, ORC_ERR_NOMEM = -7 };

@@ -55,6 +55,8 @@ class OrcDesc(ctypes.Structure):
         ("src_xc", ctypes.c_double * 3),
         ("time", ctypes.c_double),
         ("charwise", ctypes.c_int),
+        ("xnode", ctypes.POINTER(ctypes.c_double) * 3),
+        ("xmetric", ctypes.POINTER(ctypes.c_double) * 3),
     ]
 
 
@@ -84,7 +86,9 @@ def lib():
     return _lib
 
 
-def desc(spec, t: float = 0.0, charwise: bool = False) -> OrcDesc:
+def desc(spec, t: float = 0.0, charwise: bool = False, stretch=None) -> OrcDesc:
+    """The oracle's descriptor.  stretch: None (uniform) or, per direction, None or a pair
+    (x nodes, dx/dxi at the nodes) over the padded range i = -4 .. n+3."""
     d = OrcDesc()
     d.dim = spec.dim
     for a in range(3):
@@ -109,6 +113,17 @@ def desc(spec, t: float = 0.0, charwise: bool = False) -> OrcDesc:
         d.src_xc[a] = float(spec.src_xc[a])
     d.time = float(t)
     d.charwise = 1 if (charwise or getattr(spec, "charwise", False)) else 0
+    d._keep = []
+    if stretch is not None:
+        for a, pair in enumerate(stretch):
+            if pair is None or a >= spec.dim:
+                continue
+            xn, xm = (np.ascontiguousarray(v, dtype=np.float64) for v in pair)
+            if xn.shape != (spec.n[a] + 8,) or xm.shape != (spec.n[a] + 8,):
+                raise ValueError(f"direction {a}: node and metric arrays need n + 8 entries")
+            d._keep += [xn, xm]
+            d.xnode[a] = xn.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            d.xmetric[a] = xm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return d
 
 
@@ -148,7 +163,8 @@ def _markers(spec, X, U, dS, xi):
     return nm, X, U, dS, xi
 
 
-def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0, charwise=False):
+def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0, charwise=False,
+        stretch=None):
     """RHS L(Q) + S of every interior cell at time t, shape [nv][nz][ny][nx] (charwise: the
     characteristic-wise reconstruction)."""
     Q = _f64(Q)
@@ -157,7 +173,7 @@ def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0, 
     F = np.zeros((spec.dim, max(nm, 1)))
     rate = np.zeros((spec.dim, max(nm, 1)))
     alpha = np.zeros(3)
-    d = desc(spec, t, charwise)
+    d = desc(spec, t, charwise, stretch)
     rc = lib().orc_rhs(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi), _p(L), _p(F),
                        _p(rate), _p(alpha))
     if rc != ORC_OK:
@@ -181,12 +197,13 @@ def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None):
     return L
 
 
-def rk3(spec, Q, dt, nsteps=1, X=None, U=None, dS=None, xi=None, t=0.0, charwise=False):
+def rk3(spec, Q, dt, nsteps=1, X=None, U=None, dS=None, xi=None, t=0.0, charwise=False,
+        stretch=None):
     """nsteps SSP-RK3 steps from time t; returns (Q, xi)."""
     Q = _f64(Q).copy()
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     xi = xi.copy() if xi is not None else None
-    d = desc(spec, t, charwise)
+    d = desc(spec, t, charwise, stretch)
     rc = lib().orc_rk3(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi), float(dt),
                        int(nsteps))
     if rc != ORC_OK:
@@ -194,11 +211,11 @@ def rk3(spec, Q, dt, nsteps=1, X=None, U=None, dS=None, xi=None, t=0.0, charwise
     return Q, xi
 
 
-def probe(spec, Q, xp):
+def probe(spec, Q, xp, stretch=None):
     Q = _f64(Q)
     xp = _f64(xp)
     out = np.zeros(xp.shape[1])
-    d = desc(spec)
+    d = desc(spec, stretch=stretch)
     rc = lib().orc_probe(ctypes.byref(d), _p(Q), xp.shape[1], _p(xp), _p(out))
     if rc != ORC_OK:
         raise RuntimeError(f"oracle probe failed: {rc}")

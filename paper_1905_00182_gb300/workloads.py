@@ -430,6 +430,37 @@ def sphere_source_3d(n: int = 512, markers: int = 20000, Re: float = 1e4, scheme
     return dict(spec=spec, Q=None, X=X, U=U, dS=dS, dt=dt, steps=2000, probes=pr)
 
 
+def stretched_axis(n: int, h0: float, h1: float, n_inner: int, n_trans: int,
+                   center: float = 0.0):
+    """One direction of the paper's non-uniform mesh (Sec. 2; Sec. 3.2): spacing h0 over the
+    n_inner central cells, a sinusoidal transition to h1 over n_trans cells on each side,
+    h1 beyond.  Mapping x(xi) of a computational coordinate xi with unit spacing per cell,
+    dx/dxi = h0 + (h1 - h0)(1 - cos(pi s))/2 on the transition (s from 0 to 1).
+    Returns (lo, hi, nodes, metric): the box and the node coordinates and dx/dxi at the nodes
+    i = -4 .. n+3 (n + 8 entries, node i at index i + 4)."""
+    a, t = 0.5 * n_inner, float(n_trans)
+
+    def X(z):  # x - center at distance z >= 0 from the middle, in cells
+        if z <= a:
+            return h0 * z
+        if z <= a + t:
+            d = z - a
+            return h0 * a + h0 * d + 0.5 * (h1 - h0) * (d - t / math.pi * math.sin(math.pi * d / t))
+        return h0 * a + h0 * t + 0.5 * (h1 - h0) * t + h1 * (z - a - t)
+
+    def H(z):
+        if z <= a:
+            return h0
+        if z <= a + t:
+            return h0 + 0.5 * (h1 - h0) * (1.0 - math.cos(math.pi * (z - a) / t))
+        return h1
+
+    xi = np.arange(-4, n + 4) + 0.5 - 0.5 * n
+    nodes = np.array([center + math.copysign(X(abs(z)), z) for z in xi])
+    metric = np.array([H(abs(z)) for z in xi])
+    return center - X(0.5 * n), center + X(0.5 * n), nodes, metric
+
+
 def rest_state(spec: GridSpec) -> np.ndarray:
     """Uniform free-stream state of the grid (host)."""
     Q = np.empty(spec.shape())
