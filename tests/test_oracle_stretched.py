@@ -66,6 +66,9 @@ def test_free_stream_preserved_on_a_stretched_grid(dim):
         Q[c] = q[c]
     L = O.rhs(spec, Q, stretch=[(ax[2], ax[3]) for ax in axes])
     assert np.max(np.abs(L)) == 0.0
+    # the characteristic projection keeps it too (each field's stencil is constant)
+    Lw = O.rhs(spec, Q, stretch=[(ax[2], ax[3]) for ax in axes], charwise=True)
+    assert np.max(np.abs(Lw)) <= 1e-13 * np.max(np.abs(q)) / 0.05
 
 
 def _smooth_periodic_axis(n, L=1.0, eps=0.15):
