@@ -19,7 +19,6 @@ For N > 1 (torchrun) every rank runs an independent replica of the workload (wea
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess

@@ -8,7 +8,6 @@
 * the trained form stays finite on an under-resolved pulse and is closer than TENO5 to the
   exact linear-acoustics solution of the Sec. 3.1 pulse.
 """
-import dataclasses
 import math
 
 import numpy as np

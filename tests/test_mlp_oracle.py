@@ -1,5 +1,4 @@
 """Pins of the FP64 oracle of the learned reconstruction weights."""
-import math
 
 import numpy as np
 import pytest
