@@ -8,9 +8,11 @@ right-hand sides (convective + viscous + penalty IB) with their RK combinations.
 
 Metric: cell-stage updates per second (cells x 3 / step time), device-timed with CUDA events on
 the library's stream, inputs resident in HBM (each state copy is 5.4 GB > 129 MB L2, so no L2
-flush is needed).  Printed as one JSON line with the dominant kernel's roofline, the HBM
-fraction of the whole stage, an end-to-end figure through the C ABI with host buffers, the
-FP64 CPU oracle timed on the host cores, and the SM clocks sampled during the timed region.
+flush is needed).  Printed as one JSON line with the roofline of the measured unit (one whole
+stage: 106.7 algorithmic bytes per cell against the HBM peak, its operations against the ALU
+peak), each kernel class's own roofline, an end-to-end figure through the C ABI with host
+buffers, the FP64 CPU oracle timed on the host cores, and the SM clocks sampled during the
+timed region.
 
   python bench.py [--gpus N --steps K --warmup W --n 512 --scheme teno5|weno5js --strict]
   python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
@@ -151,6 +153,35 @@ def bytes_per_cell_stage(dim=3):
     # fused minimum: stage 1 reads Qn and writes Q1; stages 2, 3 read Qn and Qs, write Qo
     nv = dim + 2
     return (2 * nv * 8 + 3 * nv * 8 + 3 * nv * 8) / 3.0
+
+
+def stage_roofline(bpc, cells, stage_ms, hbm_peak, peak_kind, flops, peak_tf, traffic):
+    """The roofline of the measured unit, one whole stage (every launch of a right-hand side
+    with its RK combination and the IB): its algorithmic bytes (bpc per cell) over the mean
+    stage time against the HBM peak, and, beside it, its algorithmic operations against the
+    ALU peak.  traffic: DRAM bytes of one stage from ncu (sum over its kernels), or None."""
+    achieved = bpc * cells / (stage_ms * 1e-3) / 1e9
+    alu = flops * cells / (stage_ms * 1e-3) / 1e12
+    return {"bound": "hbm", "kernel": "whole stage (all its launches)", "achieved": achieved,
+            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "peak_note": f"{peak_kind} copy bandwidth", "bytes_per_cell_stage": bpc,
+            "stage_ms": stage_ms, "alu_achieved_tflops": alu, "alu_peak_tflops": peak_tf,
+            "alu_frac": alu / peak_tf, "traffic": traffic}
+
+
+def stage_traffic(classes, precision):
+    """DRAM bytes of one stage at the full size: the sum over the stage's kernel classes of the
+    committed ncu bytes per launch (times launches per stage), or None when a class has no
+    figure taken on the current kernel source."""
+    total = 0.0
+    for k, v in classes.items():
+        if k == "probe":
+            continue
+        b = ncu_traffic(k, precision)
+        if b is None:
+            return None
+        total += b
+    return total
 
 
 # ------------------------------------------------------------------------------------------
@@ -610,13 +641,15 @@ def run_ours(args, rank, world, local_rank):
 
     classes = {k: v for k, v in prof.items() if v["timed"] > 0}
     dom = max(classes, key=lambda k: classes[k]["ms"])
-    roofline = kernel_roofline(dom)
-    roofline["traffic"] = ncu_traffic(dom, args.precision)
+    dominant = kernel_roofline(dom)
+    dominant["traffic"] = ncu_traffic(dom, args.precision)
     kernel_rooflines = {k: {kk: kernel_roofline(k)[kk] for kk in ("bound", "frac", "avg_launch_ms")}
                         for k in classes if k in fl or k in by}
+    kernel_rooflines["dominant"] = dominant
     stage_ms = ms / world / (3 * args.steps)
     bpc = bytes_per_cell_stage()
-    hbm_achieved = bpc * spec.cells / (stage_ms * 1e-3) / 1e9
+    roofline = stage_roofline(bpc, spec.cells, stage_ms, hbm_peak, peak_kind,
+                              fl["total"], peak_tf, stage_traffic(classes, args.precision))
     out = {
         "metric": "stage-RHS cell-updates/s", "value": value, "unit": "cell-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -624,13 +657,9 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
         "config": config_dict(args, args.n),
         "roofline": roofline,
-        "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": hbm_achieved / hbm_peak, "bytes_per_cell_stage": bpc,
-                         "peak_kind": peak_kind},
         "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if v["timed"]},
         "kernel_rooflines": kernel_rooflines,
         "flops_per_cell_stage": fl["total"],
-        "alu_frac_whole_stage": fl["total"] * spec.cells / (stage_ms * 1e-3) / 1e12 / peak_tf,
         "clocks": clk, "gpu_launches": gpu_launches, "device_status": status,
     }
     if compare is not None:

@@ -337,9 +337,10 @@ int ibfsa_fsi_step(ibfsa_grid *g, ibfsa_plate *p, double dt, int nsteps);
  * synchronisation of cudaMalloc/cudaFree, and foreign-language front ends that can only pass
  * pointers they were given.  It computes what ibfsa_rhs computes for a grid with this
  * descriptor, state Q [nv][nz][ny][nx], n_markers markers (X, U [dim][n_markers], dS
- * [n_markers], xi [dim][n_markers]) into L [nv][nz][ny][nx], and the marker forces of Eq. 7
- * into F [dim][n_markers] when F is not NULL; all pointers are device memory owned by the
- * caller.  status (device int, may be NULL) receives the IBFSA_STATUS_* bits of this call.
+ * [n_markers], xi [dim][n_markers]) into L [nv][nz][ny][nx], and the marker penalty forces (as
+ * ibfsa_rhs computes them) into F [dim][n_markers] when F is not NULL; all pointers are device
+ * memory owned by the caller.  status (device int, may be NULL) receives the IBFSA_STATUS_*
+ * bits of this call.
  * The descriptor must ask for IBFSA_FP64 arithmetic (strict or fast).
  * No grid object and no workspace: its scratch (padded state, primitives, viscous fluxes, split
  * speeds) lives in one static device array of IBFSA_NOALLOC_SCRATCH_BYTES that every GPU loading
@@ -347,7 +348,9 @@ int ibfsa_fsi_step(ibfsa_grid *g, ibfsa_plate *p, double dt, int nsteps);
  * rejected with IBFSA_ERR_WORKSPACE (about 50^3 cells in 3D with viscosity, 550^2 in 2D).
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a device
  * looks up the device address of that array (cudaGetSymbolAddress, with the device current)
- * and caches it; make that first call before any stream capture.  Every call shares the array
+ * and caches it for that device's current context; make that first call before any stream
+ * capture.  After a device reset (cudaDeviceReset) the new context's first call looks the
+ * address up again, and the same rule applies to it.  Every call shares the array
  * and it keeps the previous call's contents (what must start at zero is cleared by each call);
  * calls whose work overlaps on the GPU -- different streams, or different host threads -- race
  * on it and must be serialised by the caller.  Asynchronous on cuda_stream. */

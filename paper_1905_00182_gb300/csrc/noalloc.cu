@@ -11,7 +11,11 @@
 // The array's name is only a host-side stand-in in host code, not a device address: handing it
 // to a kernel would fault or, on a GPU that can reach host memory, silently touch the wrong
 // memory.  So the first call on each device looks up the real device address with
-// cudaGetSymbolAddress (with that device current) and caches it; later calls reuse it.
+// cudaGetSymbolAddress (with that device current) and caches it, keyed by the device and by the
+// unique id of its current context; later calls in the same context reuse it.  A context that
+// is destroyed and re-created (cudaDeviceReset) has a new id, so the first call after it looks
+// the address up again instead of handing the kernels a stale one.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -30,6 +34,31 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void *g_ptr[MAX_DEVICES] = {};
+unsigned long long g_ctx[MAX_DEVICES] = {};  // context id the cached address belongs to
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// unique id of the calling thread's current context (driver entry points fetched through the
+// runtime, so the library needs no link against the driver library)
+cudaError_t current_context_id(unsigned long long *id) {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_cur || !get_id) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+      return cudaErrorNotSupported;
+    get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 
 int fail(int code, const char *fmt, ...) {
   char msg[512];
@@ -43,20 +72,29 @@ int fail(int code, const char *fmt, ...) {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// device address of the static scratch on the current device (looked up once per device)
+// device address of the static scratch on the current device (looked up once per device and
+// context)
 int scratch_address(void **out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(IBFSA_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= MAX_DEVICES) return fail(IBFSA_ERR_ARG, "device %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ptr[dev]) {
+  unsigned long long ctx = 0;
+  // no current context yet (a fresh thread before any runtime call made one): the symbol lookup
+  // below creates the primary context; its id is then read again
+  bool have_ctx = current_context_id(&ctx) == cudaSuccess;
+  if (!g_ptr[dev] || !have_ctx || g_ctx[dev] != ctx) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return fail(IBFSA_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s",
                   cudaGetErrorString(e));
+    e = current_context_id(&ctx);
+    if (e != cudaSuccess)
+      return fail(IBFSA_ERR_CUDA, "current context id: %s", cudaGetErrorString(e));
     g_ptr[dev] = p;
+    g_ctx[dev] = ctx;
   }
   *out = g_ptr[dev];
   return IBFSA_OK;

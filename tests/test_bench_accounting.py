@@ -69,3 +69,15 @@ def test_clock_record_parsing():
     c2 = object.__new__(bench.Clocks)
     c2.proc = None
     assert c2.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_stage_roofline_is_the_whole_stage_unit():
+    # 512^3 cells, 13.04 ms per stage: 106.7 B x 1.342e8 / 13.04 ms = 1.098 TB/s
+    cells = 512 ** 3
+    r = bench.stage_roofline(bench.bytes_per_cell_stage(), cells, 13.04, 6787.6, "measured",
+                             2691, 80.5, None)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert math.isclose(r["achieved"], 320.0 / 3.0 * cells / 13.04e-3 / 1e9)
+    assert math.isclose(r["frac"], r["achieved"] / 6787.6)
+    assert 0.16 < r["frac"] < 0.17
+    assert math.isclose(r["alu_frac"], 2691 * cells / 13.04e-3 / 1e12 / 80.5)
