@@ -19,7 +19,9 @@
  *      reconstruction of every component at every face (or, as an option, of every
  *      characteristic field at the face's Roe average), then -(Fhat_{i+1/2}-Fhat_{i-1/2})/h
  *                                                                (Sec. 2, Eq. 2 and the text
- *                                                                after Eq. 5)
+ *                                                                after Eq. 5); or the learned
+ *      weights: TENO5's cut-off decides, and where it keeps all three candidates (and the
+ *      stencil is not flat) a network gives their weights, the face value taken in delta form
  *   4. viscous term: 4th-order central gradients of u, tau_ij, b = u.tau (no heat flux),
  *      then (1/Re) * 4th-order central divergence of [0, tau_.j, b_j] (Eq. 2-5)
  *   5. optional sponge: L -= sigma(n) (Q - Q_inf); optional periodic Gaussian pressure source
@@ -115,8 +117,116 @@ double orc_teno5(const double *v) {
   return (w[0] / sw) * q[0] + (w[1] / sw) * q[1] + (w[2] / sw) * q[2];
 }
 
-static double recon(int scheme, const double *v) {
-  return scheme == 1 ? orc_teno5(v) : orc_weno5js(v);
+/* ----------------------------------------------------------------------------------------- */
+/* Learned reconstruction weights (the learned-weight variant of the fifth-order              */
+/* reconstruction): TENO5 decides where the data is smooth; there a small network maps the     */
+/* normalised stencil to the three weights of the same third-order candidates.                */
+/* ----------------------------------------------------------------------------------------- */
+/* nearest bfloat16 (ties to even) of x, through its nearest float */
+static double bf16_round(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, sizeof(u));
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    uint32_t lsb = (u >> 16) & 1u;
+    u = (u + 0x7fffu + lsb) & 0xffff0000u;
+    memcpy(&f, &u, sizeof(f));
+  }
+  return (double)f;
+}
+
+/* gelu, tanh form: z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) */
+static double gelu(double z) {
+  const double k = 0.79788456080286535588; /* sqrt(2/pi) */
+  return 0.5 * z * (1.0 + tanh(k * (z + 0.044715 * z * z * z)));
+}
+
+/* one dense layer: out[i] = b[i] + sum_j W[i][j] in[j], W row-major (nout x nin) */
+static void dense(const double *W, const double *b, int nout, int nin, const double *in,
+                  double *out) {
+  for (int i = 0; i < nout; i++) {
+    double s = b[i];
+    for (int j = 0; j < nin; j++) s = s + W[i * nin + j] * in[j];
+    out[i] = s;
+  }
+}
+
+/* the network's three softmax weights for the normalised stencil x[5] */
+void orc_mlp_weights(const double *theta, int round_act, const double *x, double w[3]) {
+  const double *W1 = theta, *b1 = W1 + 160, *W2 = b1 + 32, *b2 = W2 + 1024, *W3 = b2 + 32,
+               *b3 = W3 + 1024, *W4 = b3 + 32, *b4 = W4 + 96;
+  double a0[5], z[32], h1[32], h2[32], h3[32], l[3];
+  for (int j = 0; j < 5; j++) a0[j] = round_act ? bf16_round(x[j]) : x[j];
+  dense(W1, b1, 32, 5, a0, z);
+  for (int i = 0; i < 32; i++) h1[i] = round_act ? bf16_round(gelu(z[i])) : gelu(z[i]);
+  dense(W2, b2, 32, 32, h1, z);
+  for (int i = 0; i < 32; i++) h2[i] = round_act ? bf16_round(gelu(z[i])) : gelu(z[i]);
+  dense(W3, b3, 32, 32, h2, z);
+  for (int i = 0; i < 32; i++) h3[i] = round_act ? bf16_round(gelu(z[i])) : gelu(z[i]);
+  dense(W4, b4, 3, 32, h3, l);
+  double m = l[0] > l[1] ? l[0] : l[1];
+  if (l[2] > m) m = l[2];
+  double e0 = exp(l[0] - m), e1 = exp(l[1] - m), e2 = exp(l[2] - m);
+  double s = e0 + e1 + e2;
+  w[0] = e0 / s;
+  w[1] = e1 / s;
+  w[2] = e2 / s;
+}
+
+/* TENO5's cut-off decision alone: 1 when every stencil is kept (the constants of orc_teno5) */
+static int teno5_all_kept(const double *v) {
+  double q[3], beta[3], g[3];
+  candidates(v, q, beta);
+  const double eps = 1e-40, CT = 1e-5;
+  double tau5 = fabs(beta[0] - beta[2]);
+  for (int k = 0; k < 3; k++) {
+    double x = 1.0 + tau5 / (beta[k] + eps);
+    double x2 = x * x;
+    g[k] = x2 * x2 * x2;
+  }
+  double s = g[0] + g[1] + g[2];
+  for (int k = 0; k < 3; k++)
+    if (!(g[k] / s >= CT)) return 0;
+  return 1;
+}
+
+/* Learned reconstruction at the face from v[5] (upwind-ordered); *used (may be NULL) = 1 when
+ * the network supplied the weights, 0 when TENO5 did. */
+double orc_learned_recon(const double *theta, int round_act, double floor_amp, const double *v,
+                         int *used) {
+  if (used) *used = 0;
+  if (!teno5_all_kept(v)) return orc_teno5(v);
+  double amp = 0.0;
+  for (int j = 0; j < 5; j++) {
+    double dj = fabs(v[j] - v[2]);
+    if (dj > amp) amp = dj;
+  }
+  if (!(amp > floor_amp)) return orc_teno5(v);
+  double x[5], q[3], beta[3], w[3];
+  for (int j = 0; j < 5; j++) x[j] = (v[j] - v[2]) / amp;
+  candidates(x, q, beta); /* candidates of the normalised stencil (x_2 = 0) */
+  orc_mlp_weights(theta, round_act, x, w);
+  if (used) *used = 1;
+  return v[2] + amp * (w[0] * q[0] + w[1] * q[1] + w[2] * q[2]);
+}
+
+/* reconstructions that used the network / all learned reconstructions of the last orc_rhs */
+static long long g_mlp_used, g_mlp_seen;
+
+void orc_mlp_counts(long long *used, long long *seen) {
+  *used = g_mlp_used;
+  *seen = g_mlp_seen;
+}
+
+static double recon_d(const orc_desc *d, const double *v) {
+  if (d->scheme == 2) {
+    int used = 0;
+    double r = orc_learned_recon(d->mlp_params, d->mlp_round, d->mlp_floor, v, &used);
+    g_mlp_used += used;
+    g_mlp_seen += 1;
+    return r;
+  }
+  return d->scheme == 1 ? orc_teno5(v) : orc_weno5js(v);
 }
 
 /* ----------------------------------------------------------------------------------------- */
@@ -291,7 +401,7 @@ static void convective(const pgrid *G, const orc_desc *d, const double *W, const
               vp[r] = fp[m - 2 + r + NG];   /* f+_{m-2..m+2} */
               vm[r] = fm[m + 3 - r + NG];   /* f-_{m+3..m-1} (mirrored) */
             }
-            Fh[m + 1] = recon(d->scheme, vp) + recon(d->scheme, vm);
+            Fh[m + 1] = recon_d(d, vp) + recon_d(d, vm);
           }
           for (int m = 0; m < na; m++) {
             int I[3];
@@ -436,7 +546,7 @@ static int convective_charwise(const pgrid *G, const orc_desc *d, const double *
               vp[r] = sp;
               vm[r] = sm;
             }
-            h[k] = recon(d->scheme, vp) + recon(d->scheme, vm);
+            h[k] = recon_d(d, vp) + recon_d(d, vm);
           }
           for (int c = 0; c < nv; c++) {
             double s = 0.0;
@@ -703,6 +813,8 @@ static int ib_source(const pgrid *G, const orc_desc *d, const double *u, int nm,
 /* ----------------------------------------------------------------------------------------- */
 static int check_desc(const orc_desc *d) {
   if (!d || (d->dim != 2 && d->dim != 3)) return ORC_ERR_ARG;
+  if (d->scheme < 0 || d->scheme > 2) return ORC_ERR_ARG;
+  if (d->scheme == 2 && !d->mlp_params) return ORC_ERR_ARG;
   for (int a = 0; a < d->dim; a++)
     if (d->n[a] < 1 || !(d->hi[a] > d->lo[a])) return ORC_ERR_ARG;
   if (d->dim == 2 && d->n[2] != 1) return ORC_ERR_ARG;
@@ -757,6 +869,8 @@ static int rhs_impl(const orc_desc *d, const double *Q, int nm, const double *X,
     for (int a = 0; a < 3; a++) alpha[a] = alpha_in[a];
   if (alpha_out) for (int a = 0; a < 3; a++) alpha_out[a] = alpha[a];
   for (size_t o = 0; o < (size_t)G.nv * Nu; o++) L[o] = 0.0;
+  g_mlp_used = 0;
+  g_mlp_seen = 0;
   if (d->charwise) {
     rc = convective_charwise(&G, d, W, u, p, alpha, L);
     if (rc) { free(W); free(rho); free(u); free(p); return rc; }

@@ -30,6 +30,16 @@ typedef struct {
    * x(xi) of a computational coordinate with unit spacing per cell.  Immersed-boundary markers
    * and probes must have their four-point support where the metric is constant. */
   const double *xnode[3], *xmetric[3];
+  /* learned reconstruction weights (scheme 2): where TENO5 keeps all three stencils and the
+   * stencil amplitude amp = max_j |v_j - v_2| exceeds mlp_floor, the weights of the candidates
+   * come from the network 5 -> 32 -> 32 -> 32 (gelu) -> 3 (softmax) on x = (v - v_2)/amp, and
+   * the face value is v_2 + amp sum_k w_k qhat_k(x); elsewhere TENO5.  mlp_params: 2403
+   * parameters [W1 (32x5), b1, W2 (32x32), b2, W3 (32x32), b3, W4 (3x32), b4], rows = output
+   * units, used as given; mlp_round = 1 rounds the network's input and hidden activations to
+   * bfloat16 (the operand precision of the tensor-core products), accumulating in FP64. */
+  const double *mlp_params;
+  int mlp_round;
+  double mlp_floor;
 } orc_desc;
 
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_BOUNDS = -4, ORC_ERR_NOMEM = -7 };

@@ -57,6 +57,9 @@ class OrcDesc(ctypes.Structure):
         ("charwise", ctypes.c_int),
         ("xnode", ctypes.POINTER(ctypes.c_double) * 3),
         ("xmetric", ctypes.POINTER(ctypes.c_double) * 3),
+        ("mlp_params", ctypes.POINTER(ctypes.c_double)),
+        ("mlp_round", ctypes.c_int),
+        ("mlp_floor", ctypes.c_double),
     ]
 
 
@@ -83,12 +86,34 @@ def lib():
         _lib.orc_wavespeeds.argtypes = [ctypes.POINTER(OrcDesc), _D, _D]
         _lib.orc_interp_scalar.argtypes = [ctypes.POINTER(OrcDesc), _D, ctypes.c_int, _D, _D]
         _lib.orc_spread_scalar.argtypes = [ctypes.POINTER(OrcDesc), ctypes.c_int, _D, _D, _D, _D]
+        _lib.orc_mlp_weights.restype = None
+        _lib.orc_mlp_weights.argtypes = [_D, ctypes.c_int, _D, _D]
+        _lib.orc_learned_recon.restype = ctypes.c_double
+        _lib.orc_learned_recon.argtypes = [_D, ctypes.c_int, ctypes.c_double, _D,
+                                           ctypes.POINTER(ctypes.c_int)]
+        _lib.orc_mlp_counts.restype = None
+        _lib.orc_mlp_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong)] * 2
     return _lib
 
 
-def desc(spec, t: float = 0.0, charwise: bool = False, stretch=None) -> OrcDesc:
+class Learned:
+    """The learned reconstruction weights as the oracle evaluates them: the 2403 parameters used
+    as given (pass the bfloat16-rounded values the tensor cores see), the network's input and
+    hidden activations rounded to bfloat16 when round_act, and the guard's amplitude floor."""
+
+    def __init__(self, params, round_act: bool = True, floor: float = 1e-9):
+        self.params = np.ascontiguousarray(params, dtype=np.float64)
+        if self.params.shape != (2403,):
+            raise ValueError("the network has 2403 parameters")
+        self.round_act = bool(round_act)
+        self.floor = float(floor)
+
+
+def desc(spec, t: float = 0.0, charwise: bool = False, stretch=None, mlp=None) -> OrcDesc:
     """The oracle's descriptor.  stretch: None (uniform) or, per direction, None or a pair
-    (x nodes, dx/dxi at the nodes) over the padded range i = -4 .. n+3."""
+    (x nodes, dx/dxi at the nodes) over the padded range i = -4 .. n+3.  mlp: a Learned (the
+    learned-weight scheme), else the spec's WENO5-JS or TENO5 (TENO5 for the learned scheme:
+    its end-to-end oracle)."""
     d = OrcDesc()
     d.dim = spec.dim
     for a in range(3):
@@ -114,6 +139,12 @@ def desc(spec, t: float = 0.0, charwise: bool = False, stretch=None) -> OrcDesc:
     d.time = float(t)
     d.charwise = 1 if (charwise or getattr(spec, "charwise", False)) else 0
     d._keep = []
+    if mlp is not None:
+        d.scheme = 2
+        d._keep.append(mlp.params)
+        d.mlp_params = mlp.params.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.mlp_round = 1 if mlp.round_act else 0
+        d.mlp_floor = mlp.floor
     if stretch is not None:
         for a, pair in enumerate(stretch):
             if pair is None or a >= spec.dim:
@@ -164,16 +195,16 @@ def _markers(spec, X, U, dS, xi):
 
 
 def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0, charwise=False,
-        stretch=None):
+        stretch=None, mlp=None):
     """RHS L(Q) + S of every interior cell at time t, shape [nv][nz][ny][nx] (charwise: the
-    characteristic-wise reconstruction)."""
+    characteristic-wise reconstruction; mlp: a Learned, the learned-weight scheme)."""
     Q = _f64(Q)
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     L = np.zeros_like(Q)
     F = np.zeros((spec.dim, max(nm, 1)))
     rate = np.zeros((spec.dim, max(nm, 1)))
     alpha = np.zeros(3)
-    d = desc(spec, t, charwise, stretch)
+    d = desc(spec, t, charwise, stretch, mlp)
     rc = lib().orc_rhs(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi), _p(L), _p(F),
                        _p(rate), _p(alpha))
     if rc != ORC_OK:
@@ -183,13 +214,13 @@ def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0, 
     return L
 
 
-def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None):
+def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None, mlp=None):
     """Right-hand side with the split speeds alpha[3] supplied (for crops of a large state)."""
     Q = _f64(Q)
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     L = np.zeros_like(Q)
     a = _f64(np.asarray(alpha, dtype=np.float64).reshape(3))
-    d = desc(spec)
+    d = desc(spec, mlp=mlp)
     rc = lib().orc_rhs_given_alpha(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi),
                                    _p(L), _p(a))
     if rc != ORC_OK:
@@ -198,12 +229,12 @@ def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None):
 
 
 def rk3(spec, Q, dt, nsteps=1, X=None, U=None, dS=None, xi=None, t=0.0, charwise=False,
-        stretch=None):
+        stretch=None, mlp=None):
     """nsteps SSP-RK3 steps from time t; returns (Q, xi)."""
     Q = _f64(Q).copy()
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     xi = xi.copy() if xi is not None else None
-    d = desc(spec, t, charwise, stretch)
+    d = desc(spec, t, charwise, stretch, mlp)
     rc = lib().orc_rk3(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi), float(dt),
                        int(nsteps))
     if rc != ORC_OK:
@@ -465,3 +496,43 @@ def char_eigen(dim, gamma, a, Ql, Qr=None):
     if rc != ORC_OK:
         raise RuntimeError(f"oracle eigen-system failed: {rc}")
     return R, L, lam
+
+
+# --------------------------------------------------------------------------------------------
+# learned reconstruction weights (scheme 2 of the oracle)
+# --------------------------------------------------------------------------------------------
+
+def mlp_weights(params, x, round_act=True):
+    """The network's three softmax weights for normalised stencils x [B, 5]."""
+    p = _f64(np.asarray(params))
+    x = np.atleast_2d(_f64(np.asarray(x)))
+    out = np.zeros((x.shape[0], 3))
+    for b in range(x.shape[0]):
+        xb = np.ascontiguousarray(x[b])
+        wb = np.zeros(3)
+        lib().orc_mlp_weights(_p(p), 1 if round_act else 0, _p(xb), _p(wb))
+        out[b] = wb
+    return out
+
+
+def learned_recon(mlp, v):
+    """The learned reconstruction of stencils v [B, 5] (upwind-ordered): (face values, mask of
+    the stencils whose weights came from the network)."""
+    v = np.atleast_2d(_f64(np.asarray(v)))
+    out = np.zeros(v.shape[0])
+    used = np.zeros(v.shape[0], dtype=bool)
+    u = ctypes.c_int(0)
+    for b in range(v.shape[0]):
+        vb = np.ascontiguousarray(v[b])
+        out[b] = lib().orc_learned_recon(_p(mlp.params), 1 if mlp.round_act else 0, mlp.floor,
+                                         _p(vb), ctypes.byref(u))
+        used[b] = bool(u.value)
+    return out, used
+
+
+def mlp_counts():
+    """(reconstructions that used the network, all reconstructions) of the last oracle
+    right-hand side of the learned scheme."""
+    a, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    lib().orc_mlp_counts(ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
