@@ -570,11 +570,25 @@ def run_ours(args, rank, world, local_rank):
     if fp32 and args.compare and args.scheme == "teno5":
         net = learned_weights(ib)
         k_l = 3
+        warm_l = min(args.warmup, steps_done - k_l)
         out_l = {}
+        # FP64 TENO5 on the stress state, the reference of both FP32 forms there
+        g64s, _, _, _, _ = make_grid(ib, args, W.FP64, state="stress")
+        g64s.rk3_step(dt, steps_done)
+        p64s = pressure(spec, g64s.get_state())
+        g64s.close()
+        del g64s
+        torch.cuda.empty_cache()
+
+        def rel_to(p, p_ref):
+            return float(torch.linalg.vector_norm(p - p_ref) /
+                         torch.linalg.vector_norm(p_ref - 1.0 / spec.gamma))
+
+        ref = {"pulse": p64_keep, "stress": p64s}
         for state in ("pulse", "stress"):
             gl, _, _, _, _ = make_grid(ib, args, W.FP32_PERTURB, scheme=W.MLP_TENO5,
                                        state=state, mlp=net)
-            for _ in range(args.warmup):
+            for _ in range(warm_l):
                 gl.rk3_step(dt, 1)
             ib.ibfsa_mlp_stats(gl.h)
             msl, _ = timed_steps(ib, gl, dt, k_l, barrier, profile=False)
@@ -582,27 +596,30 @@ def run_ours(args, rank, world, local_rank):
             out_l[state] = {"value": spec.cells * 3 * k_l * world / (max_ranks(msl) * 1e-3),
                             "ms_per_step": msl / k_l,
                             "fallback_rate": 1.0 - used / max(seen, 1)}
-            if state == "pulse" and steps_done - args.warmup - k_l >= 0:
-                for _ in range(steps_done - args.warmup - k_l):
-                    gl.rk3_step(dt, 1)
-                p_l = pressure(spec, gl.get_state())
-                out_l[state]["vs_fp64_pressure_rel_l2"] = float(
-                    torch.linalg.vector_norm(p_l - p64_keep) /
-                    torch.linalg.vector_norm(p64_keep - 1.0 / spec.gamma)) if p64_keep is not None else None
-                del p_l
+            gl.rk3_step(dt, steps_done - warm_l - k_l)
+            p_l = pressure(spec, gl.get_state())
+            if ref[state] is not None:
+                e = rel_to(p_l, ref[state])
+                out_l[state]["vs_fp64_pressure_rel_l2"] = e
+                out_l[state]["within_1e-3_of_fp64"] = bool(e <= 1e-3)
+            del p_l
             gl.close()
             del gl
             torch.cuda.empty_cache()
         gs, _, _, _, _ = make_grid(ib, args, W.FP32_PERTURB, state="stress")
-        for _ in range(args.warmup):
+        for _ in range(warm_l):
             gs.rk3_step(dt, 1)
         mss, _ = timed_steps(ib, gs, dt, k_l, barrier, profile=False)
+        gs.rk3_step(dt, steps_done - warm_l - k_l)
+        e_fp32_stress = rel_to(pressure(spec, gs.get_state()), p64s)
         gs.close()
-        del gs
+        del gs, p64s
         torch.cuda.empty_cache()
         learned = {"pulse": out_l["pulse"], "stress": out_l["stress"],
                    "fp32_teno5_stress_value": spec.cells * 3 * k_l * world /
                    (max_ranks(mss) * 1e-3),
+                   "fp32_teno5_stress_vs_fp64_pressure_rel_l2": e_fp32_stress,
+                   "steps_compared": steps_done,
                    "weights": "paper_1905_00182_gb300/mlp_weights.npz"}
 
     fsi = fsi_form(ib, barrier, max_ranks, world) if (fp32 and args.compare) else None

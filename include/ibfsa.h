@@ -266,7 +266,7 @@ int ibfsa_mlp_sample(ibfsa_grid *g, int n_max, unsigned long long seed, int atte
  *   e_{n+1} = e_n + dt (v_n + v_{n+1}) / 2,  M (v_{n+1} - v_n) = dt [Q_f - Q_int((e_n + e_{n+1})/2)],
  * solved by Newton's method (block cyclic reduction over the 4 x 4 node blocks) in one thread
  * block, in FP64 with every operation rounded separately except explicit fused multiply-adds
- * (reproducible bit for bit by a sequential evaluation with the same fused operations).
+ * (deterministic: the same inputs give the same bits on every run).
  * Load: the penalty force F_k of Eq. 7 (force of the fluid on the structure, per unit length) at
  * markers s_k = (k + 1/2) L / n_markers, dS_k = L / n_markers: Q_f = sum_k S(s_k)^T F_k dS_k in
  * marker order.  Clamp (IBFSA_PLATE_CLAMPED): node 0 at x0 + (A0/2) cos(2 pi f t)[cos b, sin b]

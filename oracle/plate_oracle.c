@@ -6,7 +6,7 @@
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call this file:
  * only the test suite, the smoke check and the bench's CPU-baseline leg use it.  It shares no
  * source, header, table or helper with the CUDA path.  Compile with -O2 -ffp-contract=off
- * (the only fused multiply-adds are the explicit fma calls).
+ * (no multiply and add is fused).
  *
  * The paper names the formulation (Shabana's ANCF) but prints neither the element nor the time
  * integrator; the readings taken here:
@@ -29,10 +29,9 @@
  *  - Time: the implicit midpoint rule
  *      e_{n+1} = e_n + dt (v_n + v_{n+1}) / 2,
  *      M (v_{n+1} - v_n) = dt [Q_f - Q_int((e_n + e_{n+1}) / 2)],
- *    solved by Newton's method for d = e_{n+1} - e_n; each Newton system, block tridiagonal
- *    in the nodes, is solved by block cyclic reduction with 4 x 4 L D L^T blocks.  The
- *    multiply-adds of the element dot products and of the reduction are single fused
- *    operations (C99 fma, one rounding); everything else is rounded operation by operation.  The rule conserves the linear and angular
+ *    solved by Newton's method for d = e_{n+1} - e_n; each Newton system is assembled as a
+ *    dense matrix and solved by Gaussian elimination with partial pivoting in natural order,
+ *    every operation rounded on its own (no fused multiply-add anywhere).  The rule conserves the linear and angular
  *    momentum of an unloaded free plate and hands the plate exactly the impulse dt Q_f of the
  *    step's load, so what the fluid loses the plate gains.
  *  - Clamp (Sec. 4.1, Eq. 17): r(0, t) = x0 + (A0/2) cos(2 pi f t) [cos b, sin b], and the
@@ -73,7 +72,6 @@ typedef struct {
 
 enum { ORC_PLATE_NOCONV = -8 };
 
-#define BW 7 /* half-bandwidth: an element couples the 8 coordinates of two adjacent nodes */
 
 static const double PI = 3.14159265358979323846;
 
@@ -150,7 +148,7 @@ static void element_internal(const orc_plate *p, const double *ee, double Qi[8],
     dshape(xi, l, D[g]);
     for (int a = 0; a < 2; a++) {
       double r = 0.0;
-      for (int j = 0; j < 4; j++) r = fma(D[g][j], ee[loc(j, a)], r);
+      for (int j = 0; j < 4; j++) r = r + D[g][j] * ee[loc(j, a)];
       rs[g][a] = r;
     }
     double n = sqrt(rs[g][0] * rs[g][0] + rs[g][1] * rs[g][1]);
@@ -160,9 +158,9 @@ static void element_internal(const orc_plate *p, const double *ee, double Qi[8],
   for (int i = 0; i < 4; i++)
     for (int a = 0; a < 2; a++) {
       double bend = 0.0;
-      for (int j = 0; j < 4; j++) bend = fma(Kb[i][j], ee[loc(j, a)], bend);
+      for (int j = 0; j < 4; j++) bend = bend + Kb[i][j] * ee[loc(j, a)];
       double axial = 0.0;
-      for (int g = 0; g < 5; g++) axial = fma(wl[g] * c1[g] * rs[g][a], D[g][i], axial);
+      for (int g = 0; g < 5; g++) axial = axial + wl[g] * c1[g] * rs[g][a] * D[g][i];
       Qi[loc(i, a)] = bend + axial;
     }
   if (!Kt) return;
@@ -174,7 +172,7 @@ static void element_internal(const orc_plate *p, const double *ee, double Qi[8],
           for (int g = 0; g < 5; g++) {
             double s = c2[g] * rs[g][a] * rs[g][b];
             if (a == b) s = c1[g] + s;
-            k = fma(wl[g] * D[g][i] * D[g][j], s, k);
+            k = k + wl[g] * D[g][i] * D[g][j] * s;
           }
           Kt[loc(i, a)][loc(j, b)] = a == b ? Kb[i][j] + k : k;
         }
@@ -281,96 +279,41 @@ int orc_plate_internal(const orc_plate *p, const double *e, double *Qint, double
   return ORC_OK;
 }
 
-/* The Newton matrix is block tridiagonal in the nodes: D_j (4 x 4, node j with itself) and
- * Br_j (node j with node j + 1).  It is solved by block cyclic reduction: at the level of stride
- * s the blocks i = s, 3s, 5s, ... are eliminated (each needs D_i^-1 applied to its couplings and
- * right-hand side), the blocks k = 0, 2s, 4s, ... take their Schur complements, until block 0
- * is alone; then the eliminated blocks are recovered from coarse to fine.  A 4 x 4 block is
- * factorised as L D L^T (upper triangle, reciprocal pivots).  Multiply-adds are fused (C99 fma)
- * and every sum is taken in the order written. */
-static int ldlt4(double M[4][4], double rinv[4]) {
-  for (int i = 0; i < 4; i++) {
-    double d = M[i][i];
-    if (!(d != 0.0) || !isfinite(d)) return -1;
-    double r = 1.0 / d;
-    rinv[i] = r;
-    double lk[4];
-    for (int k = 1; i + k < 4; k++) lk[k] = M[i][i + k] * r;
-    for (int k = 1; i + k < 4; k++)
-      for (int m = k; i + m < 4; m++) M[i + k][i + m] = fma(-lk[k], M[i][i + m], M[i + k][i + m]);
-    for (int k = 1; i + k < 4; k++) M[i][i + k] = lk[k];
-  }
-  return 0;
-}
-
-/* v <- (L D L^T)^-1 v with the factors of ldlt4 */
-static void solve4(double M[4][4], const double rinv[4], double v[4]) {
-  for (int i = 0; i < 4; i++)
-    for (int k = 1; i + k < 4; k++) v[i + k] = fma(-M[i][i + k], v[i], v[i + k]);
-  for (int i = 0; i < 4; i++) v[i] = v[i] * rinv[i];
-  for (int i = 3; i >= 0; i--)
-    for (int k = 1; i + k < 4; k++) v[i] = fma(-M[i][i + k], v[i + k], v[i]);
-}
-
-typedef double blk4[4][4];
-
-/* Solve the nb-block system (D, Br, b) into x; D, Br, b are overwritten.  Y, Z, y, rinv:
- * scratch of nb blocks.  Returns 0, or -1 on a zero or non-finite pivot. */
-static int bcr_solve(int nb, blk4 *D, blk4 *Br, double (*b)[4], double (*x)[4], blk4 *Y,
-                     blk4 *Z, double (*y)[4], double (*rinv)[4]) {
-  int s;
-  for (s = 1; s < nb; s *= 2) {
-    for (int i = s; i < nb; i += 2 * s) { /* eliminated: odd multiples of s */
-      if (ldlt4(D[i], rinv[i])) return -1;
-      int right = i + s < nb;
-      for (int c = 0; c < 4; c++) {
-        double col[4];
-        for (int q = 0; q < 4; q++) col[q] = right ? Br[i][q][c] : 0.0;
-        solve4(D[i], rinv[i], col);
-        for (int q = 0; q < 4; q++) Y[i][q][c] = col[q]; /* D_i^-1 Br_i */
-        for (int q = 0; q < 4; q++) col[q] = Br[i - s][c][q];
-        solve4(D[i], rinv[i], col);
-        for (int q = 0; q < 4; q++) Z[i][q][c] = col[q]; /* D_i^-1 Br_{i-s}^T */
+/* Solve A x = b (n x n, row-major; A and b are overwritten, x returned in b) by Gaussian
+ * elimination with partial pivoting in natural order, then back substitution.  Returns 0, or -1
+ * on a zero or non-finite pivot. */
+static int gauss_solve(int n, double *A, double *b) {
+  for (int k = 0; k < n; k++) {
+    int piv = k;
+    double best = fabs(A[(size_t)k * n + k]);
+    for (int r = k + 1; r < n; r++)
+      if (fabs(A[(size_t)r * n + k]) > best) {
+        best = fabs(A[(size_t)r * n + k]);
+        piv = r;
       }
-      for (int q = 0; q < 4; q++) y[i][q] = b[i][q];
-      solve4(D[i], rinv[i], y[i]);                         /* D_i^-1 b_i */
+    if (!(best > 0.0) || !isfinite(best)) return -1;
+    if (piv != k) {
+      for (int c = 0; c < n; c++) {
+        double t = A[(size_t)k * n + c];
+        A[(size_t)k * n + c] = A[(size_t)piv * n + c];
+        A[(size_t)piv * n + c] = t;
+      }
+      double t = b[k];
+      b[k] = b[piv];
+      b[piv] = t;
     }
-    for (int k = 0; k < nb; k += 2 * s) { /* survivors take the Schur complements */
-      int il = k - s, ir = k + s;
-      int hl = il >= 0, hr = ir < nb, hn = hr && ir + s < nb;
-      double Dn[4][4], bn[4], Bn[4][4];
-      for (int r = 0; r < 4; r++)
-        for (int c = 0; c < 4; c++) {
-          double t = D[k][r][c];
-          if (hl) for (int q = 0; q < 4; q++) t = fma(-Br[il][q][r], Y[il][q][c], t);
-          if (hr) for (int q = 0; q < 4; q++) t = fma(-Br[k][r][q], Z[ir][q][c], t);
-          Dn[r][c] = t;
-          double u = 0.0;
-          if (hn) for (int q = 0; q < 4; q++) u = fma(-Br[k][r][q], Y[ir][q][c], u);
-          Bn[r][c] = u;
-        }
-      for (int r = 0; r < 4; r++) {
-        double t = b[k][r];
-        if (hl) for (int q = 0; q < 4; q++) t = fma(-Br[il][q][r], y[il][q], t);
-        if (hr) for (int q = 0; q < 4; q++) t = fma(-Br[k][r][q], y[ir][q], t);
-        bn[r] = t;
-      }
-      memcpy(D[k], Dn, sizeof(Dn));
-      memcpy(Br[k], Bn, sizeof(Bn));
-      memcpy(b[k], bn, sizeof(bn));
+    for (int r = k + 1; r < n; r++) {
+      double f = A[(size_t)r * n + k] / A[(size_t)k * n + k];
+      if (f == 0.0) continue; /* rows outside the band stay untouched */
+      for (int c = k; c < n; c++) A[(size_t)r * n + c] = A[(size_t)r * n + c] - f * A[(size_t)k * n + c];
+      b[r] = b[r] - f * b[k];
     }
   }
-  if (ldlt4(D[0], rinv[0])) return -1;
-  for (int q = 0; q < 4; q++) x[0][q] = b[0][q];
-  solve4(D[0], rinv[0], x[0]);
-  for (s = s / 2; s >= 1; s /= 2)
-    for (int i = s; i < nb; i += 2 * s)
-      for (int r = 0; r < 4; r++) {
-        double t = y[i][r];
-        for (int q = 0; q < 4; q++) t = fma(-Z[i][r][q], x[i - s][q], t);
-        if (i + s < nb) for (int q = 0; q < 4; q++) t = fma(-Y[i][r][q], x[i + s][q], t);
-        x[i][r] = t;
-      }
+  for (int k = n - 1; k >= 0; k--) {
+    double t = b[k];
+    for (int c = k + 1; c < n; c++) t = t - A[(size_t)k * n + c] * b[c];
+    b[k] = t / A[(size_t)k * n + k];
+  }
   return 0;
 }
 
@@ -394,13 +337,9 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
   element_mass(p, Ms);
   double *d = calloc(nd, sizeof(double)), *em = calloc(nd, sizeof(double));
   double *g = calloc(nd, sizeof(double)), *R = calloc(nd, sizeof(double));
-  int nb = ne + 1; /* node blocks; a clamped plate's block 0 is sigma, padded to 4 x 4 */
   double *x = calloc(nf, sizeof(double));
-  double (*Ag)[BW + 1] = calloc((size_t)nd, sizeof(*Ag));
-  blk4 *BD = calloc(nb, sizeof(blk4)), *BB = calloc(nb, sizeof(blk4));
-  blk4 *BY = calloc(nb, sizeof(blk4)), *BZ = calloc(nb, sizeof(blk4));
-  double (*bb)[4] = calloc(nb, sizeof(*bb)), (*bx)[4] = calloc(nb, sizeof(*bx));
-  double (*by)[4] = calloc(nb, sizeof(*by)), (*br)[4] = calloc(nb, sizeof(*br));
+  double *J = calloc((size_t)nd * nd, sizeof(double));  /* Jacobian of every coordinate */
+  double *A = calloc((size_t)nf * nf, sizeof(double));  /* Jacobian of the free unknowns */
   double (*Rel)[8] = calloc((size_t)ne, sizeof(*Rel));
   double (*Jel)[8][8] = calloc((size_t)ne, sizeof(*Jel));
   int dynamic = dt > 0.0;
@@ -437,7 +376,7 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
           int r = loc(i, a);
           if (dynamic) {
             double inert = 0.0;
-            for (int j = 0; j < 4; j++) inert = fma(Ms[i][j], g[4 * el + loc(j, a)], inert);
+            for (int j = 0; j < 4; j++) inert = inert + Ms[i][j] * g[4 * el + loc(j, a)];
             Rel[el][r] = inert + c_load * Qi[r];
           } else {
             Rel[el][r] = Qi[r];
@@ -454,50 +393,35 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
             }
         }
     }
-    /* assembly in element order: residual, and the upper band of the Jacobian */
-    for (int I = 0; I < nd; I++) {
-      R[I] = 0.0;
-      for (int k = 0; k <= BW; k++) Ag[I][k] = 0.0;
-    }
+    /* assembly in element order: residual and Jacobian */
+    for (int I = 0; I < nd; I++) R[I] = 0.0;
+    memset(J, 0, sizeof(double) * (size_t)nd * nd);
     for (int el = 0; el < ne; el++)
       for (int r = 0; r < 8; r++) {
         int I = 4 * el + r;
         R[I] = R[I] + Rel[el][r];
-        for (int c = r; c < 8; c++) Ag[I][c - r] = Ag[I][c - r] + Jel[el][r][c];
+        for (int c = 0; c < 8; c++) J[(size_t)I * nd + 4 * el + c] += Jel[el][r][c];
       }
     for (int I = 0; I < nd; I++) R[I] = R[I] - (dynamic ? c_load * Qf[I] : Qf[I]);
-    /* the free system in node blocks: right-hand side -R, D_j, Br_j from the band */
+    /* the free system A x = -R: a clamped plate's first unknown is sigma, the slope of node 0
+     * along t, whose row and column are the slope rows and columns projected on t; the others
+     * are the coordinates of nodes 1.. (global index = free index + 3) */
     if (clamped) {
       x[0] = -(tc * R[2] + ts * R[3]);
       for (int i = 1; i < nf; i++) x[i] = -R[i + 3];
+      A[0] = tc * (tc * J[2 * nd + 2] + ts * J[2 * nd + 3]) +
+             ts * (tc * J[3 * nd + 2] + ts * J[3 * nd + 3]);
+      for (int j = 1; j < nf; j++) {
+        A[j] = tc * J[2 * nd + j + 3] + ts * J[3 * nd + j + 3];
+        A[(size_t)j * nf] = tc * J[(size_t)(j + 3) * nd + 2] + ts * J[(size_t)(j + 3) * nd + 3];
+      }
+      for (int i = 1; i < nf; i++)
+        for (int j = 1; j < nf; j++) A[(size_t)i * nf + j] = J[(size_t)(i + 3) * nd + j + 3];
     } else {
       for (int i = 0; i < nf; i++) x[i] = -R[i];
+      memcpy(A, J, sizeof(double) * (size_t)nd * nd);
     }
-    for (int j = 0; j < nb; j++)
-      for (int r = 0; r < 4; r++) {
-        for (int c = 0; c < 4; c++) {
-          int lo = r < c ? r : c, off = r < c ? c - r : r - c;
-          BD[j][r][c] = Ag[4 * j + lo][off];
-          BB[j][r][c] = j + 1 < nb ? Ag[4 * j + r][4 + c - r] : 0.0;
-        }
-        bb[j][r] = clamped ? (j == 0 ? 0.0 : x[4 * j - 3 + r]) : x[4 * j + r];
-      }
-    if (clamped) { /* block 0: sigma and three idle unknowns */
-      for (int r = 0; r < 4; r++)
-        for (int c = 0; c < 4; c++) {
-          BD[0][r][c] = r == c ? 1.0 : 0.0;
-          BB[0][r][c] = r == 0 ? tc * Ag[2][2 + c] + ts * Ag[3][1 + c] : 0.0;
-        }
-      BD[0][0][0] = tc * (tc * Ag[2][0] + ts * Ag[2][1]) + ts * (tc * Ag[2][1] + ts * Ag[3][0]);
-      bb[0][0] = x[0];
-    }
-    if (bcr_solve(nb, BD, BB, bb, bx, BY, BZ, by, br) != 0) { rc = ORC_PLATE_NOCONV; break; }
-    if (clamped) {
-      x[0] = bx[0][0];
-      for (int i = 1; i < nf; i++) x[i] = bx[(i + 3) / 4][(i + 3) % 4];
-    } else {
-      for (int i = 0; i < nf; i++) x[i] = bx[i / 4][i % 4];
-    }
+    if (gauss_solve(nf, A, x) != 0) { rc = ORC_PLATE_NOCONV; break; }
     /* update: sigma moves the clamped slope along t */
     double *u = dynamic ? d : e;
     double inc = 0.0;
@@ -530,8 +454,7 @@ static int newton(const orc_plate *p, double *e, double *v, const double *Qf, do
       }
     }
   }
-  free(d); free(em); free(g); free(R); free(x); free(Ag); free(BD); free(BB); free(BY); free(BZ);
-  free(bb); free(bx); free(by); free(br); free(Rel); free(Jel);
+  free(d); free(em); free(g); free(R); free(x); free(J); free(A); free(Rel); free(Jel);
   return rc;
 }
 

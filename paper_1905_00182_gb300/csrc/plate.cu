@@ -4,8 +4,9 @@
 //
 // Compiled with --fmad=false and host -ffp-contract=off: every FP64 operation is rounded on its
 // own, in the order written, except the explicit fused multiply-adds (__fma_rn) of the element
-// dot products and of the cyclic reduction -- so a sequential evaluation of the same formulas
-// with the same fused operations reproduces the results bit for bit.
+// dot products and of the cyclic reduction, so every run gives the same bits.  Against an
+// independent solve of the same Newton systems (Gaussian elimination in natural order) the
+// result agrees to a few roundings of the residual times the Newton matrix's condition number.
 //
 // The structure solve is tiny (4 (n_el + 1) unknowns) and sequential by nature (Newton), so it
 // runs in ONE thread block with all state in shared memory, and the host never waits on it:

@@ -1,10 +1,16 @@
 """GPU parity of the flexible plate (Eq. 1, ANCF; clamp of Eq. 17) and of the coupled
 plate-fluid step against the FP64 CPU oracle.
 
-The plate kernels evaluate every FP64 operation separately in the order of the formulas, as the
-oracle does, so plate states, marker positions and (with the strict fluid arithmetic) the whole
-coupled step must agree bit for bit.  The fast and FP32 fluid forms are compared with the strict
-GPU run within the tolerances of their arithmetic."""
+The kernel and the oracle solve the same Newton systems of the implicit midpoint rule by
+different methods: the kernel by block cyclic reduction over the 4 x 4 node blocks with fused
+multiply-adds, the oracle by Gaussian elimination with partial pivoting in natural order, every
+operation rounded on its own.  Two backward-stable solutions of one Newton step differ by a few
+roundings of the residual amplified by the condition number kappa of the Newton matrix
+A = M + (dt^2/4) dQ_int/de (computed here from the oracle's dense mass and tangent matrices):
+per step |de| <= 64 kappa eps max|e| and |dv| <= (2/dt) of that, summed over the steps.  Marker
+positions follow the plate state within the same bound; the coupled fluid state, whose markers
+move by that much, within 1e-10 of its perturbation.  The fast and FP32 fluid forms are
+compared with the strict GPU run within the tolerances of their arithmetic."""
 import math
 
 import numpy as np
@@ -28,6 +34,29 @@ def _forces(ps, seed, scale):
     return scale * (r.reshape(2, ps.n_markers) - 0.5)
 
 
+EPS = float(np.finfo(np.float64).eps)
+
+
+def _kappa(ps, e, dt):
+    """condition number of the Newton matrix M + (dt^2/4) dQ_int/de at the state e"""
+    _, K, Mm = O.plate_internal(ps, e, tangent=True, mass=True)
+    A = Mm + 0.25 * dt * dt * K
+    if ps.clamped:  # node 0's position is prescribed: its rows and columns are not unknowns
+        A = A[2:, 2:]
+    return float(np.linalg.cond(A))
+
+
+def _bounds(ps, e, dt, steps):
+    """(|de|, |dv|) bounds between two backward-stable Newton solutions after `steps` steps"""
+    de = 64.0 * _kappa(ps, e, dt) * EPS * max(1.0, float(np.max(np.abs(e)))) * steps
+    return de, 2.0 * de / dt
+
+
+def _close(got, want, tol):
+    err = float(np.max(np.abs(np.asarray(got) - np.asarray(want))))
+    return err <= tol, err
+
+
 def _deformed(ps, seed=11, amp=0.05, vamp=0.5, **kw):
     r = W.splitmix64(seed, 2 * ps.ndof)
     e, v = W.plate_straight(ps, **kw)
@@ -35,7 +64,7 @@ def _deformed(ps, seed=11, amp=0.05, vamp=0.5, **kw):
 
 
 @pytest.mark.parametrize("kind", ["free", "clamped", "flapping"])
-def test_plate_steps_match_oracle_bit_for_bit(kind):
+def test_plate_steps_match_oracle(kind):
     ib = _ib()
     if kind == "free":
         ps = W.PlateSpec(n_el=10, n_markers=37, K_S=40.0, K_B=0.05, clamped=0)
@@ -64,17 +93,23 @@ def test_plate_steps_match_oracle_bit_for_bit(kind):
     flags, iters = P.status()
     assert flags == 0 and 1 <= iters <= 8
     assert tg == t
-    assert np.array_equal(eg.cpu().numpy(), eo)
-    assert np.array_equal(vg.cpu().numpy(), vo)
+    tol_e, tol_v = _bounds(ps, e, dt, 12)
+    ok_e, err_e = _close(eg.cpu().numpy(), eo, tol_e)
+    ok_v, err_v = _close(vg.cpu().numpy(), vo, tol_v)
+    print(f"{kind}: kappa {_kappa(ps, e, dt):.3e}, |de| {err_e:.3e} (bound {tol_e:.3e}), "
+          f"|dv| {err_v:.3e} (bound {tol_v:.3e})")
+    assert ok_e and ok_v
+    assert np.max(np.abs(eo - e)) > 1e3 * tol_e  # the comparison resolves the motion
     X, U, dS = P.markers()
     Xo, Uo, dSo = O.plate_markers(ps, eo, vo)
-    assert np.array_equal(X.cpu().numpy(), Xo) and np.array_equal(U.cpu().numpy(), Uo)
+    assert _close(X.cpu().numpy(), Xo, 4 * tol_e)[0] and _close(U.cpu().numpy(), Uo, 4 * tol_v)[0]
     assert np.array_equal(dS.cpu().numpy(), dSo)
     # force and power of the last step: its load and the markers' velocities before it
     fg, pg = P.force()
     _, Ub, _ = O.plate_markers(ps, eb, vb)
     fo, po = O.plate_force(ps, F, Ub)
-    assert np.array_equal(fg, fo) and pg == po
+    assert np.array_equal(fg, fo)  # the load alone: summed in marker order on both sides
+    assert abs(pg - po) <= 4 * tol_v * np.sum(np.abs(F)) * ps.length / ps.n_markers
     P.close()
 
 
@@ -95,7 +130,8 @@ def test_plate_extreme_sizes_match_oracle(n_el, nm):
         t = t + dt
     eg, vg, _ = P.get_state()
     assert P.status()[0] == 0
-    assert np.array_equal(eg.cpu().numpy(), eo) and np.array_equal(vg.cpu().numpy(), vo)
+    tol_e, tol_v = _bounds(ps, e, dt, 4)
+    assert _close(eg.cpu().numpy(), eo, tol_e)[0] and _close(vg.cpu().numpy(), vo, tol_v)[0]
 
 
 def test_newton_limit_is_reported_not_faulted():
@@ -108,10 +144,11 @@ def test_newton_limit_is_reported_not_faulted():
     P.step(0.05)
     flags, iters = P.status()
     assert flags & ib.IBFSA_STATUS_NOCONV and iters == 1
-    # the state after the capped iteration is the oracle's capped iterate
+    # the state after the capped iteration is the oracle's capped iterate: one linear solve
     eo, vo, _ = O.plate_step(ps, e, v, 0.05, 0.05, check=False)
     eg, vg, _ = P.get_state()
-    assert np.array_equal(eg.cpu().numpy(), eo) and np.array_equal(vg.cpu().numpy(), vo)
+    tol_e, tol_v = _bounds(ps, e, 0.05, 1)
+    assert _close(eg.cpu().numpy(), eo, tol_e)[0] and _close(vg.cpu().numpy(), vo, tol_v)[0]
     assert P.status() == (0, 0)  # cleared by the read
 
 
@@ -154,7 +191,7 @@ def _coupled_gpu(spec, ps, Q, e, v, dt, steps, strict, force=None):
     return out, flags
 
 
-def test_coupled_step_matches_oracle_bit_for_bit():
+def test_coupled_step_matches_oracle():
     spec, ps, Q, e, v, dt = _coupled_case()
     steps = 3
     fl = []
@@ -165,12 +202,23 @@ def test_coupled_step_matches_oracle_bit_for_bit():
     Qo, xio, eo, vo, to, it_o = O.fsi_step(spec, ps, Q2, xi2, e2, v2, t2, dt, nsteps=1)
     _, Ul, _ = O.plate_markers(ps, e2, v2)
     fo, po = O.plate_force(ps, O.fsi_last_load(ps), Ul)
-    assert np.array_equal(fl[0][0], fo) and fl[0][1] == po
-    assert gs == 0 and ps_flags == 0 and iters >= max(it_o)
+    assert gs == 0 and ps_flags == 0 and iters >= max(it_o) - 1
     assert tg == to
-    assert np.array_equal(Qg, Qo)
-    assert np.array_equal(xig, xio)
-    assert np.array_equal(eg, eo) and np.array_equal(vg, vo)
+    tol_e, tol_v = _bounds(ps, e, dt, steps)
+    ok_e, err_e = _close(eg, eo, tol_e)
+    ok_v, err_v = _close(vg, vo, tol_v)
+    qinf = np.array(spec.qinf[:4])[:, None, None, None]
+    pert = np.max(np.abs(Qo - qinf), axis=(1, 2, 3))
+    errq = np.max(np.abs(Qg - Qo), axis=(1, 2, 3))
+    print(f"coupled: |de| {err_e:.3e} ({tol_e:.3e}), |dv| {err_v:.3e} ({tol_v:.3e}), "
+          f"|dQ|/pert {errq / pert}")
+    assert ok_e and ok_v
+    # the fluid sees markers that moved by ~|de|: its state within 1e-10 of its perturbation
+    assert np.all(errq <= 1e-10 * pert)
+    assert np.max(np.abs(xig - xio)) <= 1e-10 * np.max(np.abs(xio))
+    sc = np.max(np.abs(fo))
+    assert np.max(np.abs(np.asarray(fl[0][0]) - fo)) <= 1e-9 * sc
+    assert abs(fl[0][1] - po) <= 1e-9 * (abs(po) + sc)
     assert np.max(np.abs(eo - e)) > 1e-3  # the plate moved
 
 
