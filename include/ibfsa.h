@@ -4,8 +4,9 @@
  * (arXiv:1905.00182, Sec. 2).
  *
  * What one call computes (Sec. 2):
- *   compressible Navier-Stokes, Eq. 2-5, on a uniform Cartesian grid with cell-centred nodes
- *   x_i = lo + (i + 1/2) h, h = (hi - lo)/n;  Q = [rho, rho u, rho v, (rho w), E];
+ *   compressible Navier-Stokes, Eq. 2-5, on a Cartesian grid with cell-centred nodes
+ *   x_i = lo + (i + 1/2) h, h = (hi - lo)/n, or stretched per direction (ibfsa_set_mesh);
+ *   Q = [rho, rho u, rho v, (rho w), E];
  *   convective fluxes split by a global Lax-Friedrichs splitting f+- = (F +- alpha_d Q)/2 with
  *   alpha_d = max(|u_d| + c) of the stage input, reconstructed component-wise (or, as an
  *   option, characteristic-wise) at every face by fifth-order WENO5-JS or TENO5 (text after
@@ -156,6 +157,22 @@ int ibfsa_rk3_step(ibfsa_grid *g, double dt, int nsteps);
  * of the sphere radius R and R/c: amp = -0.01, b = 16/R^2, omega = 2 pi c/R).  Evaluated at the
  * stage times t, t + dt, t + dt/2 of each step on the grid's clock. */
 int ibfsa_set_source(ibfsa_grid *g, double amp, double b, double omega, const double *xc);
+/* Non-uniform (stretched) mesh along direction a (Sec. 2: a uniform box around the body,
+ * stretched away from it; Sec. 3.2: a sinusoidal transition between the two spacings), given as
+ * a mapping x(xi) of a computational coordinate xi with unit spacing per cell: x_nodes[i + 4] is
+ * the coordinate of node i and dxdxi[i + 4] the metric dx/dxi there, for i = -4 .. n[a] + 3
+ * (n[a] + 8 entries each, ghost nodes included; host or device memory).  Every difference along
+ * a -- the convective flux difference and both fourth-order viscous differences -- is taken in
+ * xi and divided by dx/dxi at the node where it is taken; the pressure source is evaluated at the
+ * node coordinates; markers and probes must keep their four-point support (and one node beyond
+ * each side) where dx/dxi is constant (relative 1e-12), the delta then taking that spacing (else
+ * IBFSA_STATUS_BOUNDS); the sponge width stays in cells; a time step must respect the smallest
+ * spacing.  Nodes must be finite and strictly increasing, the metric positive
+ * (IBFSA_ERR_ARG otherwise); a periodic direction cannot be stretched (IBFSA_ERR_UNSUPPORTED).
+ * Both pointers NULL: back to the uniform spacing (hi - lo)/n.  The arrays are copied into the
+ * grid's workspace; synchronises the grid's stream. */
+int ibfsa_set_mesh(ibfsa_grid *g, int a, const double *x_nodes, const double *dxdxi);
+
 /* The grid's clock: ibfsa_rk3_step and ibfsa_fsi_step advance it by dt per step; ibfsa_rhs
  * evaluates the source at it.  Starts at 0. */
 int ibfsa_set_time(ibfsa_grid *g, double t);

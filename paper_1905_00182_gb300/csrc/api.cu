@@ -185,8 +185,28 @@ Layout layout_for(const ibfsa_grid_desc &d) {
   L.mlp_img = take(d.scheme == IBFSA_MLP_TENO5 ? mlp_image_bytes() : 0);
   L.mlp_counts = take(sizeof(unsigned long long) * 4);
   L.reduce = take(sizeof(double) * 4);
+  for (int a = 0; a < 3; a++) L.mesh[a] = a < d.dim ? take(mesh_bytes(p.n[a])) : take(0);
   L.total = off;
   return L;
+}
+
+// 1/(dx/dxi) and 1/(12 dx/dxi) of one direction's nodes, in FP64 (correctly rounded divisions)
+// and rounded to FP32
+__global__ void k_mesh_derive(int count, const double *__restrict__ m, double *inv, double *inv12,
+                              float *inv32, float *inv12_32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double a = 1.0 / m[i], b = 1.0 / (12.0 * m[i]);
+  inv[i] = a;
+  inv12[i] = b;
+  inv32[i] = (float)a;
+  inv12_32[i] = (float)b;
+}
+
+cudaError_t mesh_derive(int count, const double *metric, double *inv, double *inv12, float *inv32,
+                        float *inv12_32, cudaStream_t st) {
+  k_mesh_derive<<<(count + 127) / 128, 128, 0, st>>>(count, metric, inv, inv12, inv32, inv12_32);
+  return cudaGetLastError();
 }
 
 void prof_begin(Prof *pr, cudaStream_t st) {
@@ -308,6 +328,7 @@ int ibfsa_create_grid(const ibfsa_grid_desc *desc, void *d_workspace, size_t wor
   G.p.mlp_counts = (unsigned long long *)(w + L.mlp_counts);
   G.p.probe_scratch = (double *)(w + L.reduce);
   G.p.mlp_floor = 1e-9f;
+  for (int a = 0; a < 3; a++) G.mesh_ws[a] = w + L.mesh[a];  // directions start uniform
   G.mlp_set = false;
   G.t = 0.0;
   G.src_amp = 0.0;
@@ -516,6 +537,54 @@ int ibfsa_set_source(ibfsa_grid *g, double amp, double b, double omega, const do
   G.p.src_on = amp != 0.0;
   G.p.src_b = b;
   for (int a = 0; a < 3; a++) G.p.src_xc[a] = (amp != 0.0 && a < G.p.dim) ? xc[a] : 0.0;
+  return IBFSA_OK;
+}
+
+int ibfsa_set_mesh(ibfsa_grid *g, int a, const double *x_nodes, const double *dxdxi) {
+  if (!g) return fail(IBFSA_ERR_ARG, "NULL grid");
+  Grid &G = g->g;
+  if (a < 0 || a >= G.p.dim) return fail(IBFSA_ERR_ARG, "direction %d outside [0, %d)", a, G.p.dim);
+  if (!x_nodes != !dxdxi) return fail(IBFSA_ERR_ARG, "give both node coordinates and metric, or neither");
+  if (!x_nodes) {  // back to the uniform spacing of the descriptor's box
+    G.p.mx[a] = G.p.mm[a] = G.p.minv[a] = G.p.minv12[a] = nullptr;
+    G.p.minv32[a] = G.p.minv12_32[a] = nullptr;
+    return IBFSA_OK;
+  }
+  if (G.d.bc[a][0] == IBFSA_BC_PERIODIC)
+    return fail(IBFSA_ERR_UNSUPPORTED, "a stretched direction cannot be periodic");
+  const int cnt = G.p.n[a] + 2 * NG;
+  // checked on the host: finite, strictly increasing nodes, positive finite metric
+  double *hx = new (std::nothrow) double[2 * (size_t)cnt];
+  if (!hx) return fail(IBFSA_ERR_ARG, "host allocation failed");
+  double *hm = hx + cnt;
+  cudaError_t e = cudaMemcpy(hx, x_nodes, sizeof(double) * cnt, cudaMemcpyDefault);
+  if (e == cudaSuccess) e = cudaMemcpy(hm, dxdxi, sizeof(double) * cnt, cudaMemcpyDefault);
+  if (e != cudaSuccess) {
+    delete[] hx;
+    return cuda_fail(e, "ibfsa_set_mesh");
+  }
+  for (int i = 0; i < cnt; i++) {
+    bool ok = isfinite(hx[i]) && isfinite(hm[i]) && hm[i] > 0.0 && (i == 0 || hx[i] > hx[i - 1]);
+    if (!ok) {
+      delete[] hx;
+      return fail(IBFSA_ERR_ARG, "direction %d: node %d is not finite and increasing with a "
+                  "positive metric", a, i - NG);
+    }
+  }
+  char *base = (char *)G.mesh_ws[a];
+  double *dx = (double *)base, *dm = dx + cnt, *di = dm + cnt, *di12 = di + cnt;
+  float *f32 = (float *)(di12 + cnt), *f12 = f32 + cnt;
+  e = cudaMemcpyAsync(dx, hx, sizeof(double) * 2 * cnt, cudaMemcpyHostToDevice, G.stream);
+  if (e == cudaSuccess) e = mesh_derive(cnt, dm, di, di12, f32, f12, G.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G.stream);  // hx is freed below
+  delete[] hx;
+  if (e != cudaSuccess) return cuda_fail(e, "ibfsa_set_mesh");
+  G.p.mx[a] = dx;
+  G.p.mm[a] = dm;
+  G.p.minv[a] = di;
+  G.p.minv12[a] = di12;
+  G.p.minv32[a] = f32;
+  G.p.minv12_32[a] = f12;
   return IBFSA_OK;
 }
 

@@ -36,6 +36,12 @@ struct Plan {
   int src_on;
   double src_b, src_xc[3], src_scale;
   double hprod;        // product of h over active directions
+  // non-uniform mesh (Sec. 2): per direction, node coordinates x_i, the metric dx/dxi, 1/(dx/dxi)
+  // and 1/(12 dx/dxi) at the nodes i = -NG .. n+NG-1 (stored at i + NG), FP64, and the two
+  // reciprocals in FP32.  NULL: the direction is uniform with spacing h (the formulas then use
+  // h itself, so a uniform grid computes exactly what it computes without these arrays).
+  const double *mx[3], *mm[3], *minv[3], *minv12[3];
+  const float *minv32[3], *minv12_32[3];
   // TENO: 1/sum of kept linear weights per cut-off mask (bit k = stencil k kept)
   double teno_w[8][3];
   // single-precision copies for the FP32 perturbation form
@@ -110,14 +116,20 @@ struct Grid {
   bool mlp_set;     // learned weights attached (ibfsa_set_mlp)
   double t;         // the grid's clock (stage times t, t + dt, t + dt/2 of a step)
   double src_amp, src_omega;  // pressure source amplitude and angular frequency
+  void *mesh_ws[3];           // workspace of each direction's mesh arrays
   Prof prof;
 };
 
 // Workspace layout: byte offsets of every buffer for a descriptor.
 struct Layout {
   size_t Q, Q1, Q2, Qp, Wp, L, V, f, X, U, dS, F, xi, xi1, xi2, alpha, status, probe_xp,
-      probe_out, mlp_img, mlp_counts, reduce, total;
+      probe_out, mlp_img, mlp_counts, reduce, mesh[3], total;
 };
+// the mesh arrays of one direction with n cells: 4 FP64 and 2 FP32 arrays of n + 2 NG entries
+inline size_t mesh_bytes(int n) { return (size_t)(n + 2 * NG) * (4 * sizeof(double) + 2 * sizeof(float)); }
+// fills 1/(dx/dxi) and 1/(12 dx/dxi) (FP64, FP32) from the metric of one direction (api.cu)
+cudaError_t mesh_derive(int count, const double *metric, double *inv, double *inv12, float *inv32,
+                        float *inv12_32, cudaStream_t st);
 Layout layout_for(const ibfsa_grid_desc &d);
 void record_error(const char *msg);  // sets the thread-local message of ibfsa_last_error
 void plan_geometry(const ibfsa_grid_desc &d, Plan &p);

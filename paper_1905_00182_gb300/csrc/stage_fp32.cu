@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include "ibfsa_internal.h"
+#include "mesh.cuh"
 #include "mlp_tile.cuh"
 #include "tma.cuh"
 
@@ -84,15 +85,26 @@ __device__ __forceinline__ double peskin(double r) {
   return 0.0;
 }
 
+// four-point supports of point k of X [dim][stride] (Eq. 10-11); *hprod (may be NULL): the
+// product of the local spacings
 template <int DIM>
 __device__ __forceinline__ bool point_support(const Plan &p, const double *X, int stride, int k,
-                                              int j0[3], double w[3][4]) {
+                                              int j0[3], double w[3][4],
+                                              double *hprod = nullptr) {
   bool ok = true;
+  double hp = 1.0;
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     if (a < DIM) {
-      double s = (X[a * stride + k] - p.lo[a]) * p.inv_h[a] - 0.5;
-      j0[a] = (int)floor(s) - 1;
+      double s, hl;
+      if (p.mx[a]) {
+        j0[a] = mesh::support_stretched(p, a, X[a * stride + k], &s, &hl);
+      } else {
+        s = (X[a * stride + k] - p.lo[a]) * p.inv_h[a] - 0.5;
+        j0[a] = (int)floor(s) - 1;
+        hl = p.h[a];
+      }
+      hp *= hl;
 #pragma unroll
       for (int r = 0; r < 4; r++) w[a][r] = peskin(s - (double)(j0[a] + r));
       if (j0[a] < 0 || j0[a] + 3 > p.n[a] - 1) ok = false;
@@ -101,6 +113,7 @@ __device__ __forceinline__ bool point_support(const Plan &p, const double *X, in
       w[a][0] = 1.0; w[a][1] = 0.0; w[a][2] = 0.0; w[a][3] = 0.0;
     }
   }
+  if (hprod) *hprod = hp;
   return ok;
 }
 
@@ -569,8 +582,7 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
   }
   __syncthreads();
 
-  // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / h
-  const float inv_h = p.inv_h32[A];
+  // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / (dx/dxi)
   constexpr int S3 = A == 0 ? (T::SEG + 31) / 32 : (T::ROWS * T::SEG + THREADS - 1) / THREADS;
 #pragma unroll
   for (int k = 0; k < S3; k++) {
@@ -587,6 +599,7 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
     }
     if (row >= nrow || l >= ncell) continue;
     int o = ibase + row * irs + l * ias;
+    const float inv_h = mesh::inv32(p, A, seg0 + l);
 #pragma unroll
     for (int c = 0; c < NV; c++) {
       const float *hh = sh + (c * T::ROWS + row) * FST;
@@ -730,10 +743,10 @@ __global__ void __launch_bounds__(THREADS, 5)
     return;
   }
 
-  // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / h on the copied tile, then stored back
-  const float inv_h = p.inv_h32[A];
+  // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / (dx/dxi) on the copied tile, then stored back
   if (row_ok) {
     for (int l = warp; l < ncell; l += NW) {
+      const float inv_h = mesh::inv32(p, A, seg0 + l);
 #pragma unroll
       for (int c = 0; c < NV; c++) {
         const float *hh = sh + (c * R + lane) * FST;
@@ -772,7 +785,7 @@ __global__ void __launch_bounds__(THREADS) k_visc_flux32(Plan p) {
 #pragma unroll
     for (int dj = 0; dj < DIM; dj++) {
       long long st = stride[dj];
-      g[ci][dj] = d4f(u[-2 * st], u[-st], u[st], u[2 * st], p.inv_h12_32[dj]);
+      g[ci][dj] = d4f(u[-2 * st], u[-st], u[st], u[2 * st], mesh::inv12_32(p, dj, I[dj]));
     }
   }
   float div = 0.f;
@@ -857,7 +870,8 @@ __global__ void __launch_bounds__(128) k_spread32(Plan p, const double *__restri
   const int k = blockIdx.x * MPB + lm;
   const int M = p.max_markers;
   const bool live = k < p.nm;
-  if (live && r < 4 * DIM) {
+  const bool stretched = p.mx[0] || p.mx[1] || p.mx[2];
+  if (live && r < 4 * DIM && !stretched) {
     int a = r / 4, q = r % 4;
     double s = (p.X[a * M + k] - p.lo[a]) * p.inv_h[a] - 0.5;
     int j0 = (int)floor(s) - 1;
@@ -866,14 +880,27 @@ __global__ void __launch_bounds__(128) k_spread32(Plan p, const double *__restri
   }
   if (live && r == 0) {
     bool ok = true;
+    double hprod = p.hprod;
+    if (stretched) {  // one thread finds the marker's supports and its local spacings
+      int j0[3];
+      double w[3][4];
+      ok = point_support<DIM>(p, p.X, M, k, j0, w, &hprod);
 #pragma unroll
-    for (int a = 0; a < DIM; a++) {
-      double s = (p.X[a * M + k] - p.lo[a]) * p.inv_h[a] - 0.5;
-      int j0 = (int)floor(s) - 1;
-      if (j0 < 0 || j0 + 3 > p.n[a] - 1) ok = false;
+      for (int a = 0; a < DIM; a++) {
+        sj[lm][a] = j0[a];
+#pragma unroll
+        for (int q = 0; q < 4; q++) sw[lm][a][q] = w[a][q];
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < DIM; a++) {
+        double s = (p.X[a * M + k] - p.lo[a]) * p.inv_h[a] - 0.5;
+        int j0 = (int)floor(s) - 1;
+        if (j0 < 0 || j0 + 3 > p.n[a] - 1) ok = false;
+      }
     }
     sok[lm] = ok;
-    double sc = p.dS[k] / p.hprod;
+    double sc = p.dS[k] / hprod;
 #pragma unroll
     for (int a = 0; a < 3; a++) sf[lm][a] = a < DIM ? (float)(-p.F[a * M + k] * sc) : 0.f;
     if (DIM < 3) {
@@ -911,7 +938,7 @@ __device__ __forceinline__ float pressure_source32(const Plan &p, int dim, int i
   const int I[3] = {i, j, k};
   float r2 = 0.f;
   for (int a = 0; a < dim; a++) {
-    float dx = (float)(p.lo[a] + ((double)I[a] + 0.5) * p.h[a] - p.src_xc[a]);
+    float dx = (float)(mesh::node(p, a, I[a]) - p.src_xc[a]);
     r2 += dx * dx;
   }
   return expf(-(float)(p.src_b * 0.693147180559945309417) * r2) * (float)p.src_scale;
@@ -943,7 +970,8 @@ __global__ void __launch_bounds__(THREADS) k_finish32(Plan p, const float *__res
       for (int a = 0; a < DIM; a++) {
         const float *F = p.V32 + (long long)(a * (DIM + 1) + fc) * p.NB + bb;
         long long st = stride[a];
-        sum += d4f(F[-2 * st], F[-st], F[st], F[2 * st], p.inv_h12_32[a]);
+        sum += d4f(F[-2 * st], F[-st], F[st], F[2 * st],
+                   mesh::inv12_32(p, a, a == 0 ? i : a == 1 ? j : k));
       }
       Lc[fc + 1] += sum * p.inv_Re32;
     }
@@ -1062,17 +1090,24 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
       }
     }
   };
-  // gradients g[i][j] = du_i/dx_j at staged position (sx, sy) of plane c
-  auto grads = [&](const float *const pl[5], int sx, int sy, float g[3][3], float u[3]) {
+  // 1/(12 dx/dxi) of node i along a (the plan's 1/(12 h) on a uniform direction); indices of
+  // staged points beyond the box (their results are never used) are clamped into it
+  auto ihat = [&](int a, int i) -> float {
+    return p.minv12_32[a] ? p.minv12_32[a][mesh::clamp_node(p, a, i) + NG] : ih[a];
+  };
+  // gradients g[i][j] = du_i/dx_j at staged position (sx, sy) of plane c (ihz: its z metric)
+  auto grads = [&](const float *const pl[5], int sx, int sy, float ihz, float g[3][3],
+                   float u[3]) {
     int e = sy * SX + sx;
+    const float ihx = ihat(0, x0 - 4 + sx), ihy = ihat(1, y0 - 4 + sy);
 #pragma unroll
     for (int i = 0; i < 3; i++) {
       const float *m = pl[2] + i * SX * SY + e;
       u[i] = m[0];
-      g[i][0] = d4f(m[-2], m[-1], m[1], m[2], ih[0]);
-      g[i][1] = d4f(m[-2 * SX], m[-SX], m[SX], m[2 * SX], ih[1]);
+      g[i][0] = d4f(m[-2], m[-1], m[1], m[2], ihx);
+      g[i][1] = d4f(m[-2 * SX], m[-SX], m[SX], m[2 * SX], ihy);
       g[i][2] = d4f(pl[0][i * SX * SY + e], pl[1][i * SX * SY + e], pl[3][i * SX * SY + e],
-                    pl[4][i * SX * SY + e], ih[2]);
+                    pl[4][i * SX * SY + e], ihz);
     }
   };
   // viscous flux of direction a: [tau_0a, tau_1a, tau_2a, b_a]
@@ -1091,13 +1126,14 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
 
   // divergence of the viscous flux of this column's cells c-2 .. c+2, accumulated as the
   // fluxes arrive: F_v,z of plane c enters the z-differences of cells c-2, c-1, c+1, c+2
-  // (weights -1, 8, -8, 1 over 12 h), the x/y divergence of plane c enters cell c
+  // (weights -1, 8, -8, 1 over 12 dx/dxi of that cell), the x/y divergence of plane c enters
+  // cell c
   float acc[5][4];
 #pragma unroll
   for (int o = 0; o < 5; o++)
 #pragma unroll
     for (int k = 0; k < 4; k++) acc[o][k] = 0.f;
-  const float ihz8 = 8.f * ih[2];
+  const float ihx_own = ihat(0, X), ihy_own = ihat(1, Y);
   // inputs of the cell finished next (L, stage increment), loaded one plane ahead
   float Lnext[5], Dnext[5];
   auto fetch_cell = [&](int d) {
@@ -1123,9 +1159,10 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
 #pragma unroll
     for (int o = 0; o < 5; o++) pl[o] = ring + ((c + 6 + o) % 5) * PLANE;
     // own cell: all three fluxes; halo points: F_v,x (x offsets -2,-1,32,33) or F_v,y
+    const float ihz = ihat(2, c);
     {
       float g[3][3], u[3], f[4];
-      grads(pl, tx + 4, ty + 4, g, u);
+      grads(pl, tx + 4, ty + 4, ihz, g, u);
       vflux(0, g, u, f);
 #pragma unroll
       for (int k = 0; k < 4; k++) fx[(k * TY + ty) * PX + tx + 2] = f[k];
@@ -1133,25 +1170,27 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
 #pragma unroll
       for (int k = 0; k < 4; k++) fy[(k * PY + ty + 2) * TX + tx] = f[k];
       vflux(2, g, u, f);
+      const float zm2 = ihat(2, c - 2), zm1 = 8.f * ihat(2, c - 1);
+      const float zp1 = 8.f * ihat(2, c + 1), zp2 = ihat(2, c + 2);
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        acc[0][k] -= ih[2] * f[k];
-        acc[1][k] += ihz8 * f[k];
-        acc[3][k] -= ihz8 * f[k];
-        acc[4][k] += ih[2] * f[k];
+        acc[0][k] -= zm2 * f[k];
+        acc[1][k] += zm1 * f[k];
+        acc[3][k] -= zp1 * f[k];
+        acc[4][k] += zp2 * f[k];
       }
     }
     for (int e = threadIdx.x; e < 4 * TY + 4 * TX; e += VT) {
       float g[3][3], u[3], f[4];
       if (e < 4 * TY) {  // x-halo point
         int r = e / 4, h = e % 4, px = h < 2 ? h : TX + h;  // 0,1,TX+2,TX+3
-        grads(pl, px + 2, r + 4, g, u);
+        grads(pl, px + 2, r + 4, ihz, g, u);
         vflux(0, g, u, f);
 #pragma unroll
         for (int k = 0; k < 4; k++) fx[(k * TY + r) * PX + px] = f[k];
       } else {           // y-halo point
         int e2 = e - 4 * TY, col = e2 % TX, h = e2 / TX, py = h < 2 ? h : TY + h;
-        grads(pl, col + 4, py + 2, g, u);
+        grads(pl, col + 4, py + 2, ihz, g, u);
         vflux(1, g, u, f);
 #pragma unroll
         for (int k = 0; k < 4; k++) fy[(k * PY + py) * TX + col] = f[k];
@@ -1163,8 +1202,8 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
     for (int k = 0; k < 4; k++) {
       const float *Fx = fx + (k * TY + ty) * PX + tx + 2;
       const float *Fy = fy + (k * PY + ty + 2) * TX + tx;
-      acc[2][k] += d4f(Fx[-2], Fx[-1], Fx[1], Fx[2], ih[0]) +
-                   d4f(Fy[-2 * TX], Fy[-TX], Fy[TX], Fy[2 * TX], ih[1]);
+      acc[2][k] += d4f(Fx[-2], Fx[-1], Fx[1], Fx[2], ihx_own) +
+                   d4f(Fy[-2 * TX], Fy[-TX], Fy[TX], Fy[2 * TX], ihy_own);
     }
     // plane d = c - 2 is complete: viscous term, sponge, RK update
     int d = c - 2;

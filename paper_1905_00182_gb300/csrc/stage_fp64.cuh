@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "ibfsa_internal.h"
+#include "mesh.cuh"
 
 #ifndef IBFSA_STRICT
 #error "define IBFSA_STRICT to 0 or 1"
@@ -523,7 +524,9 @@ __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
 #pragma unroll
     for (int c = 0; c < NV; c++) {
       const double *hh = sh + (c * T::ROWS + row) * FST;
-      double d = divide(hh[l + 1] - hh[l], p.h[A], p.inv_h[A]);
+      // dx/dxi at the cell (the spacing h on a uniform direction)
+      double d = p.mm[A] ? divide(hh[l + 1] - hh[l], p.mm[A][I[A] + NG], p.minv[A][I[A] + NG])
+                         : divide(hh[l + 1] - hh[l], p.h[A], p.inv_h[A]);
       double prev = first ? 0.0 : p.L[c * p.N + o];
       p.L[c * p.N + o] = prev - d;
     }
@@ -558,7 +561,12 @@ __global__ void __launch_bounds__(THREADS) k_visc_flux(Plan p) {
 #pragma unroll
     for (int dj = 0; dj < DIM; dj++) {
       long long st = stride[dj];
-      g[ci][dj] = d4(u[-2 * st], u[-st], u[st], u[2 * st], p.h12[dj], p.inv_h12[dj]);
+      if (p.mm[dj]) {  // 12 dx/dxi at this node, rounded as 12 h is on a uniform direction
+        int at = I[dj] + NG;
+        g[ci][dj] = d4(u[-2 * st], u[-st], u[st], u[2 * st], 12.0 * p.mm[dj][at], p.minv12[dj][at]);
+      } else {
+        g[ci][dj] = d4(u[-2 * st], u[-st], u[st], u[2 * st], p.h12[dj], p.inv_h12[dj]);
+      }
     }
   }
   double div = 0.0;
@@ -595,7 +603,12 @@ __global__ void __launch_bounds__(THREADS) k_visc_div(Plan p) {
     for (int a = 0; a < DIM; a++) {
       const double *F = p.V + (long long)(a * (DIM + 1) + fc) * p.NB + b;
       long long st = stride[a];
-      sum += d4(F[-2 * st], F[-st], F[st], F[2 * st], p.h12[a], p.inv_h12[a]);
+      if (p.mm[a]) {
+        int at = (a == 0 ? i : a == 1 ? j : k) + NG;
+        sum += d4(F[-2 * st], F[-st], F[st], F[2 * st], 12.0 * p.mm[a][at], p.minv12[a][at]);
+      } else {
+        sum += d4(F[-2 * st], F[-st], F[st], F[2 * st], p.h12[a], p.inv_h12[a]);
+      }
     }
     long long o = (long long)(fc + 1) * p.N + t;
     p.L[o] = p.L[o] + divide(sum, p.Re, p.inv_Re);
@@ -605,20 +618,34 @@ __global__ void __launch_bounds__(THREADS) k_visc_div(Plan p) {
 // ------------------------------------------------------------------------------------------
 // immersed boundary (Eq. 7-9)
 // ------------------------------------------------------------------------------------------
+// the four-point supports of point k of X [dim][nm] in every direction (Eq. 10-11); *hprod
+// (may be NULL) receives the product of the local spacings, h^d of the delta at the point
 template <int DIM>
 __device__ __forceinline__ bool marker_support(const Plan &p, const double *X, int nm, int k,
-                                               int j0[3], double w[3][4]) {
+                                               int j0[3], double w[3][4],
+                                               double *hprod = nullptr) {
   bool ok = true;
+  double hp = 1.0;
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     if (a < DIM) {
-      j0[a] = support(p, a, X[a * nm + k], w[a]);
+      if (p.mx[a]) {
+        double s, hl;
+        j0[a] = mesh::support_stretched(p, a, X[a * nm + k], &s, &hl);
+#pragma unroll
+        for (int r = 0; r < 4; r++) w[a][r] = peskin(s - (double)(j0[a] + r));
+        hp *= hl;
+      } else {
+        j0[a] = support(p, a, X[a * nm + k], w[a]);
+        hp *= p.h[a];
+      }
       if (j0[a] < 0 || j0[a] + 3 > p.n[a] - 1) ok = false;
     } else {
       j0[a] = 0;
       w[a][0] = 1.0; w[a][1] = 0.0; w[a][2] = 0.0; w[a][3] = 0.0;
     }
   }
+  if (hprod) *hprod = hp;
   return ok;
 }
 
@@ -669,14 +696,14 @@ __global__ void k_spread_ordered(Plan p) {
   int M = p.max_markers;
   for (int k = 0; k < p.nm; k++) {
     int j0[3];
-    double w[3][4];
-    bool ok = marker_support<DIM>(p, p.X, M, k, j0, w);
+    double w[3][4], hprod;
+    bool ok = marker_support<DIM>(p, p.X, M, k, j0, w, &hprod);
     if (ok && r < 4 * 4 * C2) {
       double wt = w[0][r0] * w[1][r1] * w[2][r2];
       long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
 #pragma unroll
       for (int a = 0; a < DIM; a++)
-        p.f[a * p.N + o] -= p.F[a * M + k] * wt * p.dS[k] / p.hprod;
+        p.f[a * p.N + o] -= p.F[a * M + k] * wt * p.dS[k] / hprod;
     }
     __syncthreads();
   }
@@ -693,12 +720,12 @@ __global__ void k_spread_atomic(Plan p) {
   int r0 = r & 3, r1 = (r >> 2) & 3, r2 = DIM > 2 ? (r >> 4) : 0;
   int M = p.max_markers;
   int j0[3];
-  double w[3][4];
-  if (!marker_support<DIM>(p, p.X, M, k, j0, w)) return;
+  double w[3][4], hprod;
+  if (!marker_support<DIM>(p, p.X, M, k, j0, w, &hprod)) return;
   double wt = w[0][r0] * w[1][r1] * w[2][r2];
   long long o = int_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
   long long s = pad_index(p, j0[0] + r0, j0[1] + r1, j0[2] + r2);
-  double scale = wt * p.dS[k] / p.hprod;
+  double scale = wt * p.dS[k] / hprod;
   double pw = 0.0;
 #pragma unroll
   for (int a = 0; a < DIM; a++) {
@@ -747,7 +774,7 @@ __global__ void __launch_bounds__(THREADS) k_finish(Plan p, const double *__rest
     double r2 = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
-      double x = p.lo[a] + ((double)I[a] + 0.5) * p.h[a];
+      double x = mesh::node(p, a, I[a]);
       r2 = r2 + (x - p.src_xc[a]) * (x - p.src_xc[a]);
     }
     Lc[NV - 1] = Lc[NV - 1] + exp(-(p.src_b * LN2) * r2) * p.src_scale;

@@ -45,7 +45,7 @@ EXPORTS = (
     "ibfsa_body_force", "ibfsa_plate_workspace_bytes", "ibfsa_plate_create",
     "ibfsa_plate_destroy", "ibfsa_plate_set_state", "ibfsa_plate_get_state", "ibfsa_plate_step",
     "ibfsa_plate_markers", "ibfsa_plate_get_status", "ibfsa_fsi_step", "ibfsa_plate_force",
-    "ibfsa_set_source", "ibfsa_set_time", "ibfsa_get_time",
+    "ibfsa_set_source", "ibfsa_set_time", "ibfsa_get_time", "ibfsa_set_mesh",
 )
 MLP_NPARAM = 2403
 
@@ -160,6 +160,7 @@ def lib():
         L.ibfsa_plate_force.argtypes = [_P, _P, _P]
         L.ibfsa_set_source.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]
         L.ibfsa_set_time.argtypes = [_P, ctypes.c_double]
+        L.ibfsa_set_mesh.argtypes = [_P, ctypes.c_int, _P, _P]
         L.ibfsa_get_time.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
@@ -480,6 +481,12 @@ def ibfsa_get_time(g) -> float:
     return t.value
 
 
+def ibfsa_set_mesh(g, a: int, x_nodes: int, dxdxi: int):
+    """Stretched mesh along direction a: node coordinates and dx/dxi at i = -4 .. n+3 (pointers;
+    both 0: uniform again)."""
+    _check(lib().ibfsa_set_mesh(g, int(a), _P(x_nodes or None), _P(dxdxi or None)))
+
+
 def ibfsa_fsi_step(g, p, dt: float, nsteps: int = 1):
     _check(lib().ibfsa_fsi_step(g, p, float(dt), int(nsteps)))
 
@@ -611,6 +618,19 @@ class Grid:
 
     def set_time(self, t: float):
         ibfsa_set_time(self.h, t)
+
+    def set_mesh(self, a: int, nodes=None, metric=None):
+        """Stretch direction a: node coordinates and dx/dxi at i = -4 .. n[a]+3 (arrays of
+        n[a] + 8 entries); None: uniform again."""
+        if nodes is None:
+            ibfsa_set_mesh(self.h, a, 0, 0)
+            return
+        x = np.ascontiguousarray(nodes, dtype=np.float64)
+        m = np.ascontiguousarray(metric, dtype=np.float64)
+        if x.shape != (self.spec.n[a] + 8,) or m.shape != x.shape:
+            raise ValueError(f"direction {a}: nodes and metric need n + 8 = "
+                             f"{self.spec.n[a] + 8} entries")
+        ibfsa_set_mesh(self.h, a, x.ctypes.data, m.ctypes.data)  # copied, synchronised
 
 
 class Plate:
