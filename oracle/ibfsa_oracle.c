@@ -13,7 +13,9 @@
  * direction) every difference is taken in the computational coordinate and divided by dx/dxi:
  *
  *   1. ghost fill (4 layers) per boundary rule                 (readings: zero-gradient,
- *                                                                free stream, periodic)
+ *                                                                free stream, periodic; a
+ *      characteristic face copies its boundary cell, whose normal convective term is then the
+ *      characteristic form of Thompson's non-reflecting condition, Sec. 2)
  *   2. alpha_d = max over interior of |u_d| + c                 (global Lax-Friedrichs split)
  *   3. convective term: f+- = (F_d(Q) +- alpha_d Q)/2, fifth-order WENO5-JS or TENO5
  *      reconstruction of every component at every face (or, as an option, of every
@@ -301,7 +303,7 @@ static void fill_padded(const pgrid *G, const orc_desc *d, const double *Q, doub
       for (int l = 1; l <= NG; l++) {
         int gi = side == 0 ? -l : G->n[a] - 1 + l; /* ghost index along a */
         int src;
-        if (rule == 0) src = side == 0 ? 0 : G->n[a] - 1;
+        if (rule == 0 || rule == 3) src = side == 0 ? 0 : G->n[a] - 1;
         else if (rule == 2) src = side == 0 ? G->n[a] - l : l - 1;
         else src = -1;
         int I[3];
@@ -370,6 +372,103 @@ static double flux(const pgrid *G, const double *W, const double *u, const doubl
 }
 
 /* ----------------------------------------------------------------------------------------- */
+/* Characteristic non-reflecting boundaries (Sec. 2, after Thompson): on a face whose rule is  */
+/* 3, the ghosts copy the boundary cell (for the stencils that reach them), and at the         */
+/* boundary cell the convective term normal to the face is taken from the characteristic form  */
+/* of the Euler equations along the normal: wave amplitudes from one-sided derivatives of the  */
+/* primitives, those of the waves entering the domain set to zero.                             */
+/* ----------------------------------------------------------------------------------------- */
+/* 1 when cell m of direction a (of na cells) is the boundary cell of a characteristic face */
+static int char_cell(const orc_desc *d, int a, int m, int na) {
+  return (m == 0 && d->bc[a][0] == 3) || (m == na - 1 && d->bc[a][1] == 3);
+}
+
+/* d/dx_a of a padded field phi at interior cell I by the fourth-order one-sided difference
+ * into the domain (s = +1 from the low face, -1 from the high face), divided by dx/dxi:
+ *   (-25 f0 + 48 f1 - 36 f2 + 16 f3 - 3 f4)/12, written on the differences f_k - f0 (the
+ *   weights sum to zero) so that a constant field gives exactly zero */
+static double one_sided(const pgrid *G, const double *phi, const int I[3], int a, int s) {
+  const double c[5] = {0.0, 48.0, -36.0, 16.0, -3.0};
+  double f0 = phi[pidx(G, I[0], I[1], I[2])];
+  double acc = 0.0;
+  for (int k = 1; k < 5; k++) {
+    int J[3] = {I[0], I[1], I[2]};
+    J[a] += s * k;
+    acc = acc + c[k] * (phi[pidx(G, J[0], J[1], J[2])] - f0);
+  }
+  return (double)s * acc / (12.0 * met(G, a, I[a]));
+}
+
+/* (d F_a / d x_a) at the boundary cell I of the face (a, side) in characteristic form:
+ *   L1 = (u - c)(p_x - rho c u_x), L2 = u (c^2 rho_x - p_x), L_t = u (u_t)_x,
+ *   L5 = (u + c)(p_x + rho c u_x), u = u_a, x = x_a, u_t the transverse velocities;
+ * an amplitude whose speed (u - c, u, u + c) points into the domain is set to zero; then
+ *   d1 = (L2 + (L5 + L1)/2)/c^2, d2 = (L5 + L1)/2, d3 = (L5 - L1)/(2 rho c), d_t = L_t
+ * are the rates of rho, p, u_a, u_t, and the conservative form is
+ *   [d1, u_b d1 + rho d_b (d_a = d3), |u|^2/2 d1 + d2/(gamma - 1) + rho sum_b u_b d_b]. */
+static void char_flux_derivative(const pgrid *G, const orc_desc *d, const double *rho,
+                                 const double *u, const double *p, const int I[3], int a,
+                                 int side, double *out) {
+  int dim = G->dim, nv = G->nv;
+  int s = side == 0 ? 1 : -1;
+  size_t o = pidx(G, I[0], I[1], I[2]);
+  double r = rho[o], pr = p[o];
+  double c = sqrt(d->gamma * pr / r);
+  double ua = u[a * G->N + o];
+  double rx = one_sided(G, rho, I, a, s);
+  double px = one_sided(G, p, I, a, s);
+  double uxa = one_sided(G, u + a * G->N, I, a, s);
+  double lam1 = ua - c, lam2 = ua, lam5 = ua + c;
+  /* a speed points into the domain when it has the sign of s (low face: > 0) */
+  double L1 = (lam1 * (double)s > 0.0) ? 0.0 : lam1 * (px - r * c * uxa);
+  double L2 = (lam2 * (double)s > 0.0) ? 0.0 : lam2 * (c * c * rx - px);
+  double L5 = (lam5 * (double)s > 0.0) ? 0.0 : lam5 * (px + r * c * uxa);
+  double dv[3] = {0.0, 0.0, 0.0}; /* rates of the velocities: d3 along a, d_t across */
+  for (int b = 0; b < dim; b++) {
+    if (b == a) continue;
+    double utx = one_sided(G, u + b * G->N, I, a, s);
+    dv[b] = (lam2 * (double)s > 0.0) ? 0.0 : lam2 * utx;
+  }
+  double d1 = (L2 + 0.5 * (L5 + L1)) / (c * c);
+  double d2 = 0.5 * (L5 + L1);
+  dv[a] = (L5 - L1) / (2.0 * r * c);
+  double ke = 0.0, work = 0.0;
+  out[0] = d1;
+  for (int b = 0; b < dim; b++) {
+    double ub = u[b * G->N + o];
+    out[1 + b] = ub * d1 + r * dv[b];
+    ke = ke + ub * ub;
+    work = work + ub * dv[b];
+  }
+  out[nv - 1] = 0.5 * ke * d1 + d2 / (d->gamma - 1.0) + r * work;
+}
+
+/* L -= (dF_a/dx_a)_char at the boundary cells of every characteristic face */
+static void characteristic_faces(const pgrid *G, const orc_desc *d, const double *rho,
+                                 const double *u, const double *p, double *L) {
+  int nv = G->nv;
+  size_t Nu = (size_t)G->n[0] * G->n[1] * G->n[2];
+  for (int a = 0; a < G->dim; a++)
+    for (int side = 0; side < 2; side++) {
+      if (d->bc[a][side] != 3) continue;
+      int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+      for (int t2 = 0; t2 < G->n[b2]; t2++)
+        for (int t1 = 0; t1 < G->n[b1]; t1++) {
+          int I[3];
+          I[a] = side == 0 ? 0 : G->n[a] - 1;
+          I[b1] = t1;
+          I[b2] = t2;
+          double D[5];
+          char_flux_derivative(G, d, rho, u, p, I, a, side, D);
+          for (int c = 0; c < nv; c++) {
+            size_t o = c * Nu + uidx(G, I[0], I[1], I[2]);
+            L[o] = L[o] - D[c];
+          }
+        }
+    }
+}
+
+/* ----------------------------------------------------------------------------------------- */
 /* Convective term, component-wise reconstruction of the globally split fluxes               */
 /* ----------------------------------------------------------------------------------------- */
 static void convective(const pgrid *G, const orc_desc *d, const double *W, const double *u,
@@ -404,6 +503,7 @@ static void convective(const pgrid *G, const orc_desc *d, const double *W, const
             Fh[m + 1] = recon_d(d, vp) + recon_d(d, vm);
           }
           for (int m = 0; m < na; m++) {
+            if (char_cell(d, a, m, na)) continue; /* its normal term: characteristic_faces */
             int I[3];
             I[a] = m; I[b1] = t1; I[b2] = t2;
             size_t o = c * Nu + uidx(G, I[0], I[1], I[2]);
@@ -556,6 +656,7 @@ static int convective_charwise(const pgrid *G, const orc_desc *d, const double *
         }
         for (int c = 0; c < nv; c++)
           for (int m = 0; m < na; m++) {
+            if (char_cell(d, a, m, na)) continue;
             int I[3];
             I[a] = m; I[b1] = t1; I[b2] = t2;
             size_t o = c * Nu + uidx(G, I[0], I[1], I[2]);
@@ -822,6 +923,10 @@ static int check_desc(const orc_desc *d) {
     int p0 = d->bc[a][0] == 2, p1 = d->bc[a][1] == 2;
     if (p0 != p1) return ORC_ERR_ARG;          /* periodic on both faces or on neither */
     if (p0 && d->n[a] < NG) return ORC_ERR_ARG; /* wrap-around ghosts need n >= 4 */
+    for (int s = 0; s < 2; s++) {
+      if (d->bc[a][s] < 0 || d->bc[a][s] > 3) return ORC_ERR_ARG;
+      if (d->bc[a][s] == 3 && d->n[a] < 5) return ORC_ERR_ARG; /* one-sided 5-point stencil */
+    }
   }
   return ORC_OK;
 }
@@ -877,6 +982,7 @@ static int rhs_impl(const orc_desc *d, const double *Q, int nm, const double *X,
   } else {
     convective(&G, d, W, u, p, alpha, L);
   }
+  characteristic_faces(&G, d, rho, u, p, L);
   if (d->Re > 0.0) viscous(&G, d, u, L);
   sponge(&G, d, Q, L);
   pressure_source(&G, d, d->time, L);

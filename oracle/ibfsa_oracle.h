@@ -14,7 +14,8 @@ typedef struct {
   double gamma, Re;     /* Re <= 0: inviscid */
   double qinf[5];       /* free-stream conservative state [rho, m_x, m_y, (m_z), E] */
   int scheme;           /* 0 = WENO5-JS, 1 = TENO5 */
-  int bc[3][2];         /* 0 = zero gradient, 1 = free stream, 2 = periodic */
+  int bc[3][2];         /* 0 = zero gradient, 1 = free stream, 2 = periodic, 3 = characteristic
+                           (Thompson's non-reflecting condition; needs n >= 5) */
   int sponge_cells;     /* 0: no sponge */
   double sponge_sigma;  /* sigma_max */
   double alpha_pen, beta_pen; /* Eq. 7 constants */
