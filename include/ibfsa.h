@@ -64,8 +64,15 @@ enum { IBFSA_WENO5JS = 0, IBFSA_TENO5 = 1, IBFSA_MLP_TENO5 = 2 };
  * cancel, while the RK state, its combination, the IB markers and the probes stay FP64 */
 enum { IBFSA_FP64 = 0, IBFSA_FP32_PERTURB = 1 };
 /* boundary rules per face of the box: ghost cells copy the nearest interior cell, hold the
- * free stream, or wrap around */
-enum { IBFSA_BC_ZERO_GRAD = 0, IBFSA_BC_FREESTREAM = 1, IBFSA_BC_PERIODIC = 2 };
+ * free stream, or wrap around; or the characteristic non-reflecting condition (Sec. 2, after
+ * Thompson): ghosts copy the boundary cell, and at the boundary cell the convective term normal
+ * to the face is replaced by the characteristic form of the Euler equations along the normal --
+ * wave amplitudes L1 = (u - c)(p_x - rho c u_x), L2 = u (c^2 rho_x - p_x), L_t = u (u_t)_x,
+ * L5 = (u + c)(p_x + rho c u_x) from fourth-order one-sided derivatives of the primitives into
+ * the domain, those whose speed points into the domain set to zero, mapped back to the
+ * conservative variables (needs n >= 5 along that direction) */
+enum { IBFSA_BC_ZERO_GRAD = 0, IBFSA_BC_FREESTREAM = 1, IBFSA_BC_PERIODIC = 2,
+       IBFSA_BC_CHARACTERISTIC = 3 };
 /* status bits of ibfsa_get_status: a marker or probe support left the grid; a non-finite
  * value entered the state; a kernel gave up waiting for its tensor copies (iteration limit), so
  * the results of that call are invalid */

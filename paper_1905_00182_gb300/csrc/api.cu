@@ -37,9 +37,12 @@ static int check_desc(const ibfsa_grid_desc *d) {
   for (int a = 0; a < d->dim; a++) {
     if (d->n[a] < 1) return fail(IBFSA_ERR_ARG, "n[%d] = %d must be >= 1", a, d->n[a]);
     if (!(d->hi[a] > d->lo[a])) return fail(IBFSA_ERR_ARG, "hi[%d] must exceed lo[%d]", a, a);
-    for (int s = 0; s < 2; s++)
-      if (d->bc[a][s] < 0 || d->bc[a][s] > 2)
+    for (int s = 0; s < 2; s++) {
+      if (d->bc[a][s] < 0 || d->bc[a][s] > 3)
         return fail(IBFSA_ERR_ARG, "bc[%d][%d] = %d is not a boundary rule", a, s, d->bc[a][s]);
+      if (d->bc[a][s] == IBFSA_BC_CHARACTERISTIC && d->n[a] < 5)
+        return fail(IBFSA_ERR_ARG, "a characteristic face needs n[%d] >= 5 (got %d)", a, d->n[a]);
+    }
     bool p0 = d->bc[a][0] == IBFSA_BC_PERIODIC, p1 = d->bc[a][1] == IBFSA_BC_PERIODIC;
     if (p0 != p1) return fail(IBFSA_ERR_ARG, "periodic direction %d needs both faces periodic", a);
     if (p0 && d->n[a] < NG) return fail(IBFSA_ERR_ARG, "periodic direction %d needs n >= %d", a, NG);

@@ -57,16 +57,22 @@ __device__ __forceinline__ Free free_stream(const Plan &p) {
 
 __device__ __forceinline__ int map_index(int i, int n, int rlo, int rhi) {
   if (i < 0) {
-    if (rlo == IBFSA_BC_ZERO_GRAD) return 0;
+    if (rlo == IBFSA_BC_ZERO_GRAD || rlo == IBFSA_BC_CHARACTERISTIC) return 0;
     if (rlo == IBFSA_BC_PERIODIC) return n + i;
     return -1;
   }
   if (i >= n) {
-    if (rhi == IBFSA_BC_ZERO_GRAD) return n - 1;
+    if (rhi == IBFSA_BC_ZERO_GRAD || rhi == IBFSA_BC_CHARACTERISTIC) return n - 1;
     if (rhi == IBFSA_BC_PERIODIC) return i - n;
     return -1;
   }
   return i;
+}
+
+// the boundary cell of a characteristic face along a (its normal term comes from k_char_face32)
+__device__ __forceinline__ bool char_cell(const Plan &p, int a, int i) {
+  return (i == 0 && p.bc[a][0] == IBFSA_BC_CHARACTERISTIC) ||
+         (i == p.n[a] - 1 && p.bc[a][1] == IBFSA_BC_CHARACTERISTIC);
 }
 
 __device__ __forceinline__ long long pad_index(const Plan &p, int i, int j, int k) {
@@ -599,7 +605,8 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
     }
     if (row >= nrow || l >= ncell) continue;
     int o = ibase + row * irs + l * ias;
-    const float inv_h = mesh::inv32(p, A, seg0 + l);
+    // the boundary cell of a characteristic face takes its normal term from k_char_face32
+    const float inv_h = char_cell(p, A, seg0 + l) ? 0.f : mesh::inv32(p, A, seg0 + l);
 #pragma unroll
     for (int c = 0; c < NV; c++) {
       const float *hh = sh + (c * T::ROWS + row) * FST;
@@ -746,7 +753,7 @@ __global__ void __launch_bounds__(THREADS, 5)
   // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / (dx/dxi) on the copied tile, then stored back
   if (row_ok) {
     for (int l = warp; l < ncell; l += NW) {
-      const float inv_h = mesh::inv32(p, A, seg0 + l);
+      const float inv_h = char_cell(p, A, seg0 + l) ? 0.f : mesh::inv32(p, A, seg0 + l);
 #pragma unroll
       for (int c = 0; c < NV; c++) {
         const float *hh = sh + (c * R + lane) * FST;
@@ -757,6 +764,72 @@ __global__ void __launch_bounds__(THREADS, 5)
   tma::fence_async_shared();
   __syncthreads();
   if (threadIdx.x == 0) tma::store_4d(&tl, line0, yi, zi, 0, in);
+}
+
+// ------------------------------------------------------------------------------------------
+// characteristic non-reflecting faces (Sec. 2, after Thompson) on the perturbations: the
+// one-sided derivatives of rho', u', p' are those of rho, u, p; the wave speeds and the map
+// back to the conservative variables use the full state
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float one_sided32(const float *phi, long long o, long long st, int s,
+                                             float inv12) {
+  const float f0 = phi[o];
+  float acc = 48.f * (phi[o + s * st] - f0);
+  acc = fmaf(-36.f, phi[o + 2 * s * st] - f0, acc);
+  acc = fmaf(16.f, phi[o + 3 * s * st] - f0, acc);
+  acc = fmaf(-3.f, phi[o + 4 * s * st] - f0, acc);
+  return (float)s * acc * inv12;
+}
+
+template <int DIM>
+__global__ void k_char_face32(Plan p, int a, int side) {
+  constexpr int NV = DIM + 2;
+  const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)p.n[b1] * p.n[b2]) return;
+  int I[3];
+  I[a] = side == 0 ? 0 : p.n[a] - 1;
+  I[b1] = (int)(t % p.n[b1]);
+  I[b2] = (int)(t / p.n[b1]);
+  const int s = side == 0 ? 1 : -1;
+  const Free fs = free_stream(p);
+  const long long o = pad_index(p, I[0], I[1], I[2]);
+  const long long st = a == 0 ? 1 : a == 1 ? (long long)p.P[0] : (long long)p.P[0] * p.P[1];
+  const float inv12 = mesh::inv12_32(p, a, I[a]);
+  const float r = fs.rho + p.Qp32[o], pr = fs.p + p.Wp32[DIM * p.NP + o];
+  const float c = sqrtf(fs.gamma * pr / r);
+  const float ua = fs.u[a] + p.Wp32[a * p.NP + o];
+  const float rx = one_sided32(p.Qp32, o, st, s, inv12);
+  const float px = one_sided32(p.Wp32 + DIM * p.NP, o, st, s, inv12);
+  const float uxa = one_sided32(p.Wp32 + a * p.NP, o, st, s, inv12);
+  const float lam1 = ua - c, lam2 = ua, lam5 = ua + c, rc = r * c;
+  const float L1 = (lam1 * (float)s > 0.f) ? 0.f : lam1 * (px - rc * uxa);
+  const float L2 = (lam2 * (float)s > 0.f) ? 0.f : lam2 * (c * c * rx - px);
+  const float L5 = (lam5 * (float)s > 0.f) ? 0.f : lam5 * (px + rc * uxa);
+  float dv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    if (b == a) continue;
+    float utx = one_sided32(p.Wp32 + b * p.NP, o, st, s, inv12);
+    dv[b] = (lam2 * (float)s > 0.f) ? 0.f : lam2 * utx;
+  }
+  const float d1 = (L2 + 0.5f * (L5 + L1)) / (c * c);
+  const float d2 = 0.5f * (L5 + L1);
+  dv[a] = (L5 - L1) / (2.f * rc);
+  float D[NV];
+  float ke = 0.f, work = 0.f;
+  D[0] = d1;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    float ub = fs.u[b] + p.Wp32[b * p.NP + o];
+    D[1 + b] = ub * d1 + r * dv[b];
+    ke += ub * ub;
+    work += ub * dv[b];
+  }
+  D[NV - 1] = 0.5f * ke * d1 + d2 / fs.gm1 + r * work;
+  const long long oi = int_index(p, I[0], I[1], I[2]);
+#pragma unroll
+  for (int c2 = 0; c2 < NV; c2++) p.L32[c2 * p.N + oi] -= D[c2];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1404,6 +1477,15 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
     prof_end(pr, K_CONV_Z, st);
     if (e != cudaSuccess) return e;
   }
+  for (int a = 0; a < DIM; a++)  // characteristic faces
+    for (int side = 0; side < 2; side++) {
+      if (p.bc[a][side] != IBFSA_BC_CHARACTERISTIC) continue;
+      long long cells = (long long)p.n[(a + 1) % 3] * p.n[(a + 2) % 3];
+      prof_begin(pr, st);
+      k_char_face32<DIM><<<blocks_for(cells, THREADS), THREADS, 0, st>>>(p, a, side);
+      prof_end(pr, K_CONV_X + a, st);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   if (p.Re > 0.0 && DIM == 2) {
     prof_begin(pr, st);
     k_visc_flux32<DIM><<<blocks_for(p.NB, THREADS), THREADS, 0, st>>>(p);

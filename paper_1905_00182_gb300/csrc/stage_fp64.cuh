@@ -37,16 +37,22 @@ __device__ __forceinline__ double divide(double x, double d, double inv_d) {
 // ghost rule of one direction: interior index, or -1 for a free-stream ghost
 __device__ __forceinline__ int map_index(int i, int n, int rlo, int rhi) {
   if (i < 0) {
-    if (rlo == IBFSA_BC_ZERO_GRAD) return 0;
+    if (rlo == IBFSA_BC_ZERO_GRAD || rlo == IBFSA_BC_CHARACTERISTIC) return 0;
     if (rlo == IBFSA_BC_PERIODIC) return n + i;
     return -1;
   }
   if (i >= n) {
-    if (rhi == IBFSA_BC_ZERO_GRAD) return n - 1;
+    if (rhi == IBFSA_BC_ZERO_GRAD || rhi == IBFSA_BC_CHARACTERISTIC) return n - 1;
     if (rhi == IBFSA_BC_PERIODIC) return i - n;
     return -1;
   }
   return i;
+}
+
+// the boundary cell of a characteristic face along a (its normal term comes from k_char_face)
+__device__ __forceinline__ bool char_cell(const Plan &p, int a, int i) {
+  return (i == 0 && p.bc[a][0] == IBFSA_BC_CHARACTERISTIC) ||
+         (i == p.n[a] - 1 && p.bc[a][1] == IBFSA_BC_CHARACTERISTIC);
 }
 
 __device__ __forceinline__ long long pad_index(const Plan &p, int i, int j, int k) {
@@ -524,13 +530,88 @@ __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
 #pragma unroll
     for (int c = 0; c < NV; c++) {
       const double *hh = sh + (c * T::ROWS + row) * FST;
-      // dx/dxi at the cell (the spacing h on a uniform direction)
-      double d = p.mm[A] ? divide(hh[l + 1] - hh[l], p.mm[A][I[A] + NG], p.minv[A][I[A] + NG])
-                         : divide(hh[l + 1] - hh[l], p.h[A], p.inv_h[A]);
+      // dx/dxi at the cell (the spacing h on a uniform direction); the boundary cell of a
+      // characteristic face takes its normal term from k_char_face instead
+      double d = char_cell(p, A, I[A]) ? 0.0
+                 : p.mm[A] ? divide(hh[l + 1] - hh[l], p.mm[A][I[A] + NG], p.minv[A][I[A] + NG])
+                           : divide(hh[l + 1] - hh[l], p.h[A], p.inv_h[A]);
       double prev = first ? 0.0 : p.L[c * p.N + o];
       p.L[c * p.N + o] = prev - d;
     }
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// characteristic non-reflecting faces (Sec. 2, after Thompson): at the boundary cell the normal
+// convective term is dF_a/dx_a in characteristic form, from fourth-order one-sided derivatives
+// of the primitives with the entering waves' amplitudes set to zero
+// ------------------------------------------------------------------------------------------
+// fourth-order one-sided derivative into the domain (s = +1 from the low face, -1 from the high
+// face) of the padded field phi at padded offset o, stride st along the direction;
+// (-25 f0 + 48 f1 - 36 f2 + 16 f3 - 3 f4)/12 on the differences f_k - f0
+__device__ __forceinline__ double one_sided(const double *phi, long long o, long long st, int s,
+                                            double h12, double inv_h12) {
+  const double f0 = phi[o];
+  double acc = 0.0;
+  acc = acc + 48.0 * (phi[o + s * st] - f0);
+  acc = acc + -36.0 * (phi[o + 2 * s * st] - f0);
+  acc = acc + 16.0 * (phi[o + 3 * s * st] - f0);
+  acc = acc + -3.0 * (phi[o + 4 * s * st] - f0);
+  return divide((double)s * acc, h12, inv_h12);
+}
+
+// one thread per cell of the face (a, side): L -= (dF_a/dx_a)_char, in the order the formulas
+// are written (the strict form reproduces a sequential evaluation)
+template <int DIM>
+__global__ void k_char_face(Plan p, int a, int side) {
+  constexpr int NV = DIM + 2;
+  const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)p.n[b1] * p.n[b2]) return;
+  int I[3];
+  I[a] = side == 0 ? 0 : p.n[a] - 1;
+  I[b1] = (int)(t % p.n[b1]);
+  I[b2] = (int)(t / p.n[b1]);
+  const int s = side == 0 ? 1 : -1;
+  const long long o = pad_index(p, I[0], I[1], I[2]);
+  const long long st = a == 0 ? 1 : a == 1 ? (long long)p.P[0] : (long long)p.P[0] * p.P[1];
+  const double h12 = p.mm[a] ? 12.0 * p.mm[a][I[a] + NG] : p.h12[a];
+  const double ih12 = p.mm[a] ? p.minv12[a][I[a] + NG] : p.inv_h12[a];
+  const double r = p.Qp[o], pr = p.Wp[DIM * p.NP + o];
+  const double c = sqrt(p.gamma * pr / r);
+  const double ua = p.Wp[a * p.NP + o];
+  const double rx = one_sided(p.Qp, o, st, s, h12, ih12);
+  const double px = one_sided(p.Wp + DIM * p.NP, o, st, s, h12, ih12);
+  const double uxa = one_sided(p.Wp + a * p.NP, o, st, s, h12, ih12);
+  const double lam1 = ua - c, lam2 = ua, lam5 = ua + c;
+  // a speed points into the domain when it has the sign of s
+  const double L1 = (lam1 * (double)s > 0.0) ? 0.0 : lam1 * (px - r * c * uxa);
+  const double L2 = (lam2 * (double)s > 0.0) ? 0.0 : lam2 * (c * c * rx - px);
+  const double L5 = (lam5 * (double)s > 0.0) ? 0.0 : lam5 * (px + r * c * uxa);
+  double dv[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    if (b == a) continue;
+    double utx = one_sided(p.Wp + b * p.NP, o, st, s, h12, ih12);
+    dv[b] = (lam2 * (double)s > 0.0) ? 0.0 : lam2 * utx;
+  }
+  const double d1 = (L2 + 0.5 * (L5 + L1)) / (c * c);
+  const double d2 = 0.5 * (L5 + L1);
+  dv[a] = (L5 - L1) / (2.0 * r * c);
+  double D[NV];
+  double ke = 0.0, work = 0.0;
+  D[0] = d1;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    double ub = p.Wp[b * p.NP + o];
+    D[1 + b] = ub * d1 + r * dv[b];
+    ke = ke + ub * ub;
+    work = work + ub * dv[b];
+  }
+  D[NV - 1] = 0.5 * ke * d1 + d2 / p.gm1 + r * work;
+  const long long oi = int_index(p, I[0], I[1], I[2]);
+#pragma unroll
+  for (int c2 = 0; c2 < NV; c2++) p.L[c2 * p.N + oi] = p.L[c2 * p.N + oi] - D[c2];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -895,6 +976,16 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
     prof_end(pr, K_CONV_Z, st);
     if (e != cudaSuccess) return e;
   }
+  // characteristic faces, direction by direction, low face first
+  for (int a = 0; a < DIM; a++)
+    for (int side = 0; side < 2; side++) {
+      if (p.bc[a][side] != IBFSA_BC_CHARACTERISTIC) continue;
+      long long cells = (long long)p.n[(a + 1) % 3] * p.n[(a + 2) % 3];
+      prof_begin(pr, st);
+      k_char_face<DIM><<<blocks_for(cells, THREADS), THREADS, 0, st>>>(p, a, side);
+      prof_end(pr, K_CONV_X + a, st);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   if (p.Re > 0.0) {
     prof_begin(pr, st);
     k_visc_flux<DIM><<<blocks_for(p.NB, THREADS), THREADS, 0, st>>>(p);

@@ -32,6 +32,7 @@ FP32_PERTURB = 1
 BC_ZERO_GRAD = 0
 BC_FREESTREAM = 1
 BC_PERIODIC = 2
+BC_CHARACTERISTIC = 3
 
 
 @dataclasses.dataclass

@@ -57,6 +57,7 @@ def test_workspace_bytes_counts_buffers(ib):
     ("bc", ((2, 0), (0, 0), (0, 0)), -1), ("bc", ((2, 2), (0, 0), (0, 0)), None),
     ("n", (3, 12, 8), None), ("gamma", 1.0, -1), ("scheme", 7, -5), ("precision", 9, -5),
     ("charwise", True, None), ("charwise", 2, -1),
+    ("bc", ((3, 3), (3, 1), (0, 3)), None), ("bc", ((4, 0), (0, 0), (0, 0)), -1),
 ])
 def test_descriptor_validation(ib, field, value, code):
     spec = _good()
@@ -71,6 +72,17 @@ def test_descriptor_validation(ib, field, value, code):
         ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec))
     assert e.value.code == code
     assert ib.lib().ibfsa_last_error()
+
+
+def test_characteristic_face_needs_five_cells(ib):
+    spec = _good()
+    spec.n = (16, 12, 4)
+    spec.bc = ((0, 0), (0, 0), (0, 3))
+    with pytest.raises(ib.IbfsaError) as e:
+        ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec))
+    assert e.value.code == ib.IBFSA_ERR_ARG
+    spec.n = (16, 12, 5)
+    assert ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec)) > 0
 
 
 def test_charwise_is_fp64_only(ib):
