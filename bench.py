@@ -343,12 +343,14 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
-def make_grid(ib, args, precision, strict=False, scheme=None, state="pulse", mlp=None):
+def make_grid(ib, args, precision, strict=False, scheme=None, state="pulse", mlp=None,
+              charwise=False):
     n = args.n
     if scheme is None:
         scheme = W.TENO5 if args.scheme == "teno5" else W.WENO5JS
     spec, dt = workload_spec(n, args.markers, scheme)
     spec.precision = precision
+    spec.charwise = charwise
     X, U, dS = W.fibonacci_sphere(args.markers, 0.5)
     probes, _, _ = W.fibonacci_sphere(1000, 6.0 * n / 512.0)
     g = ib.Grid(spec, strict=strict, max_probes=probes.shape[1])
@@ -622,6 +624,19 @@ def run_ours(args, rank, world, local_rank):
                    "steps_compared": steps_done,
                    "weights": "paper_1905_00182_gb300/mlp_weights.npz"}
 
+    # the characteristic-wise option in the FP32 perturbation form on the same workload
+    charwise = None
+    if fp32 and args.compare:
+        gcw, _, _, _, _ = make_grid(ib, args, W.FP32_PERTURB, charwise=True)
+        gcw.rk3_step(dt, 1)
+        msc, _ = timed_steps(ib, gcw, dt, 2, barrier, profile=False)
+        charwise = {"value": spec.cells * 3 * 2 * world / (max_ranks(msc) * 1e-3),
+                    "ms_per_step": msc / 2, "steps": 2,
+                    "vs_componentwise_fp32": (spec.cells * 3 * 2 / (msc * 1e-3)) / value}
+        gcw.close()
+        del gcw
+        torch.cuda.empty_cache()
+
     fsi = fsi_form(ib, barrier, max_ranks, world) if (fp32 and args.compare) else None
 
     if rank != 0:
@@ -685,6 +700,8 @@ def run_ours(args, rank, world, local_rank):
             out["forms"]["learned"] = learned
         if fsi is not None:
             out["forms"]["fsi"] = fsi
+        if charwise is not None:
+            out["forms"]["charwise_fp32"] = charwise
     if e2e is not None:
         out["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:

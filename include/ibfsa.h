@@ -109,8 +109,10 @@ typedef struct {
                               split fluxes of each stencil projected on the left eigenvectors
                               of the Euler flux Jacobian along the face normal at the Roe
                               average of the face's two cells, reconstructed per field and
-                              projected back.  FP64 forms only (IBFSA_ERR_UNSUPPORTED
-                              otherwise). */
+                              projected back.  In the FP32 perturbation form the split-flux
+                              perturbations are projected, on eigenvectors built in FP32 from
+                              the face's full primitive state.  Not with IBFSA_MLP_TENO5
+                              (IBFSA_ERR_UNSUPPORTED). */
 } ibfsa_grid_desc;
 
 /* Bytes of device workspace a grid with this descriptor needs (for the caller to allocate). */

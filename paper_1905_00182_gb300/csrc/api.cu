@@ -68,8 +68,8 @@ static int check_desc(const ibfsa_grid_desc *d) {
   if (d->sponge_cells < 0 || d->max_markers < 0 || d->max_probes < 0)
     return fail(IBFSA_ERR_ARG, "negative sponge width or capacity");
   if (d->charwise != 0 && d->charwise != 1) return fail(IBFSA_ERR_ARG, "charwise must be 0 or 1");
-  if (d->charwise && d->precision != IBFSA_FP64)
-    return fail(IBFSA_ERR_UNSUPPORTED, "characteristic-wise reconstruction is FP64 only");
+  if (d->charwise && d->scheme == IBFSA_MLP_TENO5)
+    return fail(IBFSA_ERR_UNSUPPORTED, "the learned weights reconstruct component-wise");
   (void)cells;
   return IBFSA_OK;
 }

@@ -400,10 +400,88 @@ __device__ __forceinline__ void split_cell(const Free &fs, float alpha, const fl
   }
 }
 
+// Characteristic-wise option in the perturbation form: eigenvectors of the Euler flux Jacobian
+// along A at the Roe average of the face's two cells, from their full primitive state
+// (rho_inf + rho', u_inf + u', p_inf + p'), H = gamma p/((gamma - 1) rho) + |u|^2/2; right
+// eigenvectors are the columns of R, left ones the rows of Lv, in the order u-c, entropy,
+// shears, u+c.  The split-flux perturbations are projected on them: their constant free-stream
+// part would pass through L and R unchanged and cancel in the face difference.
+template <int DIM, int A>
+__device__ __forceinline__ void roe_eigen32(const Free &fs, const float wl[DIM + 2],
+                                            const float wr[DIM + 2], float R[DIM + 2][DIM + 2],
+                                            float Lv[DIM + 2][DIM + 2]) {
+  // w = [rho', u'_0 .. u'_{DIM-1}, p']
+  constexpr int NV = DIM + 2;
+  const float rl = fs.rho + wl[0], rr = fs.rho + wr[0];
+  const float sl = sqrtf(rl), sr = sqrtf(rr), inv = 1.f / (sl + sr);
+  const float kap = fs.gamma / fs.gm1;
+  float u[DIM], kl = 0.f, kr = 0.f;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    float ul = fs.u[b] + wl[1 + b], ur = fs.u[b] + wr[1 + b];
+    u[b] = (sl * ul + sr * ur) * inv;
+    kl += ul * ul;
+    kr += ur * ur;
+  }
+  const float Hl = kap * (fs.p + wl[NV - 1]) / rl + 0.5f * kl;
+  const float Hr = kap * (fs.p + wr[NV - 1]) / rr + 0.5f * kr;
+  const float H = (sl * Hl + sr * Hr) * inv;
+  float q2 = 0.f;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) q2 += u[b] * u[b];
+  const float c2 = fs.gm1 * (H - 0.5f * q2);
+  const float c = sqrtf(c2), ic = 1.f / c;
+  const float b1 = fs.gm1 / c2, b2 = 0.5f * q2 * b1;
+  const float ua = u[A];
+#pragma unroll
+  for (int i = 0; i < NV; i++)
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+      R[i][j] = 0.f;
+      Lv[i][j] = 0.f;
+    }
+  constexpr int km = 0, ke = 1, kp = NV - 1;
+  R[0][km] = 1.f;
+  R[0][ke] = 1.f;
+  R[0][kp] = 1.f;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    R[1 + b][km] = u[b] - (b == A ? c : 0.f);
+    R[1 + b][ke] = u[b];
+    R[1 + b][kp] = u[b] + (b == A ? c : 0.f);
+  }
+  R[NV - 1][km] = H - ua * c;
+  R[NV - 1][ke] = 0.5f * q2;
+  R[NV - 1][kp] = H + ua * c;
+  Lv[km][0] = 0.5f * (b2 + ua * ic);
+  Lv[kp][0] = 0.5f * (b2 - ua * ic);
+  Lv[ke][0] = 1.f - b2;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    Lv[km][1 + b] = 0.5f * (-b1 * u[b] - (b == A ? ic : 0.f));
+    Lv[kp][1 + b] = 0.5f * (-b1 * u[b] + (b == A ? ic : 0.f));
+    Lv[ke][1 + b] = b1 * u[b];
+  }
+  Lv[km][NV - 1] = 0.5f * b1;
+  Lv[kp][NV - 1] = 0.5f * b1;
+  Lv[ke][NV - 1] = -b1;
+  int t = 0;
+#pragma unroll
+  for (int b = 0; b < DIM; b++) {
+    if (b == A) continue;
+    R[1 + b][2 + t] = 1.f;
+    R[NV - 1][2 + t] = u[b];
+    Lv[2 + t][0] = -u[b];
+    Lv[2 + t][1 + b] = 1.f;
+    t++;
+  }
+}
+
 // eight blocks per SM (32 registers) for the fixed schemes, four (64 registers) for the
-// learned form's warp-wide network tiles.  The x pass gives each warp one row of the tile.
-template <int DIM, int A, int SCHEME>
-__global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
+// learned form's warp-wide network tiles, one for the characteristic-wise option (its two
+// eigen-systems per face take registers).  The x pass gives each warp one row of the tile.
+template <int DIM, int A, int SCHEME, bool CHAR = false>
+__global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR ? 1 : 8))
     k_conv32(Plan p, int first) {
   constexpr int NV = DIM + 2;
   using T = Tile<A>;
@@ -548,6 +626,57 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 8)
     if ((threadIdx.x & 31) == 0 && seen) {
       atomicAdd(&p.mlp_counts[0], (unsigned long long)used);
       atomicAdd(&p.mlp_counts[1], (unsigned long long)seen);
+    }
+  } else if constexpr (CHAR) {
+    // characteristic-wise: per face the Roe-averaged eigen-system of cells m and m+1 (staged
+    // cells fi + 2 and fi + 3), the stencils of each characteristic field, back-projection
+#pragma unroll 1
+    for (int ps = 0; ps < MAXP; ps++) {
+      int e = threadIdx.x + ps * THREADS;
+      int row, fi;
+      if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
+      else { row = e % T::ROWS; fi = e / T::ROWS; }
+#pragma unroll
+      for (int c = 0; c < NV; c++) Fh[ps][c] = 0.f;
+      if (e < T::ROWS * T::FACES && row < nrow && fi < nface) {
+        const int b = fi + 2;
+        const int sl = pbase + row * prs + (b - 3) * pas, sr = sl + pas;
+        float wl[NV], wr[NV];
+        wl[0] = p.Qp32[sl];
+        wr[0] = p.Qp32[sr];
+#pragma unroll
+        for (int k = 0; k <= DIM; k++) {
+          wl[1 + k] = p.Wp32[(size_t)k * p.NP + sl];
+          wr[1 + k] = p.Wp32[(size_t)k * p.NP + sr];
+        }
+        float Rm[NV][NV], Lv[NV][NV];
+        roe_eigen32<DIM, A>(fs, wl, wr, Rm, Lv);
+        float hk[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+          float vp[5], vm[5];
+#pragma unroll
+          for (int r = 0; r < 5; r++) {
+            float sp = 0.f, sn = 0.f;
+#pragma unroll
+            for (int c = 0; c < NV; c++) {
+              sp = fmaf(Lv[k][c], sfp[(c * T::ROWS + row) * T::LEN + b - 2 + r], sp);
+              sn = fmaf(Lv[k][c], sfm[(c * T::ROWS + row) * T::LEN + b + 3 - r], sn);
+            }
+            vp[r] = sp;
+            vm[r] = sn;
+          }
+          hk[k] = recon<SCHEME>(p, vp[0], vp[1], vp[2], vp[3], vp[4]) +
+                  recon<SCHEME>(p, vm[0], vm[1], vm[2], vm[3], vm[4]);
+        }
+#pragma unroll
+        for (int c = 0; c < NV; c++) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < NV; k++) acc = fmaf(Rm[c][k], hk[k], acc);
+          Fh[ps][c] = acc;
+        }
+      }
     }
   } else {
 #pragma unroll
@@ -1007,11 +1136,13 @@ __global__ void __launch_bounds__(128) k_spread32(Plan p, const double *__restri
 //   mode 2: Qn += b (din + dt L) in FP64 and qn32 = (float)(Qn - q_inf)
 // ------------------------------------------------------------------------------------------
 // periodic Gaussian pressure source (Sec. 3.6, Eq. 16) of cell (i, j, k): energy-equation term
+template <bool STRETCHED = true>
 __device__ __forceinline__ float pressure_source32(const Plan &p, int dim, int i, int j, int k) {
   const int I[3] = {i, j, k};
   float r2 = 0.f;
   for (int a = 0; a < dim; a++) {
-    float dx = (float)(mesh::node(p, a, I[a]) - p.src_xc[a]);
+    double x = STRETCHED ? mesh::node(p, a, I[a]) : p.lo[a] + ((double)I[a] + 0.5) * p.h[a];
+    float dx = (float)(x - p.src_xc[a]);
     r2 += dx * dx;
   }
   return expf(-(float)(p.src_b * 0.693147180559945309417) * r2) * (float)p.src_scale;
@@ -1117,6 +1248,9 @@ constexpr int PX = TX + 4, PY = TY + 4;        // flux points (halo 2)
 constexpr size_t SMEM = sizeof(float) * (5 * 3 * SX * SY + 4 * PX * TY + 4 * TX * PY);
 }  // namespace vm
 
+// STRETCHED: some direction has a non-uniform mesh (per-point metrics); otherwise the uniform
+// 1/(12 h) constants, with no per-point lookups
+template <bool STRETCHED>
 __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, const float *__restrict__ din,
                                                           float *__restrict__ dout, double *Qn,
                                                           double *__restrict__ Lout, float Bc,
@@ -1166,7 +1300,10 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
   // 1/(12 dx/dxi) of node i along a (the plan's 1/(12 h) on a uniform direction); indices of
   // staged points beyond the box (their results are never used) are clamped into it
   auto ihat = [&](int a, int i) -> float {
-    return p.minv12_32[a] ? p.minv12_32[a][mesh::clamp_node(p, a, i) + NG] : ih[a];
+    if constexpr (STRETCHED)
+      return p.minv12_32[a] ? p.minv12_32[a][mesh::clamp_node(p, a, i) + NG] : ih[a];
+    else
+      return ih[a];
   };
   // gradients g[i][j] = du_i/dx_j at staged position (sx, sy) of plane c (ihz: its z metric)
   auto grads = [&](const float *const pl[5], int sx, int sy, float ihz, float g[3][3],
@@ -1299,7 +1436,7 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
           for (int cc = 0; cc < 5; cc++) Lc[cc] -= sig * (p.qn32[cc * p.N + t] + Dnext[cc]);
         }
       }
-      if (p.src_on) Lc[4] += pressure_source32(p, 3, X, Y, d);
+      if (p.src_on) Lc[4] += pressure_source32<STRETCHED>(p, 3, X, Y, d);
       if (mode == 0) {
 #pragma unroll
         for (int cc = 0; cc < 5; cc++) Lout[cc * p.N + t] = (double)Lc[cc];
@@ -1409,6 +1546,23 @@ template <int DIM, int A, int SCHEME>
 cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
   using T = Tile<A>;
   cudaError_t e;
+  if constexpr (SCHEME != IBFSA_MLP_TENO5) {
+    if (p.charwise) {  // the characteristic-wise option: generic tiles for every direction
+      constexpr size_t smem = conv_smem<DIM, A>();
+      e = cudaFuncSetAttribute(k_conv32<DIM, A, SCHEME, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      dim3 grid;
+      if (A == 0) {
+        grid = dim3((p.n[0] + T::SEG - 1) / T::SEG, (p.n[1] + T::ROWS - 1) / T::ROWS, p.n[2]);
+      } else {
+        int nseg = (p.n[A] + T::SEG - 1) / T::SEG;
+        grid = dim3(nseg * ((p.n[0] + T::ROWS - 1) / T::ROWS), A == 1 ? p.n[2] : p.n[1]);
+      }
+      k_conv32<DIM, A, SCHEME, true><<<grid, THREADS, smem, st>>>(p, first);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (A != 0 && SCHEME != IBFSA_MLP_TENO5) {
     if (p.n[0] % 4 == 0 && !first) {
       using TT = TmaTile<DIM, A>;
@@ -1505,12 +1659,13 @@ cudaError_t run_stage(const Plan &p, const StageArgs &s, cudaStream_t st) {
   prof_begin(pr, st);
   if (p.Re > 0.0 && DIM == 3) {
     using namespace vm;
-    e = cudaFuncSetAttribute(k_visc_march32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM);
+    const bool stretched = p.minv12_32[0] || p.minv12_32[1] || p.minv12_32[2];
+    auto kern = stretched ? k_visc_march32<true> : k_visc_march32<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     dim3 grid((p.n[0] + TX - 1) / TX, (p.n[1] + TY - 1) / TY, (p.n[2] + ZC - 1) / ZC);
-    k_visc_march32<<<grid, VT, SMEM, st>>>(q, din, dout, const_cast<double *>(Qn), s.Lout,
-                                               (float)s.b, (float)s.dt, mode);
+    kern<<<grid, VT, SMEM, st>>>(q, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b,
+                                 (float)s.dt, mode);
   } else if (p.Re > 0.0)
     k_finish32<DIM, true><<<blocks_for(p.N, THREADS), THREADS, 0, st>>>(
         q, din, dout, const_cast<double *>(Qn), s.Lout, (float)s.b, (float)s.dt, mode);

@@ -85,10 +85,12 @@ def test_characteristic_face_needs_five_cells(ib):
     assert ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec)) > 0
 
 
-def test_charwise_is_fp64_only(ib):
+def test_charwise_in_every_form_but_the_learned_one(ib):
     spec = _good()
     spec.charwise = True
     spec.precision = W.FP32_PERTURB
+    assert ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec)) > 0
+    spec.scheme = W.MLP_TENO5
     with pytest.raises(ib.IbfsaError) as e:
         ib.ibfsa_workspace_bytes(ib.desc_from_spec(spec))
     assert e.value.code == ib.IBFSA_ERR_UNSUPPORTED
