@@ -255,6 +255,40 @@ __device__ __forceinline__ float teno5_pm(const Plan &tw, float2 a, float2 b, fl
   return teno5_pm_k(tw, a, b, c, d, e, kx, ky);
 }
 
+// The same packed TENO5 with a warp-uniform slow path: every lane of the warp must call it.  The
+// linear (all-kept) result is computed without branches; only when some lane of the warp has a
+// side that cuts a stencil does the whole warp enter the full TENO5 (a uniform branch, no
+// divergence to reconverge).  The all-kept test is scale-invariant, so the indicators are
+// taken times 4, (13/3) t^2 + u^2 (one multiplication fewer each), with the floor 4e-30.
+__device__ __forceinline__ float teno5_pm_warp(const Plan &tw, float2 a, float2 b, float2 c,
+                                               float2 d, float2 e) {
+  float2 t0 = __fadd2_rn(__ffma2_rn(f2(-2.f), b, a), c);
+  float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.f), c, b), d);
+  float2 t2 = __fadd2_rn(__ffma2_rn(f2(-2.f), d, c), e);
+  float2 u0 = __ffma2_rn(f2(3.f), c, __ffma2_rn(f2(-4.f), b, a));
+  float2 u1 = __ffma2_rn(f2(-1.f), d, b);
+  float2 u2 = __ffma2_rn(f2(3.f), c, __ffma2_rn(f2(-4.f), d, e));
+  const float2 k13 = f2(13.f / 3.f);
+  float2 b0 = __ffma2_rn(__fmul2_rn(k13, t0), t0, __fmul2_rn(u0, u0));
+  float2 b1 = __ffma2_rn(__fmul2_rn(k13, t1), t1, __fmul2_rn(u1, u1));
+  float2 b2 = __ffma2_rn(__fmul2_rn(k13, t2), t2, __fmul2_rn(u2, u2));
+  float2 tau = __ffma2_rn(f2(-1.f), b2, b0);
+  const bool kx = fabsf(tau.x) <= fmaf(4.f, fminf(b0.x, fminf(b1.x, b2.x)), 1.6e-29f);
+  const bool ky = fabsf(tau.y) <= fmaf(4.f, fminf(b0.y, fminf(b1.y, b2.y)), 1.6e-29f);
+  float2 lin = __fmul2_rn(f2(2.f / 60.f), a);
+  lin = __ffma2_rn(f2(-13.f / 60.f), b, lin);
+  lin = __ffma2_rn(f2(47.f / 60.f), c, lin);
+  lin = __ffma2_rn(f2(27.f / 60.f), d, lin);
+  lin = __ffma2_rn(f2(-3.f / 60.f), e, lin);
+  float h = lin.x + lin.y;
+  if (__any_sync(0xffffffffu, !(kx && ky))) {
+    float hx = kx ? lin.x : teno5(tw, a.x, b.x, c.x, d.x, e.x);
+    float hy = ky ? lin.y : teno5(tw, a.y, b.y, c.y, d.y, e.y);
+    h = hx + hy;
+  }
+  return h;
+}
+
 template <int SCHEME>
 __device__ __forceinline__ float recon(const Plan &tw, float a, float b, float c, float d,
                                        float e) {
@@ -685,19 +719,32 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
       int row, fi;
       if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
       else { row = e % T::ROWS; fi = e / T::ROWS; }
-      if (e < T::ROWS * T::FACES && row < nrow && fi < nface) {
+      if constexpr (SCHEME == IBFSA_TENO5) {
+        // every lane of the warp takes part (the slow path is warp-uniform): lanes without a
+        // face evaluate a valid one of their row (or row 0) and store nothing
+        const bool valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
+        if (!valid) {
+          fi = 0;
+          if (row >= nrow) row = 0;
+        }
         int b = fi + 2;
 #pragma unroll
         for (int c = 0; c < NV; c++) {
           const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
           const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
-          if constexpr (SCHEME == IBFSA_TENO5)
-            Fh[ps][c] = teno5_pm(p, make_float2(fp[b - 2], fm[b + 3]),
-                                 make_float2(fp[b - 1], fm[b + 2]), make_float2(fp[b], fm[b + 1]),
-                                 make_float2(fp[b + 1], fm[b]), make_float2(fp[b + 2], fm[b - 1]));
-          else
-            Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
-                        recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+          Fh[ps][c] = teno5_pm_warp(p, make_float2(fp[b - 2], fm[b + 3]),
+                                    make_float2(fp[b - 1], fm[b + 2]),
+                                    make_float2(fp[b], fm[b + 1]), make_float2(fp[b + 1], fm[b]),
+                                    make_float2(fp[b + 2], fm[b - 1]));
+        }
+      } else if (e < T::ROWS * T::FACES && row < nrow && fi < nface) {
+        int b = fi + 2;
+#pragma unroll
+        for (int c = 0; c < NV; c++) {
+          const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
+          const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
+          Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
+                      recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
         }
       }
     }
@@ -850,10 +897,11 @@ __global__ void __launch_bounds__(THREADS, 5)
       for (int c = 0; c < NV; c++) {
         const float *fp = sfp + (c * (LEN - 1) + fi) * R + lane;
         const float *fm = sfm + (c * (LEN - 1) + fi) * R + lane;   // f- of staged cell fi+1
-        if constexpr (SCHEME == IBFSA_TENO5)
-          Fh[ps][c] = teno5_pm(p, make_float2(fp[0], fm[4 * R]), make_float2(fp[R], fm[3 * R]),
-                               make_float2(fp[2 * R], fm[2 * R]), make_float2(fp[3 * R], fm[R]),
-                               make_float2(fp[4 * R], fm[0]));
+        if constexpr (SCHEME == IBFSA_TENO5)  // fi is the same for the whole warp
+          Fh[ps][c] = teno5_pm_warp(p, make_float2(fp[0], fm[4 * R]),
+                                    make_float2(fp[R], fm[3 * R]),
+                                    make_float2(fp[2 * R], fm[2 * R]),
+                                    make_float2(fp[3 * R], fm[R]), make_float2(fp[4 * R], fm[0]));
         else
           Fh[ps][c] = recon<SCHEME>(p, fp[0], fp[R], fp[2 * R], fp[3 * R], fp[4 * R]) +
                       recon<SCHEME>(p, fm[4 * R], fm[3 * R], fm[2 * R], fm[R], fm[0]);
