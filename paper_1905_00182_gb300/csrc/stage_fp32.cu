@@ -1318,30 +1318,40 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
   const int PLANE = 3 * SX * SY;
 
   // plane z (ghost range -4 .. n+3) is read into registers one iteration before it enters
-  // ring slot z mod 5, so its global-memory latency hides behind the gradients of a plane
+  // ring slot z mod 5, so its global-memory latency hides behind the gradients of a plane.
+  // Per thread, the staged points it loads and their padded offsets within a plane are fixed:
+  // computed once.
   constexpr int PER = (SX * SY + VT - 1) / VT;
+  const int PXY = p.P[0] * p.P[1];
+  const float *W0 = p.Wp32, *W1 = p.Wp32 + p.NP, *W2 = p.Wp32 + 2 * p.NP;
+  int foff[PER];
+#pragma unroll
+  for (int j = 0; j < PER; j++) {
+    int e = threadIdx.x + j * VT;
+    int sx = e % SX, sy = e / SX;
+    int gx = min(x0 - 4 + sx, p.n[0] + 3), gy = min(y0 - 4 + sy, p.n[1] + 3);
+    foff[j] = (gy + p.g[1]) * p.P[0] + (gx + p.g[0]);
+  }
   float R[PER][3];
   auto fetch = [&](int z) {
+    const int zo = (z + p.g[2]) * PXY;
 #pragma unroll
     for (int j = 0; j < PER; j++) {
-      int e = threadIdx.x + j * VT;
-      if (e < SX * SY) {
-        int sx = e % SX, sy = e / SX;
-        int gx = min(x0 - 4 + sx, p.n[0] + 3), gy = min(y0 - 4 + sy, p.n[1] + 3);
-        long long s = pad_index(p, gx, gy, z);
-#pragma unroll
-        for (int c = 0; c < 3; c++) R[j][c] = p.Wp32[c * p.NP + s];
+      if (threadIdx.x + j * VT < SX * SY) {
+        const int o = zo + foff[j];
+        R[j][0] = W0[o];
+        R[j][1] = W1[o];
+        R[j][2] = W2[o];
       }
     }
   };
-  auto put = [&](int z) {
-    float *dst = ring + ((z + 8) % 5) * PLANE;
+  auto put = [&](int slot) {
+    float *dst = ring + slot * PLANE + threadIdx.x;
 #pragma unroll
     for (int j = 0; j < PER; j++) {
-      int e = threadIdx.x + j * VT;
-      if (e < SX * SY) {
+      if (threadIdx.x + j * VT < SX * SY) {
 #pragma unroll
-        for (int c = 0; c < 3; c++) dst[c * SX * SY + e] = R[j][c];
+        for (int c = 0; c < 3; c++) dst[c * SX * SY + j * VT] = R[j][c];
       }
     }
   };
@@ -1353,11 +1363,10 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
     else
       return ih[a];
   };
-  // gradients g[i][j] = du_i/dx_j at staged position (sx, sy) of plane c (ihz: its z metric)
-  auto grads = [&](const float *const pl[5], int sx, int sy, float ihz, float g[3][3],
-                   float u[3]) {
-    int e = sy * SX + sx;
-    const float ihx = ihat(0, x0 - 4 + sx), ihy = ihat(1, y0 - 4 + sy);
+  // gradients g[i][j] = du_i/dx_j at staged position (sx, sy) = offset e of plane c (ihx, ihy,
+  // ihz: the metrics there)
+  auto grads = [&](const float *const pl[5], int e, float ihx, float ihy, float ihz,
+                   float g[3][3], float u[3]) {
 #pragma unroll
     for (int i = 0; i < 3; i++) {
       const float *m = pl[2] + i * SX * SY + e;
@@ -1392,11 +1401,33 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
 #pragma unroll
     for (int k = 0; k < 4; k++) acc[o][k] = 0.f;
   const float ihx_own = ihat(0, X), ihy_own = ihat(1, Y);
+  // the halo point this thread evaluates each plane (threads below 4 TY + 4 TX): F_v,x at x
+  // offsets -2, -1, TX, TX+1 of a row, or F_v,y at y offsets -2, -1, TY, TY+1 of a column; its
+  // staged offset, its metrics and where its flux goes, fixed for the whole march
+  const int hkind = threadIdx.x < 4 * TY ? 1 : (threadIdx.x < 4 * TY + 4 * TX ? 2 : 0);
+  int he = 0, hout = 0;
+  float hihx = ih[0], hihy = ih[1];
+  if (hkind == 1) {
+    int r = threadIdx.x / 4, h = threadIdx.x % 4, px = h < 2 ? h : TX + h;  // 0,1,TX+2,TX+3
+    he = (r + 4) * SX + px + 2;
+    hout = r * PX + px;
+    hihx = ihat(0, x0 - 4 + px + 2);
+    hihy = ihat(1, y0 + r);
+  } else if (hkind == 2) {
+    int e2 = threadIdx.x - 4 * TY, col = e2 % TX, h = e2 / TX, py = h < 2 ? h : TY + h;
+    he = (py + 2) * SX + col + 4;
+    hout = py * TX + col;
+    hihx = ihat(0, x0 + col);
+    hihy = ihat(1, y0 - 4 + py + 2);
+  }
+  const int eown = (ty + 4) * SX + tx + 4;
   // inputs of the cell finished next (L, stage increment), loaded one plane ahead
+  const int NXY = p.n[0] * p.n[1];
+  const int town = Y * p.n[0] + X;  // interior offset within a plane (own columns)
   float Lnext[5], Dnext[5];
   auto fetch_cell = [&](int d) {
     if (own && d >= zs && d < ze) {
-      long long t = int_index(p, X, Y, d);
+      const long long t = (long long)d * NXY + town;
 #pragma unroll
       for (int cc = 0; cc < 5; cc++) {
         Lnext[cc] = p.L32[cc * p.N + t];
@@ -1405,22 +1436,31 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
     }
   };
 
+  // ring slot of plane z: (z + 8) mod 5, advanced incrementally
+  int slot = (zs - 4 + 8) % 5;
   for (int z = zs - 4; z <= zs; z++) {
     fetch(z);
-    put(z);
+    put(slot);
+    slot = slot == 4 ? 0 : slot + 1;
   }
   fetch(zs + 1);
+  // slot now belongs to plane zs + 1; planes c - 2 .. c + 2 for c = zs - 2 start at slot of
+  // plane zs - 4
+  int s0 = (zs - 4 + 8) % 5;
   __syncthreads();
   for (int c = zs - 2; c < ze + 2; c++) {
     // ring slots of planes c-2 .. c+2, once per plane
     const float *pl[5];
 #pragma unroll
-    for (int o = 0; o < 5; o++) pl[o] = ring + ((c + 6 + o) % 5) * PLANE;
+    for (int o = 0; o < 5; o++) {
+      int so = s0 + o;
+      pl[o] = ring + (so >= 5 ? so - 5 : so) * PLANE;
+    }
     // own cell: all three fluxes; halo points: F_v,x (x offsets -2,-1,32,33) or F_v,y
     const float ihz = ihat(2, c);
     {
       float g[3][3], u[3], f[4];
-      grads(pl, tx + 4, ty + 4, ihz, g, u);
+      grads(pl, eown, ihx_own, ihy_own, ihz, g, u);
       vflux(0, g, u, f);
 #pragma unroll
       for (int k = 0; k < 4; k++) fx[(k * TY + ty) * PX + tx + 2] = f[k];
@@ -1438,20 +1478,18 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
         acc[4][k] += zp2 * f[k];
       }
     }
-    for (int e = threadIdx.x; e < 4 * TY + 4 * TX; e += VT) {
+    static_assert(4 * TY + 4 * TX <= VT, "one halo point per thread at most");
+    if (hkind) {
       float g[3][3], u[3], f[4];
-      if (e < 4 * TY) {  // x-halo point
-        int r = e / 4, h = e % 4, px = h < 2 ? h : TX + h;  // 0,1,TX+2,TX+3
-        grads(pl, px + 2, r + 4, ihz, g, u);
+      grads(pl, he, hihx, hihy, ihz, g, u);
+      if (hkind == 1) {  // x-halo point
         vflux(0, g, u, f);
 #pragma unroll
-        for (int k = 0; k < 4; k++) fx[(k * TY + r) * PX + px] = f[k];
+        for (int k = 0; k < 4; k++) fx[k * TY * PX + hout] = f[k];
       } else {           // y-halo point
-        int e2 = e - 4 * TY, col = e2 % TX, h = e2 / TX, py = h < 2 ? h : TY + h;
-        grads(pl, col + 4, py + 2, ihz, g, u);
         vflux(1, g, u, f);
 #pragma unroll
-        for (int k = 0; k < 4; k++) fy[(k * PY + py) * TX + col] = f[k];
+        for (int k = 0; k < 4; k++) fy[k * PY * TX + hout] = f[k];
       }
     }
     __syncthreads();
@@ -1466,7 +1504,7 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
     // plane d = c - 2 is complete: viscous term, sponge, RK update
     int d = c - 2;
     if (own && d >= zs && d < ze) {
-      long long t = int_index(p, X, Y, d);
+      const long long t = (long long)d * NXY + town;
       float Lc[5];
 #pragma unroll
       for (int cc = 0; cc < 5; cc++) Lc[cc] = Lnext[cc];
@@ -1519,10 +1557,11 @@ __global__ void __launch_bounds__(vm::VT, VM_MIN_BLOCKS) k_visc_march32(Plan p, 
 #pragma unroll
     for (int k = 0; k < 4; k++) acc[4][k] = 0.f;
     if (c + 1 < ze + 2) {
-      put(c + 3);
+      put(s0);  // plane c + 3 takes the slot of plane c - 2
       if (c + 2 < ze + 2) fetch(c + 4);
       fetch_cell(c - 1);
     }
+    s0 = s0 == 4 ? 0 : s0 + 1;
     __syncthreads();
   }
 }
