@@ -220,6 +220,14 @@ int ibfsa_body_force(ibfsa_grid *g, double *host_force, double *host_power);
  * Synchronises the grid's stream. */
 int ibfsa_get_status(ibfsa_grid *g, int *host_flags);
 
+/* Self-test of the kernels' bounded waits (not part of the method; the paper has no
+ * counterpart): one thread block waits on a shared-memory barrier that no tensor copy will
+ * complete, gives up after the poll limit the convective kernels use, and reports
+ * IBFSA_STATUS_TIMEOUT in the grid's status word (read and cleared by ibfsa_get_status) through
+ * the same code path -- no fault, no trap, nothing left in flight; the grid stays usable.
+ * Asynchronous on the grid's stream. */
+int ibfsa_selftest_wait(ibfsa_grid *g);
+
 /* Instrumentation (not part of the method): launch counts per kernel class are always kept;
  * with profiling enabled every launch is bracketed by CUDA events on the grid's stream.
  * Classes, in order: 0 pad (ghosts, primitives, split speeds), 1 IB interpolation and penalty

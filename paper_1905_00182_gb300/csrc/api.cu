@@ -718,6 +718,12 @@ int ibfsa_body_force(ibfsa_grid *g, double *host_force, double *host_power) {
   return IBFSA_OK;
 }
 
+int ibfsa_selftest_wait(ibfsa_grid *g) {
+  if (!g) return fail(IBFSA_ERR_ARG, "NULL grid");
+  cudaError_t e = wait_selftest(g->g.p, g->g.stream);
+  return e == cudaSuccess ? IBFSA_OK : cuda_fail(e, "ibfsa_selftest_wait");
+}
+
 int ibfsa_get_status(ibfsa_grid *g, int *host_flags) {
   if (!g || !host_flags) return fail(IBFSA_ERR_ARG, "NULL argument");
   Grid &G = g->g;

@@ -161,6 +161,7 @@ cudaError_t fp32_mlp_sample(const Plan &p, const double *Q, int n_max, unsigned 
                             int attempts, float *stencils, float *targets, int *count,
                             cudaStream_t st);
 cudaError_t body_force(const Plan &p, const double *U, double *out, cudaStream_t st);
+cudaError_t wait_selftest(const Plan &p, cudaStream_t st);  // bounded-wait self-test (stage_fp32.cu)
 size_t mlp_image_offset();   // byte offset of the packed image inside a training state
 size_t mlp_image_bytes();
 cudaError_t fp32_probe(const Plan &p, const double *Q, int np, const double *xp, double *out,

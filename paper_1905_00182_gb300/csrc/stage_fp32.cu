@@ -817,6 +817,21 @@ struct TmaTile {
   static_assert(R == 32, "one warp spans the x-lines of a tile");
 };
 
+// Wait (bounded) for phase `parity` of the block's barrier; every thread of the block calls it.
+// On expiry the block reports IBFSA_STATUS_TIMEOUT, thread 0 waits once more (bounded) for
+// copies still in flight, and the function returns false: the caller then returns.
+__device__ __forceinline__ bool block_wait_or_report(const Plan &p, uint64_t *bar,
+                                                     uint32_t parity) {
+  if (__syncthreads_or(!tma::mbar_wait(bar, parity))) {
+    if (threadIdx.x == 0) {
+      atomicOr(p.status, IBFSA_STATUS_TIMEOUT);
+      tma::mbar_wait(bar, parity);
+    }
+    return false;
+  }
+  return true;
+}
+
 template <int DIM, int A, int SCHEME>
 __global__ void __launch_bounds__(THREADS, 5)
     k_conv32_tma(Plan p, const __grid_constant__ CUtensorMap tq,
@@ -853,13 +868,7 @@ __global__ void __launch_bounds__(THREADS, 5)
     tma::load_4d(in + NV * LEN * R, &tw, px, py, pz, A, bar);
     tma::load_4d(in + (NV + 1) * LEN * R, &tw, px, py, pz, DIM, bar);
   }
-  if (__syncthreads_or(!tma::mbar_wait(bar, 0))) {
-    if (threadIdx.x == 0) {
-      atomicOr(p.status, IBFSA_STATUS_TIMEOUT);
-      tma::mbar_wait(bar, 0);  // a second bounded wait for copies still in flight
-    }
-    return;
-  }
+  if (!block_wait_or_report(p, bar, 0)) return;
 
   // 1. f+-' of the staged cells l = 0 .. ncell+5 (cells seg0-3 .. seg0+ncell+2)
   const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
@@ -919,13 +928,7 @@ __global__ void __launch_bounds__(THREADS, 5)
     }
   }
   __syncthreads();
-  if (__syncthreads_or(!tma::mbar_wait(bar, 1))) {
-    if (threadIdx.x == 0) {
-      atomicOr(p.status, IBFSA_STATUS_TIMEOUT);
-      tma::mbar_wait(bar, 1);
-    }
-    return;
-  }
+  if (!block_wait_or_report(p, bar, 1)) return;
 
   // 3. L' = L' - (Fhat_{m+1/2} - Fhat_{m-1/2}) / (dx/dxi) on the copied tile, then stored back
   if (row_ok) {
@@ -1887,6 +1890,24 @@ cudaError_t fp32_mlp_sample(const Plan &p, const double *Q, int n_max, unsigned 
   else
     k_mlp_sample<3><<<blocks, threads, 0, st>>>(p, n_max, seed, attempts, cf, stencils, targets,
                                                count);
+  return cudaGetLastError();
+}
+
+// Self-test of the bounded wait: one block announces bytes on its barrier and issues no copy,
+// so the phase never completes; the block must give up after the poll limit, report
+// IBFSA_STATUS_TIMEOUT through the same path as the convective kernels, and end (nothing is in
+// flight when it exits).
+__global__ void __launch_bounds__(fp32_ns::THREADS) k_wait_selftest(Plan p) {
+  __shared__ __align__(8) uint64_t bar[1];
+  if (threadIdx.x == 0) tma::mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) tma::mbar_expect_tx(bar, 16);  // no copy will deliver these bytes
+  if (!fp32_ns::block_wait_or_report(p, bar, 0)) return;
+  if (threadIdx.x == 0) atomicOr(p.status, IBFSA_STATUS_NONFINITE);  // unreachable
+}
+
+cudaError_t wait_selftest(const Plan &p, cudaStream_t st) {
+  k_wait_selftest<<<1, fp32_ns::THREADS, 0, st>>>(p);
   return cudaGetLastError();
 }
 

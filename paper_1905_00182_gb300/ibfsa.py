@@ -46,6 +46,7 @@ EXPORTS = (
     "ibfsa_plate_destroy", "ibfsa_plate_set_state", "ibfsa_plate_get_state", "ibfsa_plate_step",
     "ibfsa_plate_markers", "ibfsa_plate_get_status", "ibfsa_fsi_step", "ibfsa_plate_force",
     "ibfsa_set_source", "ibfsa_set_time", "ibfsa_get_time", "ibfsa_set_mesh",
+    "ibfsa_selftest_wait",
 )
 MLP_NPARAM = 2403
 
@@ -161,6 +162,7 @@ def lib():
         L.ibfsa_set_source.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]
         L.ibfsa_set_time.argtypes = [_P, ctypes.c_double]
         L.ibfsa_set_mesh.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.ibfsa_selftest_wait.argtypes = [_P]
         L.ibfsa_get_time.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
         _lib = L
     return _lib
@@ -485,6 +487,11 @@ def ibfsa_set_mesh(g, a: int, x_nodes: int, dxdxi: int):
     """Stretched mesh along direction a: node coordinates and dx/dxi at i = -4 .. n+3 (pointers;
     both 0: uniform again)."""
     _check(lib().ibfsa_set_mesh(g, int(a), _P(x_nodes or None), _P(dxdxi or None)))
+
+
+def ibfsa_selftest_wait(g):
+    """Run the bounded-wait self-test on the grid's stream (it reports IBFSA_STATUS_TIMEOUT)."""
+    _check(lib().ibfsa_selftest_wait(g))
 
 
 def ibfsa_fsi_step(g, p, dt: float, nsteps: int = 1):
