@@ -77,6 +77,22 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     return LIB
 
 
+PIPE_RATES = os.path.join(HERE, "pipe_rates")
+
+
+def build_pipe_rates(force: bool = False) -> str:
+    """The standalone pipe-throughput probe (csrc/pipe_rates.cu): the FP64 and FP32 fused
+    multiply-add and the multi-function unit's rates the kernels' rooflines are quoted against."""
+    src = os.path.join(CSRC, "pipe_rates.cu")
+    if not force and os.path.exists(PIPE_RATES) and os.path.getmtime(PIPE_RATES) >= os.path.getmtime(src):
+        return PIPE_RATES
+    cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", PIPE_RATES]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on pipe_rates.cu:\n{r.stdout}\n{r.stderr}")
+    return PIPE_RATES
+
+
 if __name__ == "__main__":
     import sys
     print(build(force=True, verbose=True, extra=tuple(sys.argv[1:])))

@@ -179,78 +179,138 @@ __device__ __forceinline__ void candidates(const float x[5], float q[3]) {
 namespace ibfsa {
 namespace mlp {
 
-// gelu with the hardware tanh approximation (one MUFU operation, ~2^-11 relative error, below
-// the bfloat16 rounding that follows): used for inference inside the stencil kernels
-__device__ __forceinline__ float gelu_fast(float z) {
-  float u = z * (GELU_K + GELU_K * GELU_C * z * z), th;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(u));
-  float hz = 0.5f * z;
-  return fmaf(hz, th, hz);
+// Two gelus with the hardware tanh approximation (one MUFU operation each, ~2^-11 relative
+// error, below the bfloat16 rounding that follows), the rest on packed FP32x2 arithmetic:
+// u = z (K + (K C z) z) with the inner sum as one fused multiply-add, then 0.5 z + 0.5 z tanh(u);
+// packed to bf16x2 as the next layer's operand.  Used for inference inside the stencil kernels.
+__device__ __forceinline__ uint32_t gelu2_fast(float z0, float z1) {
+  const float2 z = make_float2(z0, z1);
+  const float2 a = __fmul2_rn(make_float2(GELU_K * GELU_C, GELU_K * GELU_C), z);
+  const float2 u = __fmul2_rn(z, __ffma2_rn(a, z, make_float2(GELU_K, GELU_K)));
+  float t0, t1;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(u.x));
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(u.y));
+  const float2 hz = __fmul2_rn(make_float2(0.5f, 0.5f), z);
+  const float2 g = __ffma2_rn(hz, make_float2(t0, t1), hz);
+  return pack2(g.x, g.y);
 }
 
 __device__ __forceinline__ void gelu_pack_fast(const float z[4][4], uint32_t A[2][4]) {
 #pragma unroll
   for (int s = 0; s < 2; s++) {
-    A[s][0] = pack2(gelu_fast(z[2 * s][0]), gelu_fast(z[2 * s][1]));
-    A[s][1] = pack2(gelu_fast(z[2 * s][2]), gelu_fast(z[2 * s][3]));
-    A[s][2] = pack2(gelu_fast(z[2 * s + 1][0]), gelu_fast(z[2 * s + 1][1]));
-    A[s][3] = pack2(gelu_fast(z[2 * s + 1][2]), gelu_fast(z[2 * s + 1][3]));
+    A[s][0] = gelu2_fast(z[2 * s][0], z[2 * s][1]);
+    A[s][1] = gelu2_fast(z[2 * s][2], z[2 * s][3]);
+    A[s][2] = gelu2_fast(z[2 * s + 1][0], z[2 * s + 1][1]);
+    A[s][3] = gelu2_fast(z[2 * s + 1][2], z[2 * s + 1][3]);
   }
 }
 
-// inference only: softmax weights of rows g (wa) and g+8 (wb) in lanes t == 0
-__device__ __forceinline__ void infer_tile(const unsigned char *img, const float xa[5],
-                                           const float xb[5], int g, int t, float wa[3],
-                                           float wb[3]) {
-  float z[4][4], z4[4];
-  uint32_t A0[1][4], A[2][4];
-  input_fragment(xa, xb, t, A0);
-  dense32<1>(z, A0, img, OFF_W1, 16, OFF_B1, g, t);
-  gelu_pack_fast(z, A);
-  dense32<2>(z, A, img, OFF_W2, 32, OFF_B2, g, t);
-  gelu_pack_fast(z, A);
-  dense32<2>(z, A, img, OFF_W3, 32, OFF_B3, g, t);
-  gelu_pack_fast(z, A);
-  logits(z4, A, img, g, t);
-  float l2a = __shfl_down_sync(0xffffffffu, z4[0], 1);
-  float l2b = __shfl_down_sync(0xffffffffu, z4[2], 1);
-  float ma = fmaxf(z4[0], fmaxf(z4[1], l2a)), mb = fmaxf(z4[2], fmaxf(z4[3], l2b));
-  float ea0 = __expf(z4[0] - ma), ea1 = __expf(z4[1] - ma), ea2 = __expf(l2a - ma);
-  float eb0 = __expf(z4[2] - mb), eb1 = __expf(z4[3] - mb), eb2 = __expf(l2b - mb);
-  float ia = 1.f / (ea0 + ea1 + ea2), ib = 1.f / (eb0 + eb1 + eb2);
-  wa[0] = ea0 * ia; wa[1] = ea1 * ia; wa[2] = ea2 * ia;
-  wb[0] = eb0 * ib; wb[1] = eb1 * ib; wb[2] = eb2 * ib;
+// D = A B + C with the accumulator input in separate registers (the bias, without copies)
+__device__ __forceinline__ void mma16816_c(float d[4], const uint32_t a[4], uint32_t b0,
+                                           uint32_t b1, float c0, float c1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%10,%11,%10,%11};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c0), "f"(c1));
 }
 
-// Weights for one stencil per lane, evaluated by the whole warp on the tensor cores (two
-// 16-row tiles: lanes 0..15 and 16..31).  x: this lane's normalised stencil; active: whether
-// this lane wants the network (tiles with no active lane are skipped).  Must be called by all
-// 32 lanes.  Active lanes get the network's three weights in w; the others keep w.
-__device__ __forceinline__ void warp_weights(const unsigned char *img, const float x[5],
-                                             bool active, float w[3]) {
+// One hidden layer (32 units, gelu) for the warp's two 16-row tiles at once: each weight
+// fragment is read from shared memory once and used by both tiles' products, and each n-tile of
+// 8 units is activated and packed into the next layer's operand as soon as it is accumulated
+// (n-tile j fills k-step j/2, fragment registers 2 (j mod 2) and 2 (j mod 2) + 1).
+template <int KSTEPS>
+__device__ __forceinline__ void hidden2(const unsigned char *img, int offW, int ldW, int offB,
+                                        const uint32_t (&Ain)[2][KSTEPS][4],
+                                        uint32_t (&Aout)[2][2][4], int g, int t) {
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const float b0 = ldb(img, offB, 8 * j + 2 * t), b1 = ldb(img, offB, 8 * j + 2 * t + 1);
+    float acc[2][4];
+#pragma unroll
+    for (int s = 0; s < KSTEPS; s++) {
+      const uint32_t w0 = ldw(img, offW, ldW, 8 * j + g, 16 * s + 2 * t);
+      const uint32_t w1 = ldw(img, offW, ldW, 8 * j + g, 16 * s + 2 * t + 8);
+#pragma unroll
+      for (int T = 0; T < 2; T++) {
+        if (s == 0) mma16816_c(acc[T], Ain[T][0], w0, w1, b0, b1);
+        else mma16816(acc[T], Ain[T][s], w0, w1);
+      }
+    }
+#pragma unroll
+    for (int T = 0; T < 2; T++) {
+      Aout[T][j >> 1][2 * (j & 1)] = gelu2_fast(acc[T][0], acc[T][1]);
+      Aout[T][j >> 1][2 * (j & 1) + 1] = gelu2_fast(acc[T][2], acc[T][3]);
+    }
+  }
+}
+
+// The network's three weights for one stencil per lane, the whole warp evaluating its two
+// 16-row tiles together on the tensor cores (lane 16 T + r is row r of tile T).  x: this lane's
+// normalised stencil.  Must be called by all 32 lanes; every lane gets the weights of its own
+// stencil (the caller keeps them where it wants the network).
+__device__ __forceinline__ void warp_weights2(const unsigned char *img, const float x[5],
+                                              float w[3]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  unsigned any = __ballot_sync(0xffffffffu, active);
+  // layer 1's operand: row g (+8) of tile T takes the bf16 pair k = 2t, 2t+1 of its stencil,
+  // (x0 x1), (x2 x3), (x4 0) for t = 0, 1, 2 and zeros for t = 3 and k >= 8
+  const uint32_t p0 = pack2(x[0], x[1]), p1 = pack2(x[2], x[3]), p2 = pack2(x[4], 0.f);
+  uint32_t A0[2][1][4];
 #pragma unroll
   for (int T = 0; T < 2; T++) {
-    if (((any >> (16 * T)) & 0xffffu) == 0u) continue;  // warp-uniform
-    float xa[5], xb[5];
 #pragma unroll
-    for (int j = 0; j < 5; j++) {
-      xa[j] = __shfl_sync(0xffffffffu, x[j], 16 * T + g);
-      xb[j] = __shfl_sync(0xffffffffu, x[j], 16 * T + g + 8);
+    for (int h = 0; h < 2; h++) {
+      const int src = 16 * T + g + 8 * h;
+      const uint32_t q0 = __shfl_sync(0xffffffffu, p0, src);
+      const uint32_t q1 = __shfl_sync(0xffffffffu, p1, src);
+      const uint32_t q2 = __shfl_sync(0xffffffffu, p2, src);
+      A0[T][0][h] = t == 0 ? q0 : (t == 1 ? q1 : (t == 2 ? q2 : 0u));
     }
-    float wa[3], wb[3];
-    infer_tile(img, xa, xb, g, t, wa, wb);
-    // row r of tile T belongs to lane 16 T + r; lane 4 (r mod 8) holds it (wa for r < 8)
-    int r = lane - 16 * T;
-    int src = 4 * (r & 7);
+    A0[T][0][2] = 0u;
+    A0[T][0][3] = 0u;
+  }
+  uint32_t Ab[2][2][4], Ac[2][2][4];
+  hidden2<1>(img, OFF_W1, 16, OFF_B1, A0, Ab, g, t);
+  hidden2<2>(img, OFF_W2, 32, OFF_B2, Ab, Ac, g, t);
+  hidden2<2>(img, OFF_W3, 32, OFF_B3, Ac, Ab, g, t);
+  // logits (n-tile 0: logits 0..7, 0..2 used): rows g / g+8 in c0, c1 / c2, c3 of lane 4g
+  // (logits 0, 1) and lane 4g + 1 (logit 2)
+  float z4[2][4];
+  {
+    const float b0 = ldb(img, OFF_B4, 2 * t), b1 = ldb(img, OFF_B4, 2 * t + 1);
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-      float va = __shfl_sync(0xffffffffu, wa[k], src);
-      float vb = __shfl_sync(0xffffffffu, wb[k], src);
-      if (active && r >= 0 && r < 16) w[k] = r < 8 ? va : vb;
+    for (int s = 0; s < 2; s++) {
+      const uint32_t w0 = ldw(img, OFF_W4, 32, g, 16 * s + 2 * t);
+      const uint32_t w1 = ldw(img, OFF_W4, 32, g, 16 * s + 2 * t + 8);
+#pragma unroll
+      for (int T = 0; T < 2; T++) {
+        if (s == 0) mma16816_c(z4[T], Ab[T][0], w0, w1, b0, b1);
+        else mma16816(z4[T], Ab[T][1], w0, w1);
+      }
     }
   }
+  // each lane gathers the three logits of its own stencil and takes their softmax
+  const int T = lane >> 4, r = lane & 15, s0 = 4 * (r & 7), hi = r >> 3;
+  float l[2][2][3];  // [tile][row half][logit]
+#pragma unroll
+  for (int u = 0; u < 2; u++) {
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      l[u][h][0] = __shfl_sync(0xffffffffu, z4[u][2 * h], s0);
+      l[u][h][1] = __shfl_sync(0xffffffffu, z4[u][2 * h + 1], s0);
+      l[u][h][2] = __shfl_sync(0xffffffffu, z4[u][2 * h], s0 + 1);
+    }
+  }
+  float v[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+    v[k] = T ? (hi ? l[1][1][k] : l[1][0][k]) : (hi ? l[0][1][k] : l[0][0][k]);
+  const float m = fmaxf(v[0], fmaxf(v[1], v[2]));
+  const float e0 = __expf(v[0] - m), e1 = __expf(v[1] - m), e2 = __expf(v[2] - m);
+  const float inv = __fdividef(1.f, e0 + e1 + e2);  // the sum lies in [1, 3]
+  w[0] = e0 * inv;
+  w[1] = e1 * inv;
+  w[2] = e2 * inv;
 }
 
 }  // namespace mlp

@@ -220,11 +220,12 @@ __device__ __forceinline__ float teno5_fast(const Plan &tw, float a, float b, fl
 // TENO5 at one face for both split fluxes at once on packed FP32x2 arithmetic (.x: the f+
 // stencil, .y: the f- stencil, each ordered upwind to downwind): smoothness indicators and the
 // linear combination for both sides in one instruction each; a side that fails the all-kept
-// test takes the full scalar TENO5.  Returns h+ + h-.
+// test takes the full scalar TENO5.  Returns each side's face value and whether it keeps all
+// three stencils (kx / ky: by the all-kept test or by the full cut-off).
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-__device__ __forceinline__ float teno5_pm_k(const Plan &tw, float2 a, float2 b, float2 c,
-                                            float2 d, float2 e, bool &kx, bool &ky) {
+__device__ __forceinline__ float2 teno5_sides(const Plan &tw, float2 a, float2 b, float2 c,
+                                              float2 d, float2 e, bool &kx, bool &ky) {
   float2 t0 = __fadd2_rn(__ffma2_rn(f2(-2.f), b, a), c);
   float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.f), c, b), d);
   float2 t2 = __fadd2_rn(__ffma2_rn(f2(-2.f), d, c), e);
@@ -243,16 +244,21 @@ __device__ __forceinline__ float teno5_pm_k(const Plan &tw, float2 a, float2 b, 
   lin = __ffma2_rn(f2(47.f / 60.f), c, lin);
   lin = __ffma2_rn(f2(27.f / 60.f), d, lin);
   lin = __ffma2_rn(f2(-3.f / 60.f), e, lin);
-  if (kx && ky) return lin.x + lin.y;
-  float hx = kx ? lin.x : teno5(tw, a.x, b.x, c.x, d.x, e.x);
-  float hy = ky ? lin.y : teno5(tw, a.y, b.y, c.y, d.y, e.y);
-  return hx + hy;
-}
-
-__device__ __forceinline__ float teno5_pm(const Plan &tw, float2 a, float2 b, float2 c,
-                                          float2 d, float2 e) {
-  bool kx, ky;
-  return teno5_pm_k(tw, a, b, c, d, e, kx, ky);
+  if (!kx) {
+    Cands k = candidates(a.x, b.x, c.x, d.x, e.x);
+    int mask = teno_mask(k);
+    const float *w = tw.teno_w32[mask];
+    lin.x = w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
+    kx = mask == 7;
+  }
+  if (!ky) {
+    Cands k = candidates(a.y, b.y, c.y, d.y, e.y);
+    int mask = teno_mask(k);
+    const float *w = tw.teno_w32[mask];
+    lin.y = w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
+    ky = mask == 7;
+  }
+  return lin;
 }
 
 // The same packed TENO5 with a warp-uniform slow path: every lane of the warp must call it.  The
@@ -388,27 +394,6 @@ struct Tile {
 template <int DIM, int A>
 constexpr size_t conv_smem() {
   return sizeof(float) * 2 * (DIM + 2) * Tile<A>::ROWS * Tile<A>::LEN;  // >= face-flux area
-}
-
-// learned weights: reconstruction of one stencil with the TENO5 guard; every lane of the warp
-// must call it (the network runs warp-wide on the tensor cores)
-__device__ __forceinline__ float recon_mlp(const Plan &p, const unsigned char *img, bool valid,
-                                           float a, float b, float c, float d, float e,
-                                           unsigned &used, unsigned &seen) {
-  Cands k = candidates(a, b, c, d, e);
-  int mask = teno_all_kept(k.b0, k.b1, k.b2) ? 7 : teno_mask(k);
-  float v[5] = {a, b, c, d, e}, x[5];
-  float amp = mlp::normalise(v, x);
-  bool elig = valid && mask == 7 && amp > p.mlp_floor;
-  const float *tw = p.teno_w32[mask];
-  float w[3] = {tw[0], tw[1], tw[2]};
-  mlp::warp_weights(img, x, elig, w);
-  unsigned ball = __ballot_sync(0xffffffffu, elig), vb = __ballot_sync(0xffffffffu, valid);
-  used += __popc(ball);
-  seen += __popc(vb);
-  // delta form: constant stencils are reproduced exactly whatever the weights
-  return elig ? c + w[0] * (k.q0 - c) + w[1] * (k.q1 - c) + w[2] * (k.q2 - c)
-              : w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
 }
 
 // split fluxes f+-' = (F' +- alpha q') / 2 along A of one staged cell, from q', u'_A and p';
@@ -603,12 +588,12 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
   if constexpr (SCHEME == IBFSA_MLP_TENO5) {
     unsigned char *img = reinterpret_cast<unsigned char *>(smf + 2 * NV * T::ROWS * T::LEN);
     unsigned used = 0, seen = 0;
-#pragma unroll
-    // Rolled loop over (pass, component) with one call site of the warp-wide network
-    // (unrolled, the network's code was copied 2 x NV x MAXP times and the kernel ran out of the
-    // instruction cache).  Both split-flux sides first take packed TENO5; where no lane of the
-    // warp would use the network (TENO5 keeping all three stencils and an amplitude above the
-    // floor), that is the result, else both sides go through the network's reconstruction.
+    // Rolled loop over (pass, component) and over the two split-flux sides, with one call site
+    // of the warp-wide network (unrolled, the network's code was copied 2 x NV x MAXP times and
+    // the kernel ran out of the instruction cache).  Both sides first take packed TENO5; a side
+    // on which some lane of the warp is eligible (TENO5 keeping all three stencils and an
+    // amplitude above the floor) then runs the network for all 32 lanes' stencils of that side
+    // and its eligible lanes take the delta-form reconstruction with the network's weights.
 #pragma unroll
     for (int ps = 0; ps < MAXP; ps++)
 #pragma unroll
@@ -625,37 +610,51 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
       const int b = fi + 2;
       const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
       const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
+      // .x: the f+ stencil, .y: the f- stencil, each ordered upwind to downwind
+      const float2 va = make_float2(fp[b - 2], fm[b + 3]), vb = make_float2(fp[b - 1], fm[b + 2]),
+                   vc = make_float2(fp[b], fm[b + 1]), vd = make_float2(fp[b + 1], fm[b]),
+                   ve = make_float2(fp[b + 2], fm[b - 1]);
       bool kx, ky;
-      float hlin = teno5_pm_k(p, make_float2(fp[b - 2], fm[b + 3]),
-                              make_float2(fp[b - 1], fm[b + 2]), make_float2(fp[b], fm[b + 1]),
-                              make_float2(fp[b + 1], fm[b]), make_float2(fp[b + 2], fm[b - 1]),
-                              kx, ky);
-      // eligibility exactly as recon_mlp decides it
-      bool el[2];
-#pragma unroll
-      for (int sgn = 0; sgn < 2; sgn++) {
-        const float *f = sgn ? fm : fp;
-        const int o = sgn ? b + 3 : b - 2, st = sgn ? -1 : 1;
-        float v0 = f[o], v1 = f[o + st], v2 = f[o + 2 * st], v3 = f[o + 3 * st], v4 = f[o + 4 * st];
-        float amp = fmaxf(fmaxf(fabsf(v0 - v2), fabsf(v1 - v2)), fmaxf(fabsf(v3 - v2), fabsf(v4 - v2)));
-        bool kept = sgn ? ky : kx;
-        if (!kept && valid) kept = teno_mask(candidates(v0, v1, v2, v3, v4)) == 7;
-        el[sgn] = valid && kept && amp > p.mlp_floor;
-      }
-      if (__ballot_sync(0xffffffffu, el[0] || el[1]) == 0u) {
-        Fh[ps][c] = hlin;
-        seen += 2 * __popc(__ballot_sync(0xffffffffu, valid));
-        continue;
-      }
-      float h = 0.f;
+      float2 h = teno5_sides(p, va, vb, vc, vd, ve, kx, ky);
+      // the normalised stencil x = (v - v_2)/amp, amp = max_j |v_j - v_2|
+      const float2 da = __ffma2_rn(f2(-1.f), vc, va), db = __ffma2_rn(f2(-1.f), vc, vb);
+      const float2 dd = __ffma2_rn(f2(-1.f), vc, vd), de = __ffma2_rn(f2(-1.f), vc, ve);
+      const float ax = fmaxf(fmaxf(fabsf(da.x), fabsf(db.x)), fmaxf(fabsf(dd.x), fabsf(de.x)));
+      const float ay = fmaxf(fmaxf(fabsf(da.y), fabsf(db.y)), fmaxf(fabsf(dd.y), fabsf(de.y)));
+      const bool ex = valid && kx && ax > p.mlp_floor, ey = valid && ky && ay > p.mlp_floor;
+      const unsigned bx = __ballot_sync(0xffffffffu, ex), by = __ballot_sync(0xffffffffu, ey);
+      seen += 2 * __popc(__ballot_sync(0xffffffffu, valid));
+      used += __popc(bx) + __popc(by);
 #pragma unroll 1
-      for (int sgn = 0; sgn < 2; sgn++) {
-        const float *f = sgn ? fm : fp;
-        const int o = sgn ? b + 3 : b - 2, st = sgn ? -1 : 1;
-        h += recon_mlp(p, img, valid, f[o], f[o + st], f[o + 2 * st], f[o + 3 * st],
-                       f[o + 4 * st], used, seen);
+      for (int sd = 0; sd < 2; sd++) {
+        if ((sd ? by : bx) == 0u) continue;  // warp-uniform
+        // this side's stencil, re-read from shared memory (nothing of it stays live across the
+        // network), ordered upwind to downwind
+        const volatile float *f = sd ? fm : fp;
+        const int o = sd ? b + 3 : b - 2, st = sd ? -1 : 1;
+        float v[5];
+#pragma unroll
+        for (int j = 0; j < 5; j++) v[j] = f[o + j * st];
+        float amp = 0.f;
+#pragma unroll
+        for (int j = 0; j < 5; j++) amp = fmaxf(amp, fabsf(v[j] - v[2]));
+        const float inv = amp > 1e-30f ? __fdividef(1.f, amp) : 0.f;
+        float x[5];
+#pragma unroll
+        for (int j = 0; j < 5; j++) x[j] = (v[j] - v[2]) * inv;
+        float w[3];
+        mlp::warp_weights2(img, x, w);
+        if (sd ? ey : ex) {
+#pragma unroll
+          for (int j = 0; j < 5; j++) v[j] = f[o + j * st];
+          // delta form: constant stencils are reproduced exactly whatever the weights
+          const Cands k = candidates(v[0], v[1], v[2], v[3], v[4]);
+          const float hs = v[2] + w[0] * (k.q0 - v[2]) + w[1] * (k.q1 - v[2]) + w[2] * (k.q2 - v[2]);
+          if (sd) h.y = hs;
+          else h.x = hs;
+        }
       }
-      Fh[ps][c] = h;
+      Fh[ps][c] = h.x + h.y;
     }
     if ((threadIdx.x & 31) == 0 && seen) {
       atomicAdd(&p.mlp_counts[0], (unsigned long long)used);
