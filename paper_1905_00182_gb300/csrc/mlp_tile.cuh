@@ -179,10 +179,13 @@ __device__ __forceinline__ void candidates(const float x[5], float q[3]) {
 namespace ibfsa {
 namespace mlp {
 
-// Two gelus with the hardware tanh approximation (one MUFU operation each, ~2^-11 relative
-// error, below the bfloat16 rounding that follows), the rest on packed FP32x2 arithmetic:
-// u = z (K + (K C z) z) with the inner sum as one fused multiply-add, then 0.5 z + 0.5 z tanh(u);
-// packed to bf16x2 as the next layer's operand.  Used for inference inside the stencil kernels.
+// Two activations with the hardware tanh approximation (one MUFU operation each, ~2^-11
+// relative error, below the bfloat16 rounding that follows), the rest on packed FP32x2
+// arithmetic: u = z (K + (K C z) z) with the inner sum as one fused multiply-add, then
+// z + z tanh(u) = 2 gelu(z), packed to bf16x2 as the next layer's operand.  The factor 2 is
+// taken back exactly by the halved weights of the next layer in the inference image
+// (stage_inference_image): a power of two commutes with every rounding on the way.  Used for
+// inference inside the stencil kernels.
 __device__ __forceinline__ uint32_t gelu2_fast(float z0, float z1) {
   const float2 z = make_float2(z0, z1);
   const float2 a = __fmul2_rn(make_float2(GELU_K * GELU_C, GELU_K * GELU_C), z);
@@ -190,18 +193,28 @@ __device__ __forceinline__ uint32_t gelu2_fast(float z0, float z1) {
   float t0, t1;
   asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(u.x));
   asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(u.y));
-  const float2 hz = __fmul2_rn(make_float2(0.5f, 0.5f), z);
-  const float2 g = __ffma2_rn(hz, make_float2(t0, t1), hz);
+  const float2 g = __ffma2_rn(z, make_float2(t0, t1), z);
   return pack2(g.x, g.y);
 }
 
-__device__ __forceinline__ void gelu_pack_fast(const float z[4][4], uint32_t A[2][4]) {
+// Copy of the packed parameter image into shared memory for inference, with the weights of
+// layers 2, 3 and 4 halved (bfloat16 times 0.5 is exact above 2^-126), to take the activations
+// of gelu2_fast (twice gelu) back to gelu.  Called by all threads of the block.
+__device__ __forceinline__ void stage_inference_image(uint4 *dst, const uint4 *src, int tid,
+                                                      int nthreads) {
+  for (int i = tid; i < PACKED_BYTES / 16; i += nthreads) {
+    uint4 v = src[i];
+    if (i >= OFF_W2 / 16 && i < OFF_W2T / 16) {
+      uint32_t *w = reinterpret_cast<uint32_t *>(&v);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(0.5f, 0.5f);
 #pragma unroll
-  for (int s = 0; s < 2; s++) {
-    A[s][0] = gelu2_fast(z[2 * s][0], z[2 * s][1]);
-    A[s][1] = gelu2_fast(z[2 * s][2], z[2 * s][3]);
-    A[s][2] = gelu2_fast(z[2 * s + 1][0], z[2 * s + 1][1]);
-    A[s][3] = gelu2_fast(z[2 * s + 1][2], z[2 * s + 1][3]);
+      for (int k = 0; k < 4; k++) {
+        __nv_bfloat162 x = *reinterpret_cast<__nv_bfloat162 *>(&w[k]);
+        x = __hmul2(x, h);
+        w[k] = *reinterpret_cast<uint32_t *>(&x);
+      }
+    }
+    dst[i] = v;
   }
 }
 

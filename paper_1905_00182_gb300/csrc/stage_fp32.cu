@@ -549,9 +549,8 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
   const float *Wpr = p.Wp32 + (size_t)DIM * p.NP;
 
   if constexpr (SCHEME == IBFSA_MLP_TENO5) {
-    uint4 *dst = reinterpret_cast<uint4 *>(smf + 2 * NV * T::ROWS * T::LEN);
-    const uint4 *src = reinterpret_cast<const uint4 *>(p.mlp_img);
-    for (int i = threadIdx.x; i < mlp::PACKED_BYTES / 16; i += THREADS) dst[i] = src[i];
+    mlp::stage_inference_image(reinterpret_cast<uint4 *>(smf + 2 * NV * T::ROWS * T::LEN),
+                               reinterpret_cast<const uint4 *>(p.mlp_img), threadIdx.x, THREADS);
   }
   // 1. f+-' of the staged cells (seg0-3 .. seg0+ncell+2)
   constexpr int S1 = A == 0 ? (T::LEN + 31) / 32 : (T::ROWS * T::LEN + THREADS - 1) / THREADS;
