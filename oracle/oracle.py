@@ -214,13 +214,13 @@ def rhs(spec, Q, X=None, U=None, dS=None, xi=None, return_markers=False, t=0.0, 
     return L
 
 
-def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None, mlp=None):
+def rhs_given_alpha(spec, Q, alpha, X=None, U=None, dS=None, xi=None, mlp=None, charwise=False):
     """Right-hand side with the split speeds alpha[3] supplied (for crops of a large state)."""
     Q = _f64(Q)
     nm, X, U, dS, xi = _markers(spec, X, U, dS, xi)
     L = np.zeros_like(Q)
     a = _f64(np.asarray(alpha, dtype=np.float64).reshape(3))
-    d = desc(spec, mlp=mlp)
+    d = desc(spec, charwise=charwise, mlp=mlp)
     rc = lib().orc_rhs_given_alpha(ctypes.byref(d), _p(Q), nm, _p(X), _p(U), _p(dS), _p(xi),
                                    _p(L), _p(a))
     if rc != ORC_OK:
