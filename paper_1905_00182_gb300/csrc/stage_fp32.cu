@@ -261,19 +261,27 @@ __device__ __forceinline__ float2 teno5_sides(const Plan &tw, float2 a, float2 b
   return lin;
 }
 
-// The same packed TENO5 with a warp-uniform slow path: every lane of the warp must call it.  The
-// linear (all-kept) result is computed without branches; only when some lane of the warp has a
-// side that cuts a stencil does the whole warp enter the full TENO5 (a uniform branch, no
-// divergence to reconverge).  The all-kept test is scale-invariant, so the indicators are
-// taken times 4, (13/3) t^2 + u^2 (one multiplication fewer each), with the floor 4e-30.
-__device__ __forceinline__ float teno5_pm_warp(const Plan &tw, float2 a, float2 b, float2 c,
-                                               float2 d, float2 e) {
-  float2 t0 = __fadd2_rn(__ffma2_rn(f2(-2.f), b, a), c);
-  float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.f), c, b), d);
-  float2 t2 = __fadd2_rn(__ffma2_rn(f2(-2.f), d, c), e);
-  float2 u0 = __ffma2_rn(f2(3.f), c, __ffma2_rn(f2(-4.f), b, a));
-  float2 u1 = __ffma2_rn(f2(-1.f), d, b);
-  float2 u2 = __ffma2_rn(f2(3.f), c, __ffma2_rn(f2(-4.f), d, e));
+// TENO5 at one face for both split fluxes on packed FP32x2 arithmetic, with a warp-uniform slow
+// path: every lane of the warp must call it.  The input is the interleaved face stencil
+// z_k = (f+ at staged cell i+k, f- at staged cell i+k+1), k = 0..4, of the face between staged
+// cells i+2 and i+3: the .x lanes are the f+ stencil upwind to downwind, the .y lanes the f-
+// stencil downwind to upwind, so one 8-byte load per k fetches both sides.  With the f- stencil
+// reversed, the packed indicator of z0 z1 z2 is (beta_0+, beta_2-) and that of z2 z3 z4 is
+// (beta_2+, beta_0-) (the second differences and the squared one-sided differences are
+// symmetric under the reversal), so tau5 and the all-kept test are those of each side; the
+// linear combination takes per-lane coefficient pairs.  The all-kept test is scale-invariant, so
+// the indicators are taken times 4, (13/3) t^2 + u^2 (one multiplication fewer each), with the
+// floor 4e-30.  The linear (all-kept) result is computed without branches; only when some lane
+// of the warp has a side that cuts a stencil does the whole warp enter the full TENO5 (a uniform
+// branch, no divergence to reconverge).
+__device__ __forceinline__ float teno5_pz_warp(const Plan &tw, float2 z0, float2 z1, float2 z2,
+                                               float2 z3, float2 z4) {
+  float2 t0 = __fadd2_rn(__ffma2_rn(f2(-2.f), z1, z0), z2);
+  float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.f), z2, z1), z3);
+  float2 t2 = __fadd2_rn(__ffma2_rn(f2(-2.f), z3, z2), z4);
+  float2 u0 = __ffma2_rn(f2(3.f), z2, __ffma2_rn(f2(-4.f), z1, z0));
+  float2 u1 = __ffma2_rn(f2(-1.f), z3, z1);
+  float2 u2 = __ffma2_rn(f2(3.f), z2, __ffma2_rn(f2(-4.f), z3, z4));
   const float2 k13 = f2(13.f / 3.f);
   float2 b0 = __ffma2_rn(__fmul2_rn(k13, t0), t0, __fmul2_rn(u0, u0));
   float2 b1 = __ffma2_rn(__fmul2_rn(k13, t1), t1, __fmul2_rn(u1, u1));
@@ -281,15 +289,15 @@ __device__ __forceinline__ float teno5_pm_warp(const Plan &tw, float2 a, float2 
   float2 tau = __ffma2_rn(f2(-1.f), b2, b0);
   const bool kx = fabsf(tau.x) <= fmaf(4.f, fminf(b0.x, fminf(b1.x, b2.x)), 1.6e-29f);
   const bool ky = fabsf(tau.y) <= fmaf(4.f, fminf(b0.y, fminf(b1.y, b2.y)), 1.6e-29f);
-  float2 lin = __fmul2_rn(f2(2.f / 60.f), a);
-  lin = __ffma2_rn(f2(-13.f / 60.f), b, lin);
-  lin = __ffma2_rn(f2(47.f / 60.f), c, lin);
-  lin = __ffma2_rn(f2(27.f / 60.f), d, lin);
-  lin = __ffma2_rn(f2(-3.f / 60.f), e, lin);
+  float2 lin = __fmul2_rn(make_float2(2.f / 60.f, -3.f / 60.f), z0);
+  lin = __ffma2_rn(make_float2(-13.f / 60.f, 27.f / 60.f), z1, lin);
+  lin = __ffma2_rn(f2(47.f / 60.f), z2, lin);
+  lin = __ffma2_rn(make_float2(27.f / 60.f, -13.f / 60.f), z3, lin);
+  lin = __ffma2_rn(make_float2(-3.f / 60.f, 2.f / 60.f), z4, lin);
   float h = lin.x + lin.y;
   if (__any_sync(0xffffffffu, !(kx && ky))) {
-    float hx = kx ? lin.x : teno5(tw, a.x, b.x, c.x, d.x, e.x);
-    float hy = ky ? lin.y : teno5(tw, a.y, b.y, c.y, d.y, e.y);
+    float hx = kx ? lin.x : teno5(tw, z0.x, z1.x, z2.x, z3.x, z4.x);
+    float hy = ky ? lin.y : teno5(tw, z4.y, z3.y, z2.y, z1.y, z0.y);
     h = hx + hy;
   }
   return h;
@@ -509,6 +517,9 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
   // 32 lanes hit 32 different banks
   constexpr int FST = A == 0 ? T::FACES : T::FACES + 1;
   extern __shared__ float smf[];
+  // component-wise TENO5 stages the interleaved face stencils z_l = (f+ at l, f- at l+1),
+  // [NV][ROWS][LEN] float2 (teno5_pz_warp); the other schemes f+ and f- apart, [NV][ROWS][LEN]
+  constexpr bool ZL = SCHEME == IBFSA_TENO5 && !CHAR;
   float *sfp = smf;
   float *sfm = smf + NV * T::ROWS * T::LEN;
   const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
@@ -573,10 +584,19 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
 #pragma unroll
     for (int c = 0; c < NV; c++) q[c] = p.Qp32[(size_t)c * p.NP + s];
     split_cell<DIM, A>(fs, alpha, q, Wa[s], Wpr[s], fpv, fmv);
+    if constexpr (ZL) {
 #pragma unroll
-    for (int c = 0; c < NV; c++) {
-      sfp[(c * T::ROWS + row) * T::LEN + l] = fpv[c];
-      sfm[(c * T::ROWS + row) * T::LEN + l] = fmv[c];
+      for (int c = 0; c < NV; c++) {
+        float2 *zr = reinterpret_cast<float2 *>(smf) + (c * T::ROWS + row) * T::LEN;
+        zr[l].x = fpv[c];
+        if (l > 0) zr[l - 1].y = fmv[c];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NV; c++) {
+        sfp[(c * T::ROWS + row) * T::LEN + l] = fpv[c];
+        sfm[(c * T::ROWS + row) * T::LEN + l] = fmv[c];
+      }
     }
   }
   __syncthreads();
@@ -725,15 +745,11 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
           fi = 0;
           if (row >= nrow) row = 0;
         }
-        int b = fi + 2;
+        // face fi + 1/2 - 1 between staged cells fi + 2 and fi + 3: z_fi .. z_fi+4
 #pragma unroll
         for (int c = 0; c < NV; c++) {
-          const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
-          const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
-          Fh[ps][c] = teno5_pm_warp(p, make_float2(fp[b - 2], fm[b + 3]),
-                                    make_float2(fp[b - 1], fm[b + 2]),
-                                    make_float2(fp[b], fm[b + 1]), make_float2(fp[b + 1], fm[b]),
-                                    make_float2(fp[b + 2], fm[b - 1]));
+          const float2 *z = reinterpret_cast<const float2 *>(smf) + (c * T::ROWS + row) * T::LEN + fi;
+          Fh[ps][c] = teno5_pz_warp(p, z[0], z[1], z[2], z[3], z[4]);
         }
       } else if (e < T::ROWS * T::FACES && row < nrow && fi < nface) {
         int b = fi + 2;
@@ -878,10 +894,20 @@ __global__ void __launch_bounds__(THREADS, 5)
       for (int c = 0; c < NV; c++) q[c] = in[(c * LEN + l) * R + lane];
       split_cell<DIM, A>(fs, alpha, q, in[(NV * LEN + l) * R + lane],
                          in[((NV + 1) * LEN + l) * R + lane], fpv, fmv);
+      if constexpr (SCHEME == IBFSA_TENO5) {
+        // interleaved face stencils z_l = (f+ at l, f- at l+1), [NV][LEN-1][R] float2
+        float2 *Z = reinterpret_cast<float2 *>(sfp);
 #pragma unroll
-      for (int c = 0; c < NV; c++) {
-        if (l < LEN - 1) sfp[(c * (LEN - 1) + l) * R + lane] = fpv[c];
-        if (l > 0) sfm[(c * (LEN - 1) + l - 1) * R + lane] = fmv[c];
+        for (int c = 0; c < NV; c++) {
+          if (l < LEN - 1) Z[(c * (LEN - 1) + l) * R + lane].x = fpv[c];
+          if (l > 0) Z[(c * (LEN - 1) + l - 1) * R + lane].y = fmv[c];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NV; c++) {
+          if (l < LEN - 1) sfp[(c * (LEN - 1) + l) * R + lane] = fpv[c];
+          if (l > 0) sfm[(c * (LEN - 1) + l - 1) * R + lane] = fmv[c];
+        }
       }
     }
   }
@@ -902,16 +928,15 @@ __global__ void __launch_bounds__(THREADS, 5)
     if (fi < nface) {
 #pragma unroll
       for (int c = 0; c < NV; c++) {
-        const float *fp = sfp + (c * (LEN - 1) + fi) * R + lane;
-        const float *fm = sfm + (c * (LEN - 1) + fi) * R + lane;   // f- of staged cell fi+1
-        if constexpr (SCHEME == IBFSA_TENO5)  // fi is the same for the whole warp
-          Fh[ps][c] = teno5_pm_warp(p, make_float2(fp[0], fm[4 * R]),
-                                    make_float2(fp[R], fm[3 * R]),
-                                    make_float2(fp[2 * R], fm[2 * R]),
-                                    make_float2(fp[3 * R], fm[R]), make_float2(fp[4 * R], fm[0]));
-        else
+        if constexpr (SCHEME == IBFSA_TENO5) {  // fi is the same for the whole warp
+          const float2 *z = reinterpret_cast<const float2 *>(sfp) + (c * (LEN - 1) + fi) * R + lane;
+          Fh[ps][c] = teno5_pz_warp(p, z[0], z[R], z[2 * R], z[3 * R], z[4 * R]);
+        } else {
+          const float *fp = sfp + (c * (LEN - 1) + fi) * R + lane;
+          const float *fm = sfm + (c * (LEN - 1) + fi) * R + lane;   // f- of staged cell fi+1
           Fh[ps][c] = recon<SCHEME>(p, fp[0], fp[R], fp[2 * R], fp[3 * R], fp[4 * R]) +
                       recon<SCHEME>(p, fm[4 * R], fm[3 * R], fm[2 * R], fm[R], fm[0]);
+        }
       }
     }
   }
