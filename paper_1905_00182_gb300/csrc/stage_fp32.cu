@@ -303,6 +303,48 @@ __device__ __forceinline__ float teno5_pz_warp(const Plan &tw, float2 z0, float2
   return h;
 }
 
+// teno5_pz_warp per side: returns (h+, h-) and whether each side keeps all three stencils (by
+// the all-kept test or, where that fails, by the full cut-off).  Every lane of the warp must call
+// it.
+__device__ __forceinline__ float2 teno5_pz_sides(const Plan &tw, float2 z0, float2 z1, float2 z2,
+                                                 float2 z3, float2 z4, bool &kx, bool &ky) {
+  float2 t0 = __fadd2_rn(__ffma2_rn(f2(-2.f), z1, z0), z2);
+  float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.f), z2, z1), z3);
+  float2 t2 = __fadd2_rn(__ffma2_rn(f2(-2.f), z3, z2), z4);
+  float2 u0 = __ffma2_rn(f2(3.f), z2, __ffma2_rn(f2(-4.f), z1, z0));
+  float2 u1 = __ffma2_rn(f2(-1.f), z3, z1);
+  float2 u2 = __ffma2_rn(f2(3.f), z2, __ffma2_rn(f2(-4.f), z3, z4));
+  const float2 k13 = f2(13.f / 3.f);
+  float2 b0 = __ffma2_rn(__fmul2_rn(k13, t0), t0, __fmul2_rn(u0, u0));
+  float2 b1 = __ffma2_rn(__fmul2_rn(k13, t1), t1, __fmul2_rn(u1, u1));
+  float2 b2 = __ffma2_rn(__fmul2_rn(k13, t2), t2, __fmul2_rn(u2, u2));
+  float2 tau = __ffma2_rn(f2(-1.f), b2, b0);
+  kx = fabsf(tau.x) <= fmaf(4.f, fminf(b0.x, fminf(b1.x, b2.x)), 1.6e-29f);
+  ky = fabsf(tau.y) <= fmaf(4.f, fminf(b0.y, fminf(b1.y, b2.y)), 1.6e-29f);
+  float2 lin = __fmul2_rn(make_float2(2.f / 60.f, -3.f / 60.f), z0);
+  lin = __ffma2_rn(make_float2(-13.f / 60.f, 27.f / 60.f), z1, lin);
+  lin = __ffma2_rn(f2(47.f / 60.f), z2, lin);
+  lin = __ffma2_rn(make_float2(27.f / 60.f, -13.f / 60.f), z3, lin);
+  lin = __ffma2_rn(make_float2(-3.f / 60.f, 2.f / 60.f), z4, lin);
+  if (__any_sync(0xffffffffu, !(kx && ky))) {
+    if (!kx) {
+      const Cands k = candidates(z0.x, z1.x, z2.x, z3.x, z4.x);
+      const int mask = teno_mask(k);
+      const float *w = tw.teno_w32[mask];
+      lin.x = w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
+      kx = mask == 7;
+    }
+    if (!ky) {
+      const Cands k = candidates(z4.y, z3.y, z2.y, z1.y, z0.y);
+      const int mask = teno_mask(k);
+      const float *w = tw.teno_w32[mask];
+      lin.y = w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
+      ky = mask == 7;
+    }
+  }
+  return lin;
+}
+
 template <int SCHEME>
 __device__ __forceinline__ float recon(const Plan &tw, float a, float b, float c, float d,
                                        float e) {
@@ -517,9 +559,10 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
   // 32 lanes hit 32 different banks
   constexpr int FST = A == 0 ? T::FACES : T::FACES + 1;
   extern __shared__ float smf[];
-  // component-wise TENO5 stages the interleaved face stencils z_l = (f+ at l, f- at l+1),
-  // [NV][ROWS][LEN] float2 (teno5_pz_warp); the other schemes f+ and f- apart, [NV][ROWS][LEN]
-  constexpr bool ZL = SCHEME == IBFSA_TENO5 && !CHAR;
+  // component-wise TENO5 and the learned weights stage the interleaved face stencils
+  // z_l = (f+ at l, f- at l+1), [NV][ROWS][LEN] float2 (teno5_pz_warp); the other schemes f+ and
+  // f- apart, [NV][ROWS][LEN]
+  constexpr bool ZL = (SCHEME == IBFSA_TENO5 || SCHEME == IBFSA_MLP_TENO5) && !CHAR;
   float *sfp = smf;
   float *sfm = smf + NV * T::ROWS * T::LEN;
   const float alpha = (float)__longlong_as_double((long long)p.alpha_bits[A]);
@@ -607,74 +650,98 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
   if constexpr (SCHEME == IBFSA_MLP_TENO5) {
     unsigned char *img = reinterpret_cast<unsigned char *>(smf + 2 * NV * T::ROWS * T::LEN);
     unsigned used = 0, seen = 0;
-    // Rolled loop over (pass, component) and over the two split-flux sides, with one call site
-    // of the warp-wide network (unrolled, the network's code was copied 2 x NV x MAXP times and
-    // the kernel ran out of the instruction cache).  Both sides first take packed TENO5; a side
-    // on which some lane of the warp is eligible (TENO5 keeping all three stencils and an
-    // amplitude above the floor) then runs the network for all 32 lanes' stencils of that side
-    // and its eligible lanes take the delta-form reconstruction with the network's weights.
+    // Two phases.  First, unrolled as the component-wise pass, packed TENO5 at every face and the
+    // eligibility of each side (TENO5 keeping all three stencils and an amplitude above the
+    // floor), one bit per (pass, component, side).  Then a rolled loop over (pass, component)
+    // with one call site of the warp-wide network (unrolled, the network's code was copied
+    // 2 x NV x MAXP times and the kernel ran out of the instruction cache) visits only the faces
+    // where some lane of the warp is eligible: a side with an eligible lane runs the network for
+    // all 32 lanes' stencils of that side, and its eligible lanes take the delta-form
+    // reconstruction with the network's weights.
+    static_assert(2 * MAXP * NV <= 32, "one eligibility bit per (pass, component, side)");
+    const float2 *Z = reinterpret_cast<const float2 *>(smf);
+    unsigned emask = 0;
 #pragma unroll
-    for (int ps = 0; ps < MAXP; ps++)
+    for (int ps = 0; ps < MAXP; ps++) {
+      int e = threadIdx.x + ps * THREADS;
+      int row, fi;
+      if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
+      else { row = e % T::ROWS; fi = e / T::ROWS; }
+      const bool valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
+      if (!valid) { row = 0; fi = 0; }  // in-bounds reads; results discarded
+      seen += valid ? 2 * NV : 0;
 #pragma unroll
-      for (int c = 0; c < NV; c++) Fh[ps][c] = 0.f;
+      for (int c = 0; c < NV; c++) {
+        const float2 *z = Z + (c * T::ROWS + row) * T::LEN + fi;
+        const float2 z0 = z[0], z1 = z[1], z2 = z[2], z3 = z[3], z4 = z[4];
+        bool kx, ky;
+        const float2 h = teno5_pz_sides(p, z0, z1, z2, z3, z4, kx, ky);
+        Fh[ps][c] = h.x + h.y;
+        // amplitude max_j |v_j - v_2| of each side (the same set of values in either order)
+        const float2 d0 = __ffma2_rn(f2(-1.f), z2, z0), d1 = __ffma2_rn(f2(-1.f), z2, z1);
+        const float2 d3 = __ffma2_rn(f2(-1.f), z2, z3), d4 = __ffma2_rn(f2(-1.f), z2, z4);
+        const float ax = fmaxf(fmaxf(fabsf(d0.x), fabsf(d1.x)), fmaxf(fabsf(d3.x), fabsf(d4.x)));
+        const float ay = fmaxf(fmaxf(fabsf(d0.y), fabsf(d1.y)), fmaxf(fabsf(d3.y), fabsf(d4.y)));
+        const bool ex = valid && kx && ax > p.mlp_floor, ey = valid && ky && ay > p.mlp_floor;
+        const int j = 2 * (ps * NV + c);
+        emask |= (ex ? 1u << j : 0u) | (ey ? 2u << j : 0u);
+      }
+    }
+    used = __popc(emask);
 #pragma unroll 1
     for (int it = 0; it < MAXP * NV; it++) {
+      const unsigned bits = (emask >> (2 * it)) & 3u;
+      const unsigned bx = __ballot_sync(0xffffffffu, bits & 1u);
+      const unsigned by = __ballot_sync(0xffffffffu, bits & 2u);
+      if ((bx | by) == 0u) continue;  // warp-uniform
       const int ps = it / NV, c = it % NV;
       int e = threadIdx.x + ps * THREADS;
       int row, fi;
       if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
       else { row = e % T::ROWS; fi = e / T::ROWS; }
-      bool valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
-      if (!valid) { row = 0; fi = 0; }  // in-bounds reads; results discarded
-      const int b = fi + 2;
-      const float *fp = sfp + (c * T::ROWS + row) * T::LEN;
-      const float *fm = sfm + (c * T::ROWS + row) * T::LEN;
-      // .x: the f+ stencil, .y: the f- stencil, each ordered upwind to downwind
-      const float2 va = make_float2(fp[b - 2], fm[b + 3]), vb = make_float2(fp[b - 1], fm[b + 2]),
-                   vc = make_float2(fp[b], fm[b + 1]), vd = make_float2(fp[b + 1], fm[b]),
-                   ve = make_float2(fp[b + 2], fm[b - 1]);
-      bool kx, ky;
-      float2 h = teno5_sides(p, va, vb, vc, vd, ve, kx, ky);
-      // the normalised stencil x = (v - v_2)/amp, amp = max_j |v_j - v_2|
-      const float2 da = __ffma2_rn(f2(-1.f), vc, va), db = __ffma2_rn(f2(-1.f), vc, vb);
-      const float2 dd = __ffma2_rn(f2(-1.f), vc, vd), de = __ffma2_rn(f2(-1.f), vc, ve);
-      const float ax = fmaxf(fmaxf(fabsf(da.x), fabsf(db.x)), fmaxf(fabsf(dd.x), fabsf(de.x)));
-      const float ay = fmaxf(fmaxf(fabsf(da.y), fabsf(db.y)), fmaxf(fabsf(dd.y), fabsf(de.y)));
-      const bool ex = valid && kx && ax > p.mlp_floor, ey = valid && ky && ay > p.mlp_floor;
-      const unsigned bx = __ballot_sync(0xffffffffu, ex), by = __ballot_sync(0xffffffffu, ey);
-      seen += 2 * __popc(__ballot_sync(0xffffffffu, valid));
-      used += __popc(bx) + __popc(by);
+      const bool valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
+      if (!valid) { row = 0; fi = 0; }
+      const float2 *z = Z + (c * T::ROWS + row) * T::LEN + fi;
+      // phase 1's TENO5 values again, where some lane keeps one of them (a side it is not
+      // eligible on): warp-uniform
+      float2 h = make_float2(0.f, 0.f);
+      if (__any_sync(0xffffffffu, bits != 3u)) {
+        bool kx, ky;
+        h = teno5_pz_sides(p, z[0], z[1], z[2], z[3], z[4], kx, ky);
+      }
 #pragma unroll 1
       for (int sd = 0; sd < 2; sd++) {
         if ((sd ? by : bx) == 0u) continue;  // warp-uniform
-        // this side's stencil, re-read from shared memory (nothing of it stays live across the
-        // network), ordered upwind to downwind
-        const volatile float *f = sd ? fm : fp;
-        const int o = sd ? b + 3 : b - 2, st = sd ? -1 : 1;
+        // this side's stencil upwind to downwind, re-read from shared memory (nothing of it
+        // stays live across the network): f+ = z_0..z_4 .x, f- = z_4..z_0 .y
+        const volatile float *f = reinterpret_cast<const volatile float *>(z) + sd;
+        const int o = sd ? 8 : 0, st = sd ? -2 : 2;
         float v[5];
 #pragma unroll
-        for (int j = 0; j < 5; j++) v[j] = f[o + j * st];
+        for (int k = 0; k < 5; k++) v[k] = f[o + k * st];
         float amp = 0.f;
 #pragma unroll
-        for (int j = 0; j < 5; j++) amp = fmaxf(amp, fabsf(v[j] - v[2]));
+        for (int k = 0; k < 5; k++) amp = fmaxf(amp, fabsf(v[k] - v[2]));
         const float inv = amp > 1e-30f ? __fdividef(1.f, amp) : 0.f;
         float x[5];
 #pragma unroll
-        for (int j = 0; j < 5; j++) x[j] = (v[j] - v[2]) * inv;
+        for (int k = 0; k < 5; k++) x[k] = (v[k] - v[2]) * inv;
         float w[3];
         mlp::warp_weights2(img, x, w);
-        if (sd ? ey : ex) {
+        if ((bits >> sd) & 1u) {
 #pragma unroll
-          for (int j = 0; j < 5; j++) v[j] = f[o + j * st];
+          for (int k = 0; k < 5; k++) v[k] = f[o + k * st];
           // delta form: constant stencils are reproduced exactly whatever the weights
-          const Cands k = candidates(v[0], v[1], v[2], v[3], v[4]);
-          const float hs = v[2] + w[0] * (k.q0 - v[2]) + w[1] * (k.q1 - v[2]) + w[2] * (k.q2 - v[2]);
+          const Cands q = candidates(v[0], v[1], v[2], v[3], v[4]);
+          const float hs = v[2] + w[0] * (q.q0 - v[2]) + w[1] * (q.q1 - v[2]) + w[2] * (q.q2 - v[2]);
           if (sd) h.y = hs;
           else h.x = hs;
         }
       }
       Fh[ps][c] = h.x + h.y;
     }
+    used = __reduce_add_sync(0xffffffffu, used);  // warp totals
+    seen = __reduce_add_sync(0xffffffffu, seen);
     if ((threadIdx.x & 31) == 0 && seen) {
       atomicAdd(&p.mlp_counts[0], (unsigned long long)used);
       atomicAdd(&p.mlp_counts[1], (unsigned long long)seen);
