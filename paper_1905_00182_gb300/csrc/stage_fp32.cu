@@ -345,6 +345,94 @@ __device__ __forceinline__ float2 teno5_pz_sides(const Plan &tw, float2 z0, floa
   return lin;
 }
 
+// The learned weights' face loop, in two phases.  First, unrolled as the component-wise pass,
+// packed TENO5 at every face and the eligibility of each side (TENO5 keeping all three stencils
+// and an amplitude above the floor), one bit per (pass, component, side).  Then a rolled loop
+// over (pass, component) with one call site of the warp-wide network (unrolled, the network's
+// code was copied 2 x NV x MAXP times and the kernel ran out of the instruction cache) visits
+// only the faces where some lane of the warp is eligible: a side with an eligible lane runs the
+// network for all 32 lanes' stencils of that side, and its eligible lanes take the delta-form
+// reconstruction with the network's weights.  zat(ps, c, valid) gives the interleaved stencil
+// z_0 (z_k ZS float2 further) of this thread's face slot ps, component c, and whether the slot
+// holds a face (an empty slot points at a valid stencil, its results unused).  Every lane of the
+// warp must call it; used / seen accumulate this lane's counts.
+template <int MAXP, int NV, int ZS, typename ZAt>
+__device__ __forceinline__ void learned_faces(const Plan &p, const unsigned char *img,
+                                              float (&Fh)[MAXP][NV], unsigned &used,
+                                              unsigned &seen, ZAt zat) {
+  static_assert(2 * MAXP * NV <= 32, "one eligibility bit per (pass, component, side)");
+  unsigned emask = 0;
+#pragma unroll
+  for (int ps = 0; ps < MAXP; ps++) {
+    bool valid = false;
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+      const float2 *z = zat(ps, c, valid);
+      const float2 z0 = z[0], z1 = z[ZS], z2 = z[2 * ZS], z3 = z[3 * ZS], z4 = z[4 * ZS];
+      bool kx, ky;
+      const float2 h = teno5_pz_sides(p, z0, z1, z2, z3, z4, kx, ky);
+      Fh[ps][c] = h.x + h.y;
+      // amplitude max_j |v_j - v_2| of each side (the same set of values in either order)
+      const float2 d0 = __ffma2_rn(f2(-1.f), z2, z0), d1 = __ffma2_rn(f2(-1.f), z2, z1);
+      const float2 d3 = __ffma2_rn(f2(-1.f), z2, z3), d4 = __ffma2_rn(f2(-1.f), z2, z4);
+      const float ax = fmaxf(fmaxf(fabsf(d0.x), fabsf(d1.x)), fmaxf(fabsf(d3.x), fabsf(d4.x)));
+      const float ay = fmaxf(fmaxf(fabsf(d0.y), fabsf(d1.y)), fmaxf(fabsf(d3.y), fabsf(d4.y)));
+      const bool ex = valid && kx && ax > p.mlp_floor, ey = valid && ky && ay > p.mlp_floor;
+      const int j = 2 * (ps * NV + c);
+      emask |= (ex ? 1u << j : 0u) | (ey ? 2u << j : 0u);
+    }
+    seen += valid ? 2 * NV : 0;
+  }
+  used += __popc(emask);
+#pragma unroll 1
+  for (int it = 0; it < MAXP * NV; it++) {
+    const unsigned bits = (emask >> (2 * it)) & 3u;
+    const unsigned bx = __ballot_sync(0xffffffffu, bits & 1u);
+    const unsigned by = __ballot_sync(0xffffffffu, bits & 2u);
+    if ((bx | by) == 0u) continue;  // warp-uniform
+    const int ps = it / NV, c = it % NV;
+    bool valid;
+    const float2 *z = zat(ps, c, valid);
+    // phase 1's TENO5 values again, where some lane keeps one of them (a side it is not
+    // eligible on): warp-uniform
+    float2 h = make_float2(0.f, 0.f);
+    if (__any_sync(0xffffffffu, bits != 3u)) {
+      bool kx, ky;
+      h = teno5_pz_sides(p, z[0], z[ZS], z[2 * ZS], z[3 * ZS], z[4 * ZS], kx, ky);
+    }
+#pragma unroll 1
+    for (int sd = 0; sd < 2; sd++) {
+      if ((sd ? by : bx) == 0u) continue;  // warp-uniform
+      // this side's stencil upwind to downwind, re-read from shared memory (nothing of it stays
+      // live across the network): f+ = z_0..z_4 .x, f- = z_4..z_0 .y
+      const volatile float *f = reinterpret_cast<const volatile float *>(z) + sd;
+      const int o = sd ? 8 * ZS : 0, st = sd ? -2 * ZS : 2 * ZS;
+      float v[5];
+#pragma unroll
+      for (int k = 0; k < 5; k++) v[k] = f[o + k * st];
+      float amp = 0.f;
+#pragma unroll
+      for (int k = 0; k < 5; k++) amp = fmaxf(amp, fabsf(v[k] - v[2]));
+      const float inv = amp > 1e-30f ? __fdividef(1.f, amp) : 0.f;
+      float x[5];
+#pragma unroll
+      for (int k = 0; k < 5; k++) x[k] = (v[k] - v[2]) * inv;
+      float w[3];
+      mlp::warp_weights2(img, x, w);
+      if ((bits >> sd) & 1u) {
+#pragma unroll
+        for (int k = 0; k < 5; k++) v[k] = f[o + k * st];
+        // delta form: constant stencils are reproduced exactly whatever the weights
+        const Cands q = candidates(v[0], v[1], v[2], v[3], v[4]);
+        const float hs = v[2] + w[0] * (q.q0 - v[2]) + w[1] * (q.q1 - v[2]) + w[2] * (q.q2 - v[2]);
+        if (sd) h.y = hs;
+        else h.x = hs;
+      }
+    }
+    Fh[ps][c] = h.x + h.y;
+  }
+}
+
 template <int SCHEME>
 __device__ __forceinline__ float recon(const Plan &tw, float a, float b, float c, float d,
                                        float e) {
@@ -650,96 +738,16 @@ __global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : (CHAR
   if constexpr (SCHEME == IBFSA_MLP_TENO5) {
     unsigned char *img = reinterpret_cast<unsigned char *>(smf + 2 * NV * T::ROWS * T::LEN);
     unsigned used = 0, seen = 0;
-    // Two phases.  First, unrolled as the component-wise pass, packed TENO5 at every face and the
-    // eligibility of each side (TENO5 keeping all three stencils and an amplitude above the
-    // floor), one bit per (pass, component, side).  Then a rolled loop over (pass, component)
-    // with one call site of the warp-wide network (unrolled, the network's code was copied
-    // 2 x NV x MAXP times and the kernel ran out of the instruction cache) visits only the faces
-    // where some lane of the warp is eligible: a side with an eligible lane runs the network for
-    // all 32 lanes' stencils of that side, and its eligible lanes take the delta-form
-    // reconstruction with the network's weights.
-    static_assert(2 * MAXP * NV <= 32, "one eligibility bit per (pass, component, side)");
     const float2 *Z = reinterpret_cast<const float2 *>(smf);
-    unsigned emask = 0;
-#pragma unroll
-    for (int ps = 0; ps < MAXP; ps++) {
+    learned_faces<MAXP, NV, 1>(p, img, Fh, used, seen, [&](int ps, int c, bool &valid) {
       int e = threadIdx.x + ps * THREADS;
       int row, fi;
       if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
       else { row = e % T::ROWS; fi = e / T::ROWS; }
-      const bool valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
+      valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
       if (!valid) { row = 0; fi = 0; }  // in-bounds reads; results discarded
-      seen += valid ? 2 * NV : 0;
-#pragma unroll
-      for (int c = 0; c < NV; c++) {
-        const float2 *z = Z + (c * T::ROWS + row) * T::LEN + fi;
-        const float2 z0 = z[0], z1 = z[1], z2 = z[2], z3 = z[3], z4 = z[4];
-        bool kx, ky;
-        const float2 h = teno5_pz_sides(p, z0, z1, z2, z3, z4, kx, ky);
-        Fh[ps][c] = h.x + h.y;
-        // amplitude max_j |v_j - v_2| of each side (the same set of values in either order)
-        const float2 d0 = __ffma2_rn(f2(-1.f), z2, z0), d1 = __ffma2_rn(f2(-1.f), z2, z1);
-        const float2 d3 = __ffma2_rn(f2(-1.f), z2, z3), d4 = __ffma2_rn(f2(-1.f), z2, z4);
-        const float ax = fmaxf(fmaxf(fabsf(d0.x), fabsf(d1.x)), fmaxf(fabsf(d3.x), fabsf(d4.x)));
-        const float ay = fmaxf(fmaxf(fabsf(d0.y), fabsf(d1.y)), fmaxf(fabsf(d3.y), fabsf(d4.y)));
-        const bool ex = valid && kx && ax > p.mlp_floor, ey = valid && ky && ay > p.mlp_floor;
-        const int j = 2 * (ps * NV + c);
-        emask |= (ex ? 1u << j : 0u) | (ey ? 2u << j : 0u);
-      }
-    }
-    used = __popc(emask);
-#pragma unroll 1
-    for (int it = 0; it < MAXP * NV; it++) {
-      const unsigned bits = (emask >> (2 * it)) & 3u;
-      const unsigned bx = __ballot_sync(0xffffffffu, bits & 1u);
-      const unsigned by = __ballot_sync(0xffffffffu, bits & 2u);
-      if ((bx | by) == 0u) continue;  // warp-uniform
-      const int ps = it / NV, c = it % NV;
-      int e = threadIdx.x + ps * THREADS;
-      int row, fi;
-      if constexpr (A == 0) { row = e / T::FACES; fi = e % T::FACES; }
-      else { row = e % T::ROWS; fi = e / T::ROWS; }
-      const bool valid = e < T::ROWS * T::FACES && row < nrow && fi < nface;
-      if (!valid) { row = 0; fi = 0; }
-      const float2 *z = Z + (c * T::ROWS + row) * T::LEN + fi;
-      // phase 1's TENO5 values again, where some lane keeps one of them (a side it is not
-      // eligible on): warp-uniform
-      float2 h = make_float2(0.f, 0.f);
-      if (__any_sync(0xffffffffu, bits != 3u)) {
-        bool kx, ky;
-        h = teno5_pz_sides(p, z[0], z[1], z[2], z[3], z[4], kx, ky);
-      }
-#pragma unroll 1
-      for (int sd = 0; sd < 2; sd++) {
-        if ((sd ? by : bx) == 0u) continue;  // warp-uniform
-        // this side's stencil upwind to downwind, re-read from shared memory (nothing of it
-        // stays live across the network): f+ = z_0..z_4 .x, f- = z_4..z_0 .y
-        const volatile float *f = reinterpret_cast<const volatile float *>(z) + sd;
-        const int o = sd ? 8 : 0, st = sd ? -2 : 2;
-        float v[5];
-#pragma unroll
-        for (int k = 0; k < 5; k++) v[k] = f[o + k * st];
-        float amp = 0.f;
-#pragma unroll
-        for (int k = 0; k < 5; k++) amp = fmaxf(amp, fabsf(v[k] - v[2]));
-        const float inv = amp > 1e-30f ? __fdividef(1.f, amp) : 0.f;
-        float x[5];
-#pragma unroll
-        for (int k = 0; k < 5; k++) x[k] = (v[k] - v[2]) * inv;
-        float w[3];
-        mlp::warp_weights2(img, x, w);
-        if ((bits >> sd) & 1u) {
-#pragma unroll
-          for (int k = 0; k < 5; k++) v[k] = f[o + k * st];
-          // delta form: constant stencils are reproduced exactly whatever the weights
-          const Cands q = candidates(v[0], v[1], v[2], v[3], v[4]);
-          const float hs = v[2] + w[0] * (q.q0 - v[2]) + w[1] * (q.q1 - v[2]) + w[2] * (q.q2 - v[2]);
-          if (sd) h.y = hs;
-          else h.x = hs;
-        }
-      }
-      Fh[ps][c] = h.x + h.y;
-    }
+      return Z + (c * T::ROWS + row) * T::LEN + fi;
+    });
     used = __reduce_add_sync(0xffffffffu, used);  // warp totals
     seen = __reduce_add_sync(0xffffffffu, seen);
     if ((threadIdx.x & 31) == 0 && seen) {
@@ -914,21 +922,25 @@ __device__ __forceinline__ bool block_wait_or_report(const Plan &p, uint64_t *ba
 }
 
 template <int DIM, int A, int SCHEME>
-__global__ void __launch_bounds__(THREADS, 5)
+__global__ void __launch_bounds__(THREADS, SCHEME == IBFSA_MLP_TENO5 ? 4 : 5)
     k_conv32_tma(Plan p, const __grid_constant__ CUtensorMap tq,
                  const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap tl) {
   using TT = TmaTile<DIM, A>;
   using T = Tile<A>;
   constexpr int NV = TT::NV, R = TT::R, LEN = TT::LEN, SEG = TT::SEG;
   constexpr int FST = T::FACES + 1;
-  static_assert(SCHEME != IBFSA_MLP_TENO5, "fixed schemes only");
+  // TENO5 and the learned weights stage interleaved face stencils z_l = (f+ at l, f- at l+1)
+  constexpr bool ZL = SCHEME == IBFSA_TENO5 || SCHEME == IBFSA_MLP_TENO5;
   extern __shared__ __align__(128) float smf[];
   float *in = smf;                         // [NV + 2][LEN][R], then L' [NV][SEG][R]
   float *sfp = smf + TT::IN;               // [NV][LEN - 1][R]: f+ at staged cells 0..LEN-2
   float *sfm = sfp + TT::SF;               // [NV][LEN - 1][R]: f- at staged cells 1..LEN-1
   uint64_t *bar = reinterpret_cast<uint64_t *>(sfm + TT::SF);
+  // the learned weights' parameter image follows the barrier (16-byte aligned)
+  unsigned char *img = reinterpret_cast<unsigned char *>(bar) + 16;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = THREADS / 32;
+  static_assert((sizeof(float) * (TT::IN + 2 * TT::SF) + 16) % 16 == 0, "image alignment");
 
   const int nseg = (p.n[A] + SEG - 1) / SEG;
   const int seg0 = (blockIdx.x % nseg) * SEG;
@@ -940,6 +952,9 @@ __global__ void __launch_bounds__(THREADS, 5)
   const int yi = A == 1 ? seg0 : other, zi = A == 1 ? other : seg0;  // first owned cell
 
   if (threadIdx.x == 0) tma::mbar_init(bar, 1);
+  if constexpr (SCHEME == IBFSA_MLP_TENO5)
+    mlp::stage_inference_image(reinterpret_cast<uint4 *>(img),
+                               reinterpret_cast<const uint4 *>(p.mlp_img), threadIdx.x, THREADS);
   __syncthreads();
   if (threadIdx.x == 0) {
     tma::mbar_expect_tx(bar, (uint32_t)(sizeof(float) * TT::IN));
@@ -961,7 +976,7 @@ __global__ void __launch_bounds__(THREADS, 5)
       for (int c = 0; c < NV; c++) q[c] = in[(c * LEN + l) * R + lane];
       split_cell<DIM, A>(fs, alpha, q, in[(NV * LEN + l) * R + lane],
                          in[((NV + 1) * LEN + l) * R + lane], fpv, fmv);
-      if constexpr (SCHEME == IBFSA_TENO5) {
+      if constexpr (ZL) {
         // interleaved face stencils z_l = (f+ at l, f- at l+1), [NV][LEN-1][R] float2
         float2 *Z = reinterpret_cast<float2 *>(sfp);
 #pragma unroll
@@ -989,6 +1004,22 @@ __global__ void __launch_bounds__(THREADS, 5)
   //    fi .. fi+4, f- at fi+1 .. fi+5
   constexpr int MAXP = (T::FACES + NW - 1) / NW;
   float Fh[MAXP][NV];
+  if constexpr (SCHEME == IBFSA_MLP_TENO5) {
+    const float2 *Z = reinterpret_cast<const float2 *>(sfp);
+    unsigned used = 0, seen = 0;
+    learned_faces<MAXP, NV, R>(p, img, Fh, used, seen, [&](int ps, int c, bool &valid) {
+      int fi = warp + ps * NW;
+      valid = fi < nface && row_ok;
+      if (fi >= nface) fi = 0;  // in-bounds reads; results discarded
+      return Z + (c * (LEN - 1) + fi) * R + lane;
+    });
+    used = __reduce_add_sync(0xffffffffu, used);  // warp totals
+    seen = __reduce_add_sync(0xffffffffu, seen);
+    if (lane == 0 && seen) {
+      atomicAdd(&p.mlp_counts[0], (unsigned long long)used);
+      atomicAdd(&p.mlp_counts[1], (unsigned long long)seen);
+    }
+  } else {
 #pragma unroll
   for (int ps = 0; ps < MAXP; ps++) {
     const int fi = warp + ps * NW;
@@ -1006,6 +1037,7 @@ __global__ void __launch_bounds__(THREADS, 5)
         }
       }
     }
+  }
   }
   __syncthreads();
   float *sh = sfp;  // face fluxes [NV][R][FST]
@@ -1743,18 +1775,20 @@ cudaError_t launch_conv(const Plan &p, int first, cudaStream_t st) {
       return cudaGetLastError();
     }
   }
-  if constexpr (A != 0 && SCHEME != IBFSA_MLP_TENO5) {
+  if constexpr (A != 0) {
     if (p.n[0] % 4 == 0 && !first) {
       using TT = TmaTile<DIM, A>;
+      constexpr size_t smem =
+          TT::BYTES + (SCHEME == IBFSA_MLP_TENO5 ? (size_t)mlp::PACKED_BYTES : 0);
       e = cudaFuncSetAttribute(k_conv32_tma<DIM, A, SCHEME>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::BYTES);
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       CUtensorMap tq, tw, tl;
       if ((e = conv_tensor_maps<DIM, A>(p, &tq, &tw, &tl)) != cudaSuccess) return e;
       int nseg = (p.n[A] + T::SEG - 1) / T::SEG;
       int nx = (p.n[0] + T::ROWS - 1) / T::ROWS;
       dim3 grid(nseg * nx, A == 1 ? p.n[2] : p.n[1]);
-      k_conv32_tma<DIM, A, SCHEME><<<grid, THREADS, TT::BYTES, st>>>(p, tq, tw, tl);
+      k_conv32_tma<DIM, A, SCHEME><<<grid, THREADS, smem, st>>>(p, tq, tw, tl);
       return cudaGetLastError();
     }
   }
