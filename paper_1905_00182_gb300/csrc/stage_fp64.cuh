@@ -168,16 +168,19 @@ __device__ __forceinline__ double teno5(const Plan &p, double a, double b, doubl
 // Fast arithmetic only: TENO5 keeps every stencil when tau5 <= 4 (min beta + eps) -- each
 // gamma_k lies in [1, 5^6], so chi_k >= 1/(3 5^6) = 2.1e-5 > C_T -- and the reconstruction is
 // the optimal linear combination (2a - 13b + 47c + 27d - 3e)/60 (the strict form evaluates
-// every step as written).
+// every step as written).  The test is scale-invariant: it takes the indicators times 4,
+// (13/3) t^2 + u^2, exactly 4 beta_k (a power of two commutes with every rounding), against
+// 4 min + 1.6e-39; the linear combination takes the coefficients over 60.
 __device__ __forceinline__ double teno5_fast(const Plan &p, double a, double b, double c,
                                              double d, double e) {
-  const double k13 = 13.0 / 12.0;
+  const double k13 = 13.0 / 3.0;
   double t, u, b0, b1, b2;
-  t = a - 2.0 * b + c; u = a - 4.0 * b + 3.0 * c; b0 = k13 * t * t + 0.25 * u * u;
-  t = b - 2.0 * c + d; u = b - d;                 b1 = k13 * t * t + 0.25 * u * u;
-  t = c - 2.0 * d + e; u = 3.0 * c - 4.0 * d + e; b2 = k13 * t * t + 0.25 * u * u;
-  if (fabs(b0 - b2) <= 4.0 * (fmin(b0, fmin(b1, b2)) + 1e-40))
-    return (2.0 * a - 13.0 * b + 47.0 * c + 27.0 * d - 3.0 * e) * (1.0 / 60.0);
+  t = a - 2.0 * b + c; u = a - 4.0 * b + 3.0 * c; b0 = k13 * t * t + u * u;
+  t = b - 2.0 * c + d; u = b - d;                 b1 = k13 * t * t + u * u;
+  t = c - 2.0 * d + e; u = 3.0 * c - 4.0 * d + e; b2 = k13 * t * t + u * u;
+  if (fabs(b0 - b2) <= 4.0 * fmin(b0, fmin(b1, b2)) + 1.6e-39)
+    return (2.0 / 60.0) * a - (13.0 / 60.0) * b + (47.0 / 60.0) * c + (27.0 / 60.0) * d -
+           (3.0 / 60.0) * e;
   return teno5(p, a, b, c, d, e);
 }
 
