@@ -217,49 +217,8 @@ __device__ __forceinline__ float teno5_fast(const Plan &tw, float a, float b, fl
   return teno5(tw, a, b, c, d, e);
 }
 
-// TENO5 at one face for both split fluxes at once on packed FP32x2 arithmetic (.x: the f+
-// stencil, .y: the f- stencil, each ordered upwind to downwind): smoothness indicators and the
-// linear combination for both sides in one instruction each; a side that fails the all-kept
-// test takes the full scalar TENO5.  Returns each side's face value and whether it keeps all
-// three stencils (kx / ky: by the all-kept test or by the full cut-off).
+// make_float2(v, v)
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
-
-__device__ __forceinline__ float2 teno5_sides(const Plan &tw, float2 a, float2 b, float2 c,
-                                              float2 d, float2 e, bool &kx, bool &ky) {
-  float2 t0 = __fadd2_rn(__ffma2_rn(f2(-2.f), b, a), c);
-  float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.f), c, b), d);
-  float2 t2 = __fadd2_rn(__ffma2_rn(f2(-2.f), d, c), e);
-  float2 u0 = __ffma2_rn(f2(3.f), c, __ffma2_rn(f2(-4.f), b, a));
-  float2 u1 = __ffma2_rn(f2(-1.f), d, b);
-  float2 u2 = __ffma2_rn(f2(3.f), c, __ffma2_rn(f2(-4.f), d, e));
-  const float2 k13 = f2(13.f / 12.f), q = f2(0.25f);
-  float2 b0 = __ffma2_rn(__fmul2_rn(k13, t0), t0, __fmul2_rn(__fmul2_rn(q, u0), u0));
-  float2 b1 = __ffma2_rn(__fmul2_rn(k13, t1), t1, __fmul2_rn(__fmul2_rn(q, u1), u1));
-  float2 b2 = __ffma2_rn(__fmul2_rn(k13, t2), t2, __fmul2_rn(__fmul2_rn(q, u2), u2));
-  float2 tau = __ffma2_rn(f2(-1.f), b2, b0);
-  kx = fabsf(tau.x) <= 4.f * (fminf(b0.x, fminf(b1.x, b2.x)) + 1e-30f);
-  ky = fabsf(tau.y) <= 4.f * (fminf(b0.y, fminf(b1.y, b2.y)) + 1e-30f);
-  float2 lin = __fmul2_rn(f2(2.f / 60.f), a);
-  lin = __ffma2_rn(f2(-13.f / 60.f), b, lin);
-  lin = __ffma2_rn(f2(47.f / 60.f), c, lin);
-  lin = __ffma2_rn(f2(27.f / 60.f), d, lin);
-  lin = __ffma2_rn(f2(-3.f / 60.f), e, lin);
-  if (!kx) {
-    Cands k = candidates(a.x, b.x, c.x, d.x, e.x);
-    int mask = teno_mask(k);
-    const float *w = tw.teno_w32[mask];
-    lin.x = w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
-    kx = mask == 7;
-  }
-  if (!ky) {
-    Cands k = candidates(a.y, b.y, c.y, d.y, e.y);
-    int mask = teno_mask(k);
-    const float *w = tw.teno_w32[mask];
-    lin.y = w[0] * k.q0 + w[1] * k.q1 + w[2] * k.q2;
-    ky = mask == 7;
-  }
-  return lin;
-}
 
 // TENO5 at one face for both split fluxes on packed FP32x2 arithmetic, with a warp-uniform slow
 // path: every lane of the warp must call it.  The input is the interleaved face stencil
