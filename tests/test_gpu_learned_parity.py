@@ -1,6 +1,8 @@
 """The learned-weight form (IBFSA_MLP_TENO5) element by element against the oracle's learned
 scheme, on the stress state (smooth random modes in every primitive plus a 10 % contact step),
-where the network supplies the weights of nearly every reconstruction.
+where the network supplies the weights of nearly every reconstruction: 2D with the generic and
+with the tensor-copy tiles in y, 3D, and 2D on a stretched x direction with characteristic
+non-reflecting faces.
 
 The GPU evaluates the same definition as the oracle -- TENO5's cut-off as the guard, the
 normalised stencil, the network on bfloat16 parameters and bfloat16 activations, the delta-form
@@ -56,8 +58,11 @@ def _spec(dim, n):
                       precision=W.FP32_PERTURB, bc=bc)
 
 
-def _gpu_rhs(ib, spec, Q, net=None):
+def _gpu_rhs(ib, spec, Q, net=None, mesh=None):
     g = ib.Grid(spec)
+    for a, m in enumerate(mesh or []):
+        if m is not None:
+            g.set_mesh(a, *m)
     if net is not None:
         ib.ibfsa_set_mlp(g.h, net.ptr)
         ib.ibfsa_mlp_stats(g.h)
@@ -69,21 +74,35 @@ def _gpu_rhs(ib, spec, Q, net=None):
     return L, counts
 
 
-@pytest.mark.parametrize("dim,n", [(2, (90, 70, 1)), (3, (36, 30, 28))])
-def test_learned_rhs_matches_the_oracle_on_the_stress_state(dim, n):
+# (dim, n, variant): the x extent 90 takes the generic tiles in y, 92 and 36 the tensor-copy
+# tiles; "stretched+char" stretches x (the contact inside the uniform part) and puts the
+# characteristic non-reflecting rule on both x faces and the high-y face (zero-gradient low y)
+CASES = [(2, (90, 70, 1), None), (2, (92, 70, 1), None), (3, (36, 30, 28), None),
+         (2, (92, 70, 1), "stretched+char")]
+
+
+@pytest.mark.parametrize("dim,n,variant", CASES)
+def test_learned_rhs_matches_the_oracle_on_the_stress_state(dim, n, variant):
     ib = _ib()
     spec = _spec(dim, n)
+    mesh = None
+    if variant == "stretched+char":
+        ax = W.stretched_axis(n[0], 1.0 / n[0], 1.6 / n[0], 40, 8, center=0.5)
+        mesh = [(ax[2], ax[3]), None]
+        CH = W.BC_CHARACTERISTIC
+        spec = dataclasses.replace(spec, lo=(ax[0], 0.0, 0.0), hi=(ax[1], 1.0, 1.0),
+                                   bc=((CH, CH), (0, CH), (0, 0)))
     Q = W.stress_state_torch(spec, device="cpu").numpy()
     params = _params()
     net = ib.MLP(params)
-    L_ml, (used, seen) = _gpu_rhs(ib, spec, Q, net)
-    L_te, _ = _gpu_rhs(ib, dataclasses.replace(spec, scheme=W.TENO5), Q)
+    L_ml, (used, seen) = _gpu_rhs(ib, spec, Q, net, mesh)
+    L_te, _ = _gpu_rhs(ib, dataclasses.replace(spec, scheme=W.TENO5), Q, None, mesh)
 
     mlp = O.Learned(M.bf16(np.asarray(params, dtype=np.float32).astype(np.float64)),
                     round_act=True, floor=1e-9)
-    Lo_ml = O.rhs(spec, Q, mlp=mlp)
+    Lo_ml = O.rhs(spec, Q, mlp=mlp, stretch=mesh)
     o_used, o_seen = O.mlp_counts()
-    Lo_te = O.rhs(spec, Q)
+    Lo_te = O.rhs(spec, Q, stretch=mesh)
 
     # the GPU evaluates the faces on its tiles' edges once for each tile (its counts include
     # them); the oracle counts each face once: compare the shares
