@@ -1,7 +1,7 @@
 // pipe_rates.cu -- throughput of the arithmetic pipes the stage kernels lean on: the FP64
 // fused multiply-add (the FP64 forms' bound), the FP32 fused multiply-add scalar and packed
-// (FP32x2), and the multi-function unit's tanh, exp2 and reciprocal approximations (the learned
-// weights' gelu and softmax).  Standalone executable, no library calls on a hot path; prints one
+// (FP32x2), the multi-function unit's tanh, exp2 and reciprocal approximations (the learned
+// weights' gelu and softmax), and the FP64 <-> FP32 conversions.  Standalone executable, no library calls on a hot path; prints one
 // line per operation: elements per second over the whole GPU and elements per clock per SM at
 // the device's maximum SM clock.
 //
@@ -105,6 +105,22 @@ __global__ void k_rcp(double *out, double s) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
+// double -> float -> double: two conversions per element (the pipe they issue to bounds it)
+__global__ void k_cvt(double *out, double s) {
+  double x[CHAINS];
+  for (int c = 0; c < CHAINS; c++) x[c] = 1.0 + s * (threadIdx.x + c + 1);
+  for (int i = 0; i < ITERS; i++)
+#pragma unroll
+    for (int c = 0; c < CHAINS; c++) {
+      float f;
+      asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(f) : "d"(x[c]));
+      asm volatile("cvt.f64.f32 %0, %1;" : "=d"(x[c]) : "f"(f));
+    }
+  double r = 0;
+  for (int c = 0; c < CHAINS; c++) r += x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
 struct Op {
   const char *name;
   void (*k)(double *, double);
@@ -129,7 +145,8 @@ int main() {
   const Op ops[] = {{"fma.rn.f64", k_dfma, 1},         {"fma.rn.f32", k_ffma, 1},
                     {"fma.rn.f32x2 (packed)", k_ffma2, 2}, {"tanh.approx.f32", k_tanh, 1},
                     {"tanh.approx.f16x2", k_tanh_h2, 2}, {"ex2.approx.ftz.f32", k_ex2, 1},
-                    {"rcp.approx.ftz.f32 (+1)", k_rcp, 1}};
+                    {"rcp.approx.ftz.f32 (+1)", k_rcp, 1},
+                    {"cvt f64->f32->f64 (pairs)", k_cvt, 2}};
   printf("SMs %d, maximum SM clock %.0f MHz\n", sms, khz / 1e3);
   for (const Op &op : ops) {
     for (int r = 0; r < 3; r++) op.k<<<grid, block>>>(out, 1e-3);
