@@ -166,7 +166,11 @@ def stage_roofline(bpc, cells, stage_ms, hbm_peak, peak_kind, flops, peak_tf, tr
             "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
             "peak_note": f"{peak_kind} copy bandwidth", "bytes_per_cell_stage": bpc,
             "stage_ms": stage_ms, "alu_achieved_tflops": alu, "alu_peak_tflops": peak_tf,
-            "alu_frac": alu / peak_tf, "traffic": traffic}
+            "alu_frac": alu / peak_tf,
+            "alu_note": "algorithmic operations of the method (TENO5's non-linear weights at "
+                        "every face); the FP32 and fast FP64 forms take the linear weights "
+                        "where TENO5 keeps every stencil, so this rate can exceed the pipe's",
+            "traffic": traffic}
 
 
 def stage_traffic(classes, precision):

@@ -168,19 +168,22 @@ __device__ __forceinline__ double teno5(const Plan &p, double a, double b, doubl
 // Fast arithmetic only: TENO5 keeps every stencil when tau5 <= 4 (min beta + eps) -- each
 // gamma_k lies in [1, 5^6], so chi_k >= 1/(3 5^6) = 2.1e-5 > C_T -- and the reconstruction is
 // the optimal linear combination (2a - 13b + 47c + 27d - 3e)/60 (the strict form evaluates
-// every step as written).  Only this sufficient test is taken in FP32, on the FP64 second and
-// first differences rounded to FP32 (the FP64 pipe is the bound: three FP32 indicators replace
-// nine FP64 operations and the comparison five): indicators times 4, (13/3) t^2 + u^2, against
-// 4 min + 1.6e-29.  Their relative error, a few 1e-7, is far inside the test's factor-2 margin
-// (chi_k >= 2.1e-5 against C_T = 1e-5), so a stencil the test keeps is one TENO5 keeps; where
-// the test fails, the full FP64 TENO5 decides.  Differences below FP32's range flush to zero
-// and pass the test; their stencils vary by less than 1e-17 of the flux, whatever TENO5 would
-// cut.  The linear combination takes the coefficients over 60.
+// every step as written).  Only this sufficient test is taken in FP32 (the FP64 pipe is the
+// bound; a conversion issues at the FP64 rate): the four first differences in FP64, rounded to
+// FP32, give t and u of every indicator (t0 = d2 - d1, u0 = 3 d2 - d1, t1 = d3 - d2,
+// u1 = -(d2 + d3), t2 = d4 - d3, u2 = d4 - 3 d3), taken times 4, (13/3) t^2 + u^2, against
+// 4 min + 1.6e-29.  Each indicator is a positive definite form of its two differences, so its
+// relative error stays a few 1e-7 (where t or u cancels, the other term dominates) -- far
+// inside the test's factor-2 margin in chi_k (2.1e-5 against C_T = 1e-5): a stencil the test
+// keeps is one TENO5 keeps; where the test fails, the full FP64 TENO5 decides.  Differences
+// below FP32's range flush to zero and pass the test; their stencils vary by less than 1e-17
+// of the flux, whatever TENO5 would cut.  The linear combination takes the coefficients over 60.
 __device__ __forceinline__ double teno5_fast(const Plan &p, double a, double b, double c,
                                              double d, double e) {
-  const float t0 = (float)(a - 2.0 * b + c), u0 = (float)(a - 4.0 * b + 3.0 * c);
-  const float t1 = (float)(b - 2.0 * c + d), u1 = (float)(b - d);
-  const float t2 = (float)(c - 2.0 * d + e), u2 = (float)(3.0 * c - 4.0 * d + e);
+  const float d1 = (float)(b - a), d2 = (float)(c - b), d3 = (float)(d - c), d4 = (float)(e - d);
+  const float t0 = d2 - d1, u0 = fmaf(3.f, d2, -d1);
+  const float t1 = d3 - d2, u1 = d2 + d3;
+  const float t2 = d4 - d3, u2 = fmaf(-3.f, d3, d4);
   const float k13 = 13.f / 3.f;
   const float b0 = fmaf(k13 * t0, t0, u0 * u0);
   const float b1 = fmaf(k13 * t1, t1, u1 * u1);
