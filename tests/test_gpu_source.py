@@ -49,18 +49,18 @@ def test_source_steps_match_oracle(strict):
     Q = g.get_state().cpu().numpy()
     assert g.status() == 0
     Qo, _ = O.rk3(spec, Q0, dt, steps, w["X"], w["U"], w["dS"], t=t0)
-    # strict: only the exp of the source differs; fast: also fused multiply-adds and
-    # reciprocals everywhere (a few roundings of the state per stage, as in the fast parity tests)
-    # (the fast form's atomic spreading reorders the marker sums, measured in the norm as in
-    # the fast cylinder-pulse test)
+    # strict: only the exp of the source differs (a few roundings of each component's own free
+    # stream value); fast: also fused multiply-adds, reciprocals, atomic spreading (marker sums
+    # reordered) and TENO5's linear weights wherever its sufficient all-kept test passes -- a few
+    # roundings per stage of split fluxes whose scale is the free stream's largest component
+    # (E), twelve stages here: per element within 64 eps of it (measured at most 22 eps, in
+    # momentum; 12 eps in density)
+    qmax = max(abs(v) for v in spec.qinf[:spec.nv])
     for c in range(spec.nv):
-        if strict:
-            pert = np.max(np.abs(Qo[c] - spec.qinf[c]))
-            assert pert > 0
-            assert np.max(np.abs(Q[c] - Qo[c])) <= 1e-12 * pert + 4 * EPS * abs(spec.qinf[c]), c
-        else:
-            pert = np.linalg.norm(Qo[c] - spec.qinf[c])
-            assert np.linalg.norm(Q[c] - Qo[c]) <= 1e-10 * pert + 36 * EPS * abs(spec.qinf[c]), c
+        pert = np.max(np.abs(Qo[c] - spec.qinf[c]))
+        assert pert > 0
+        tol = 4 * EPS * abs(spec.qinf[c]) if strict else 64 * EPS * qmax
+        assert np.max(np.abs(Q[c] - Qo[c])) <= 1e-12 * pert + tol, c
 
 
 def test_source_fp32_form_within_1e3():
