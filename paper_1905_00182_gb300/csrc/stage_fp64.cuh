@@ -244,16 +244,18 @@ __global__ void __launch_bounds__(THREADS) k_pad(Plan p, const double *__restric
     for (int c = 0; c < NV; c++) p.Qp[c * p.NP + t] = q[c];
     double rho = q[0];
     double ke = 0.0, u[DIM];
+    // strict: each division as the oracle writes it; fast: one reciprocal of rho
+    const double inv_rho = STRICT ? 0.0 : 1.0 / rho;
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
-      u[a] = q[1 + a] / rho;
+      u[a] = STRICT ? q[1 + a] / rho : q[1 + a] * inv_rho;
       ke += q[1 + a] * u[a];
       p.Wp[a * p.NP + t] = u[a];
     }
     double pr = p.gm1 * (q[NV - 1] - 0.5 * ke);
     p.Wp[DIM * p.NP + t] = pr;
     if (interior) {
-      double c = sqrt(p.gamma * pr / rho);
+      double c = sqrt(STRICT ? p.gamma * pr / rho : p.gamma * pr * inv_rho);
 #pragma unroll
       for (int a = 0; a < DIM; a++) wmax[a] = fabs(u[a]) + c;
     }
