@@ -177,10 +177,11 @@ __device__ __forceinline__ double teno5(const Plan &p, double a, double b, doubl
 // inside the test's factor-2 margin in chi_k (2.1e-5 against C_T = 1e-5): a stencil the test
 // keeps is one TENO5 keeps; where the test fails, the full FP64 TENO5 decides.  Differences
 // below FP32's range flush to zero and pass the test; their stencils vary by less than 1e-17
-// of the flux, whatever TENO5 would cut.  The linear combination takes the coefficients over 60.
+// of the flux, whatever TENO5 would cut.
 __device__ __forceinline__ double teno5_fast(const Plan &p, double a, double b, double c,
                                              double d, double e) {
-  const float d1 = (float)(b - a), d2 = (float)(c - b), d3 = (float)(d - c), d4 = (float)(e - d);
+  const double e1 = b - a, e2 = c - b, e3 = d - c, e4 = e - d;
+  const float d1 = (float)e1, d2 = (float)e2, d3 = (float)e3, d4 = (float)e4;
   const float t0 = d2 - d1, u0 = fmaf(3.f, d2, -d1);
   const float t1 = d3 - d2, u1 = d2 + d3;
   const float t2 = d4 - d3, u2 = fmaf(-3.f, d3, d4);
@@ -188,9 +189,10 @@ __device__ __forceinline__ double teno5_fast(const Plan &p, double a, double b, 
   const float b0 = fmaf(k13 * t0, t0, u0 * u0);
   const float b1 = fmaf(k13 * t1, t1, u1 * u1);
   const float b2 = fmaf(k13 * t2, t2, u2 * u2);
+  // the linear combination as c plus its differences, (-2 d1 + 11 d2 + 24 d3 - 3 d4)/60: four
+  // fused multiply-adds, and a constant stencil gives c exactly
   if (fabsf(b0 - b2) <= fmaf(4.f, fminf(b0, fminf(b1, b2)), 1.6e-29f))
-    return (2.0 / 60.0) * a - (13.0 / 60.0) * b + (47.0 / 60.0) * c + (27.0 / 60.0) * d -
-           (3.0 / 60.0) * e;
+    return fma(-3.0 / 60.0, e4, fma(24.0 / 60.0, e3, fma(11.0 / 60.0, e2, fma(-2.0 / 60.0, e1, c))));
   return teno5(p, a, b, c, d, e);
 }
 
@@ -377,6 +379,10 @@ __host__ __device__ constexpr size_t conv_smem_bytes() {
 template <int DIM, int A, int SCHEME, bool CHAR>
 __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
   constexpr int NV = DIM + 2;
+  // TENO5's weights depend on ratios of indicators only (its floors aside), so its fast
+  // component-wise form can reconstruct F +- alpha q and halve once at the face; WENO5-JS's
+  // eps = 1e-6 is not scale-free
+  constexpr bool FOLD = !STRICT && !CHAR && SCHEME == IBFSA_TENO5;
   using T = ConvTile<A>;
   extern __shared__ double sm[];
   double *sfp = sm;                              // [NV][ROWS][LEN]
@@ -435,8 +441,9 @@ __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
           F = q * ua;
           if (c - 1 == A) F += pr;
         }
-        sfp[(c * T::ROWS + row) * T::LEN + l] = 0.5 * (F + alpha * q);
-        sfm[(c * T::ROWS + row) * T::LEN + l] = 0.5 * (F - alpha * q);
+        // fast component-wise TENO5: F +- alpha q, the halves taken once at the face
+        sfp[(c * T::ROWS + row) * T::LEN + l] = FOLD ? fma(alpha, q, F) : 0.5 * (F + alpha * q);
+        sfm[(c * T::ROWS + row) * T::LEN + l] = FOLD ? fma(-alpha, q, F) : 0.5 * (F - alpha * q);
       }
     } else {
 #pragma unroll
@@ -512,8 +519,9 @@ __global__ void __launch_bounds__(THREADS) k_conv(Plan p, int first) {
         for (int c = 0; c < NV; c++) {
           const double *fp = sfp + (c * T::ROWS + row) * T::LEN;
           const double *fm = sfm + (c * T::ROWS + row) * T::LEN;
-          Fh[ps][c] = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
-                      recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+          const double h = recon<SCHEME>(p, fp[b - 2], fp[b - 1], fp[b], fp[b + 1], fp[b + 2]) +
+                           recon<SCHEME>(p, fm[b + 3], fm[b + 2], fm[b + 1], fm[b], fm[b - 1]);
+          Fh[ps][c] = FOLD ? 0.5 * h : h;
         }
       }
     }
