@@ -50,7 +50,7 @@ enum {
   IBFSA_ERR_CUDA = -2,        /* a CUDA runtime call failed */
   IBFSA_ERR_NONFINITE = -3,   /* state holds NaN/Inf (reported by ibfsa_get_status) */
   IBFSA_ERR_BOUNDS = -4,      /* marker/probe support outside the interior */
-  IBFSA_ERR_UNSUPPORTED = -5, /* descriptor asks for a variant this build does not provide */
+  IBFSA_ERR_UNSUPPORTED = -5, /* descriptor asks for a variant the library does not provide */
   IBFSA_ERR_WORKSPACE = -6    /* workspace too small or misaligned */
 };
 

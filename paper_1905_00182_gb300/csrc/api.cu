@@ -58,11 +58,11 @@ static int check_desc(const ibfsa_grid_desc *d) {
   if (!(d->gamma > 1.0)) return fail(IBFSA_ERR_ARG, "gamma must exceed 1");
   if (!(d->qinf[0] > 0.0)) return fail(IBFSA_ERR_ARG, "free-stream density must be positive");
   if (d->scheme != IBFSA_WENO5JS && d->scheme != IBFSA_TENO5 && d->scheme != IBFSA_MLP_TENO5)
-    return fail(IBFSA_ERR_UNSUPPORTED, "scheme %d is not provided by this build", d->scheme);
+    return fail(IBFSA_ERR_UNSUPPORTED, "scheme %d is not provided by the library", d->scheme);
   if (d->scheme == IBFSA_MLP_TENO5 && d->precision != IBFSA_FP32_PERTURB)
     return fail(IBFSA_ERR_UNSUPPORTED, "the learned weights run in the FP32 perturbation form");
   if (d->precision != IBFSA_FP64 && d->precision != IBFSA_FP32_PERTURB)
-    return fail(IBFSA_ERR_UNSUPPORTED, "precision %d is not provided by this build", d->precision);
+    return fail(IBFSA_ERR_UNSUPPORTED, "precision %d is not provided by the library", d->precision);
   if (d->precision == IBFSA_FP32_PERTURB && d->strict_fp)
     return fail(IBFSA_ERR_UNSUPPORTED, "strict_fp applies to the FP64 arithmetic only");
   if (d->sponge_cells < 0 || d->max_markers < 0 || d->max_probes < 0)
