@@ -94,7 +94,10 @@ typedef struct {
                               cell by cell in marker order -- the result is reproducible bit
                               for bit by a sequential FP64 evaluation of the same formulas in
                               the same order.  0: fused multiply-add and reciprocals allowed,
-                              spreading by atomics (faster; rounding differs). */
+                              spreading by atomics, TENO5's linear weights taken wherever its
+                              sufficient all-kept test (tau5 <= 4 min beta, evaluated in FP32
+                              on the stencil's FP64 differences) passes -- the weights TENO5
+                              gives there (faster; rounding differs). */
   int bc[3][2];            /* IBFSA_BC_* for the low/high face of each direction; periodic
                               needs both faces periodic and n >= 4 */
   int sponge_cells;        /* width S of an absorbing layer (0 = none): L -= sigma (Q - qinf)
