@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(THREADS) k_pad(Plan p, const double *__restric
   constexpr int NV = DIM + 2;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double wmax[3] = {0.0, 0.0, 0.0};
+  double c2 = 0.0, ua[3] = {0.0, 0.0, 0.0};  // fast form: c^2 and |u_a| of an interior cell
+  bool have = false;
   if (t < p.NP) {
     int ix = (int)(t % p.P[0]);
     long long r = t / p.P[0];
@@ -257,26 +259,67 @@ __global__ void __launch_bounds__(THREADS) k_pad(Plan p, const double *__restric
     double pr = p.gm1 * (q[NV - 1] - 0.5 * ke);
     p.Wp[DIM * p.NP + t] = pr;
     if (interior) {
-      double c = sqrt(STRICT ? p.gamma * pr / rho : p.gamma * pr * inv_rho);
+      if constexpr (STRICT) {
+        const double c = sqrt(p.gamma * pr / rho);
 #pragma unroll
-      for (int a = 0; a < DIM; a++) wmax[a] = fabs(u[a]) + c;
+        for (int a = 0; a < DIM; a++) wmax[a] = fabs(u[a]) + c;
+      } else {
+        c2 = p.gamma * pr * inv_rho;
+#pragma unroll
+        for (int a = 0; a < DIM; a++) ua[a] = fabs(u[a]);
+        have = true;
+      }
     }
   }
-  // block max of the (non-negative) speeds, then one atomic per block on the ordered bits
-  __shared__ double red[3][THREADS / 32];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if constexpr (!STRICT) {
+    // The block's maxima in FP32 first: the FP64 sound speed is taken only where |u| + c in
+    // FP32 lies within 2e-6 of the block's FP32 maximum (their relative errors, and that of
+    // the threshold, stay below 3e-7, so the cell of the exact maximum is among them); the
+    // other cells give 0 -- the same FP64 maxima for a fraction of the square roots.
+    __shared__ float red32[3][THREADS / 32];
+    const float c32 = have ? sqrtf((float)c2) : 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+      float v = have ? (float)ua[a] + c32 : 0.f;
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) red32[a][wid] = v;
+    }
+    __syncthreads();
+    float m32[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < DIM; a++)
+      for (int w = 0; w < THREADS / 32; w++) m32[a] = fmaxf(m32[a], red32[a][w]);
+    bool near = false;
+#pragma unroll
+    for (int a = 0; a < DIM; a++)
+      near |= have && !((float)ua[a] + c32 < m32[a] * (1.f - 2e-6f));  // NaN counts as near
+    if (near) {
+      const double c = sqrt(c2);
+#pragma unroll
+      for (int a = 0; a < DIM; a++) wmax[a] = ua[a] + c;
+    }
+  }
+  // block max of the (non-negative) speeds on their bits (the order of non-negative doubles is
+  // that of their bit patterns; a NaN's pattern exceeds every finite one), then one atomic per
+  // block
+  __shared__ unsigned long long red[3][THREADS / 32];
 #pragma unroll
   for (int a = 0; a < DIM; a++) {
-    double v = wmax[a];
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    unsigned long long v = (unsigned long long)__double_as_longlong(wmax[a]);
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
     if (lane == 0) red[a][wid] = v;
   }
   __syncthreads();
   if (threadIdx.x < DIM) {
-    double v = 0.0;
-    for (int w = 0; w < THREADS / 32; w++) v = fmax(v, red[threadIdx.x][w]);
+    unsigned long long b = 0;
+    for (int w = 0; w < THREADS / 32; w++) b = red[threadIdx.x][w] > b ? red[threadIdx.x][w] : b;
+    const double v = __longlong_as_double((long long)b);
     if (!(v <= 1e300)) atomicOr(p.status, IBFSA_STATUS_NONFINITE);
-    else atomicMax(&p.alpha_bits[threadIdx.x], (unsigned long long)__double_as_longlong(v));
+    else atomicMax(&p.alpha_bits[threadIdx.x], b);
   }
 }
 
