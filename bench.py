@@ -37,7 +37,8 @@ from paper_1905_00182_gb300 import workloads as W  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
 SMS = 152
-FP64_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per SM per clock (measured 1.19 TFLOP/s at ~2.0 GHz)
+FP64_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per SM per clock by the unit count (the pipe-rate probe
+                              # measures 1.7)
 FP32_FLOP_PER_CLK_PER_SM = 256  # 128 FP32 FMA lanes per SM per clock
 
 
