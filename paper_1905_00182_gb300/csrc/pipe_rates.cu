@@ -1,9 +1,9 @@
 // pipe_rates.cu -- throughput of the arithmetic pipes the stage kernels lean on: the FP64
 // fused multiply-add (the FP64 forms' bound), the FP32 fused multiply-add scalar and packed
 // (FP32x2), the multi-function unit's tanh, exp2 and reciprocal approximations (the learned
-// weights' gelu and softmax), and the FP64 <-> FP32 conversions.  Standalone executable, no library calls on a hot path; prints one
-// line per operation: elements per second over the whole GPU and elements per clock per SM at
-// the device's maximum SM clock.
+// weights' gelu and softmax), and the FP64 <-> FP32 conversions.  Standalone executable, no
+// library calls on a hot path; prints one line per operation: elements per second over the
+// whole GPU and elements per clock per SM at the device's maximum SM clock.
 //
 // Each thread runs eight independent dependency chains of the operation (enough to fill the
 // pipes at 8 warps per SM quarter); the grid is 8 blocks of 256 threads per SM; each kernel is
